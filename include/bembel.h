@@ -1,0 +1,220 @@
+/*
+ * bembel.h - C ABI of the GB300 (sm_103a) isogeometric single-layer BEM library.
+ *
+ * The library assembles and applies the Galerkin matrix of the single-layer
+ * boundary integral operators of the Bembel paper (Doelz, Harbrecht, Kurz,
+ * Multerer, Schoeps, Wolf), App. B eq. (LS) Laplace and eq. (HS) Helmholtz,
+ *   <S phi_j, phi_i> = int_Gamma int_Gamma G(x, y) phi_j(y) phi_i(x),
+ * on the B-spline space S^2 of App. E lifted to the patches of App. D by the
+ * 2-form Piola transform, with the far field compressed by interpolating the
+ * kernel on the parameter domain (Sec. 2, embedded fast multipole / H^2) and
+ * the near field integrated by Gauss rules and Duffy-type regularisation
+ * (Sec. 2).  All compute runs in CUDA kernels on the current device; there is
+ * no CPU fallback.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Return value: BEMBEL_OK (0) or one of the BEMBEL_E* codes below; on error
+ *   bembel_last_error() returns a message (thread-local, valid until the next
+ *   call on the same thread).  No C++ exception crosses this boundary.
+ * - Handles (bembel_geom*, bembel_op*) are created and owned by the library;
+ *   release them with the matching *_destroy call.  A handle may be used by one
+ *   host thread at a time.
+ * - Vector arguments named *_dev are caller-owned DEVICE pointers.  Block
+ *   vectors are column-major n x nrhs (column r starts at r*n elements).
+ *   Real operators (Laplace) use double; complex operators (Helmholtz) use
+ *   interleaved complex double {re, im}, i.e. 2*n*nrhs doubles.
+ * - Work is ordered on the stream given in bembel_opts.stream at assembly
+ *   (NULL = legacy default stream).  bembel_matvec and bembel_eval return
+ *   without synchronising; bembel_assemble, bembel_rhs and bembel_solve
+ *   return after the stream has drained.
+ * - Global dof numbering of S^2 on level L and degree d (n1 = 2^L + d):
+ *   dof = patch * n1^2 + j2 * n1 + j1, with (j1, j2) the B-spline indices along
+ *   the first and second patch parameter.
+ */
+#ifndef BEMBEL_H
+#define BEMBEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define BEMBEL_OK 0
+#define BEMBEL_EINVAL 1        /* invalid argument or handle                   */
+#define BEMBEL_ENOMEM 2        /* device or host allocation failed             */
+#define BEMBEL_ECUDA 3         /* a CUDA call failed (message has the reason)  */
+#define BEMBEL_ENOTCONV 4      /* GMRES reached max_iter; x holds its iterate  */
+#define BEMBEL_ETIMEOUT 5      /* reserved: a bounded device wait expired      */
+#define BEMBEL_EUNSUPPORTED 6  /* valid request the library does not implement */
+
+/* ---- enumerations ---------------------------------------------------------- */
+enum bembel_geom_kind {
+  BEMBEL_GEOM_SPHERE6 = 0,          /* unit sphere, 6 cube-face patches gamma = c/|c| */
+  BEMBEL_GEOM_PERTURBED_SPHERE = 1  /* r(x) = 1 + amp * sum a_lm Y_lm(x), 1 <= l <= 4   */
+};
+enum bembel_op_kind {
+  BEMBEL_LAPLACE_SL = 0,   /* App. B (LS): G = 1/(4 pi r)                 */
+  BEMBEL_HELMHOLTZ_SL = 1, /* App. B (HS): G = exp(-i kappa r)/(4 pi r)    */
+  BEMBEL_MAXWELL_SL = 2    /* App. B (MS): not implemented (EUNSUPPORTED) */
+};
+enum bembel_precision {
+  BEMBEL_PREC_FP64 = 0,  /* everything in FP64                                       */
+  BEMBEL_PREC_MIXED = 1  /* FP64 assembly and residuals; FP32 inner solves/matvecs    */
+};
+enum bembel_rhs_kind {
+  BEMBEL_RHS_POINT_SOURCE = 0, /* g(x) = exp(-i kappa |x-x0|)/|x-x0| (kappa = 0: 1/|x-x0|); params: 3 per rhs */
+  BEMBEL_RHS_PLANE_WAVE = 1    /* g(x) = exp(-i kappa d.x); params: direction d, 3 per rhs */
+};
+enum bembel_precond_kind {
+  BEMBEL_PRECOND_NONE = 0,
+  BEMBEL_PRECOND_BLOCK_JACOBI = 1 /* inverse of the near-field diagonal leaf blocks */
+};
+
+typedef struct bembel_geom bembel_geom;
+typedef struct bembel_op bembel_op;
+
+/* Geometry description (App. D boundary representation; Sec. 4.1 allows
+ * arbitrary smooth parametric patch maps).  Host memory; copied by
+ * bembel_geom_create. */
+typedef struct {
+  int kind;              /* enum bembel_geom_kind                                    */
+  int n_coeffs;          /* PERTURBED_SPHERE: number of a_lm, must be 24 (l = 1..4)  */
+  const double* coeffs;  /* PERTURBED_SPHERE: a_lm ordered (l, m = -l..l), host ptr   */
+  double amplitude;      /* PERTURBED_SPHERE: amp (0.1 in the perturbed workload)     */
+} bembel_geom_desc;
+
+/* Assembly options.  Fill with bembel_opts_default, then override. */
+typedef struct {
+  double eta;        /* admissibility max(diam) <= eta * dist of the cluster balls (1.6)   */
+  int leaf_level;    /* quadtree leaf level; -1: max(0, level - 1)                           */
+  int g_regular;     /* Gauss points per direction on separated near-field pairs (4)         */
+  int g_singular;    /* Gauss points per variable of the Duffy rules (5)                     */
+  int precision;     /* enum bembel_precision (FP64)                                         */
+  void* stream;      /* cudaStream_t used by every call on the operator (NULL: default)      */
+} bembel_opts;
+
+/* Counters describing an assembled operator (host struct). */
+typedef struct {
+  int64_t ndofs;            /* global S^2 dofs                                  */
+  int64_t nlocal;           /* element-local dofs (elements * (d+1)^2)          */
+  int64_t nelements;
+  int64_t n_clusters;       /* clusters over all levels                         */
+  int64_t n_far_blocks;     /* ordered admissible cluster pairs                 */
+  int64_t n_near_blocks;    /* ordered non-admissible leaf cluster pairs        */
+  int64_t n_pairs_regular;  /* unordered separated near element pairs           */
+  int64_t n_pairs_identical;
+  int64_t n_pairs_edge;
+  int64_t n_pairs_vertex;
+  int64_t near_bytes;       /* FP64 near-field storage                          */
+  int64_t far_bytes;        /* FP64 coupling storage                            */
+  int leaf_level;
+  int q;
+  int degree;
+  int level;
+  double assemble_ms;       /* device time of the assembly kernels               */
+  double setup_ms;          /* host time of topology, trees and pair lists      */
+  /* device time per assembly phase (CUDA events on the operator's stream):
+   * 0 tabulation, 1 regular near field, 2 identical, 3 common edge,
+   * 4 common vertex, 5 coupling, 6 FP32 copies, 7 unused */
+  double phase_ms[8];
+} bembel_op_info;
+
+/* Solver options and report (Sec. 4.6: GMRES, restarted). */
+typedef struct {
+  double tol;         /* relative residual ||b - A x|| / ||b|| per column (1e-8) */
+  int restart;        /* Krylov dimension m (30)                                  */
+  int max_iter;       /* total Arnoldi steps per column (1000)                    */
+  int precond;        /* enum bembel_precond_kind (NONE)                          */
+  int refine;         /* MIXED operators: FP64 iterative refinement on/off (1)    */
+} bembel_solve_opts;
+
+typedef struct {
+  int iterations;        /* Arnoldi steps of the slowest column (inner steps summed over refinement) */
+  int refinements;       /* outer FP64 refinement steps (0 for FP64 solves)       */
+  double rel_residual;   /* largest final relative residual over columns (FP64)   */
+  double solve_ms;       /* host wall time of the call                            */
+} bembel_solve_info;
+
+/* Defaults: eta 1.6, leaf_level -1, g_regular 4, g_singular 5, FP64, stream NULL. */
+void bembel_opts_default(bembel_opts* o);
+/* Defaults: tol 1e-8, restart 30, max_iter 1000, NONE, refine 1. */
+void bembel_solve_opts_default(bembel_solve_opts* o);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* bembel_last_error(void);
+
+/* Number of CUDA kernel launches issued by this library since it was loaded
+ * (all threads).  Diagnostic counter for launch accounting; never fails. */
+int64_t bembel_kernel_launches(void);
+
+/* Create a geometry (App. D: patches with outward normals meeting at full
+ * edges or vertices; the matching condition holds for both kinds by
+ * construction).  desc and desc->coeffs are read during the call only.
+ * Errors: EINVAL (NULL pointers, unknown kind, wrong n_coeffs), ENOMEM. */
+int bembel_geom_create(const bembel_geom_desc* desc, bembel_geom** out);
+int bembel_geom_destroy(bembel_geom* g);
+
+/* Assemble the compressed single-layer Galerkin matrix (Sec. 2, Sec. 4.5).
+ *   op     enum bembel_op_kind; Laplace (LS) or Helmholtz (HS)
+ *   k_re, k_im  complex wavenumber kappa (Sec. 4.2); ignored for Laplace
+ *   level  refinement level L: 2^L x 2^L elements per patch (App. E)
+ *   p      ansatz degree d of S^2 (d = 0: piecewise constants), 0 <= d <= 2
+ *   q      interpolation points per direction per cluster; q = 0 assembles
+ *          the matrix densely (no admissible blocks); 1 <= q <= 8 otherwise
+ *   o      options (NULL: defaults); copied
+ * Builds the element topology, cluster tree and block tree on the host, then
+ * runs the tabulation, near-field (regular + singular) quadrature and
+ * coupling kernels.  The geometry must outlive the operator.
+ * Errors: EINVAL (bad sizes, 0 <= level <= 10 required), EUNSUPPORTED
+ * (Maxwell), ENOMEM, ECUDA. */
+int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q,
+                    const bembel_opts* o, bembel_op** out);
+int bembel_op_destroy(bembel_op* op);
+
+/* Number of global dofs (rows = cols of the Galerkin matrix, Sec. 4.5 rows()/cols()). */
+int bembel_ndofs(const bembel_op* op, int64_t* n);
+/* Fill *info with the operator's counters. */
+int bembel_op_info_get(const bembel_op* op, bembel_op_info* info);
+
+/* y = A x for nrhs columns (Sec. 4.5 "H * x"): gather to element-local
+ * coefficients, leaf moments, upward transfer, coupling, downward transfer,
+ * near field, scatter.  x_dev, y_dev: device, column-major ndofs x nrhs, real
+ * or interleaved complex per the operator; must not overlap.  Uses library
+ * scratch owned by the operator (grown on demand, so the first call with a
+ * larger nrhs allocates).  Precision: FP64 unless the operator is MIXED and
+ * fp32 != 0, in which case x and y are FP32 (float / interleaved complex
+ * float) and the FP32 copies of the near and coupling matrices are used.
+ * Errors: EINVAL (NULL, nrhs < 1), ENOMEM, ECUDA. */
+int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
+
+/* Load vectors b_i = int_Gamma g phi_i (Sec. 4.4) for nrhs data functions of
+ * the given kind (enum bembel_rhs_kind), with params (host, 3 doubles per rhs).
+ * b_dev: device, column-major ndofs x nrhs, FP64 (complex for Helmholtz).
+ * Tensor Gauss with g points per direction on every element (g <= 10).
+ * Errors: EINVAL, ECUDA. */
+int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, int g, void* b_dev);
+
+/* Solve A x = b for nrhs columns with restarted GMRES (Sec. 4.6), x0 = 0.
+ * b_dev, x_dev: device FP64 (complex for Helmholtz), column-major.  MIXED
+ * operators with refine = 1 run FP32 inner GMRES inside FP64 iterative
+ * refinement (residual r = b - A x in FP64 each outer step).  info may be NULL.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOTCONV (x holds the last iterate). */
+int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, const bembel_solve_opts* so,
+                 bembel_solve_info* info);
+
+/* Potential u(x) = sum_j rho_j int G(x, gamma(t)) phi_hat_j(t) dt (Sec. 4.7;
+ * (LS)/(HS)) at npts points.  pts_dev: device, npts x 3 row-major FP64;
+ * rho_dev: device ndofs x nrhs; out_dev: device npts x nrhs column-major
+ * (complex for Helmholtz).  Tensor Gauss with g points per direction per
+ * element (g <= 10); points should keep a distance of a few elements from Gamma.
+ * Errors: EINVAL, ECUDA. */
+int bembel_eval(const bembel_op* op, const double* pts_dev, int64_t npts, const void* rho_dev, int nrhs, int g,
+                void* out_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEMBEL_H */

@@ -1,0 +1,226 @@
+"""ctypes binding of the C ABI in include/bembel.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device
+vectors are torch CUDA tensors: a block of nrhs columns of length n is a
+contiguous tensor of shape (nrhs, n) (column-major n x nrhs in C terms), dtype
+float64 / complex128 (float32 / complex64 for the FP32 matvec).  There is no
+fallback: if libbembel.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbembel.so")
+
+BEMBEL_OK, BEMBEL_EINVAL, BEMBEL_ENOMEM, BEMBEL_ECUDA, BEMBEL_ENOTCONV, BEMBEL_ETIMEOUT, BEMBEL_EUNSUPPORTED = range(7)
+BEMBEL_GEOM_SPHERE6, BEMBEL_GEOM_PERTURBED_SPHERE = 0, 1
+BEMBEL_LAPLACE_SL, BEMBEL_HELMHOLTZ_SL, BEMBEL_MAXWELL_SL = 0, 1, 2
+BEMBEL_PREC_FP64, BEMBEL_PREC_MIXED = 0, 1
+BEMBEL_RHS_POINT_SOURCE, BEMBEL_RHS_PLANE_WAVE = 0, 1
+BEMBEL_PRECOND_NONE, BEMBEL_PRECOND_BLOCK_JACOBI = 0, 1
+
+EXPORTED = [
+    "bembel_opts_default", "bembel_solve_opts_default", "bembel_last_error", "bembel_geom_create",
+    "bembel_geom_destroy", "bembel_assemble", "bembel_op_destroy", "bembel_ndofs", "bembel_op_info_get",
+    "bembel_matvec", "bembel_rhs", "bembel_solve", "bembel_eval", "bembel_kernel_launches",
+]
+
+
+class BembelError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bembel error {code}: {msg}")
+        self.code = code
+
+
+class GeomDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_coeffs", C.c_int), ("coeffs", C.POINTER(C.c_double)),
+                ("amplitude", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("eta", C.c_double), ("leaf_level", C.c_int), ("g_regular", C.c_int), ("g_singular", C.c_int),
+                ("precision", C.c_int), ("stream", C.c_void_p)]
+
+
+class OpInfo(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "ndofs", "nlocal", "nelements", "n_clusters", "n_far_blocks", "n_near_blocks", "n_pairs_regular",
+        "n_pairs_identical", "n_pairs_edge", "n_pairs_vertex", "near_bytes", "far_bytes")] + [
+        ("leaf_level", C.c_int), ("q", C.c_int), ("degree", C.c_int), ("level", C.c_int),
+        ("assemble_ms", C.c_double), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 8)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int), ("precond", C.c_int),
+                ("refine", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double),
+                ("solve_ms", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libbembel.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with `python -m paper_1906_00785_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, dbl, ci = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    L.bembel_opts_default.argtypes = [C.POINTER(Opts)]
+    L.bembel_opts_default.restype = None
+    L.bembel_solve_opts_default.argtypes = [C.POINTER(SolveOpts)]
+    L.bembel_solve_opts_default.restype = None
+    L.bembel_last_error.argtypes = []
+    L.bembel_last_error.restype = C.c_char_p
+    L.bembel_kernel_launches.argtypes = []
+    L.bembel_kernel_launches.restype = i64
+    L.bembel_geom_create.argtypes = [C.POINTER(GeomDesc), C.POINTER(vp)]
+    L.bembel_geom_destroy.argtypes = [vp]
+    L.bembel_assemble.argtypes = [vp, ci, dbl, dbl, ci, ci, ci, C.POINTER(Opts), C.POINTER(vp)]
+    L.bembel_op_destroy.argtypes = [vp]
+    L.bembel_ndofs.argtypes = [vp, C.POINTER(i64)]
+    L.bembel_op_info_get.argtypes = [vp, C.POINTER(OpInfo)]
+    L.bembel_matvec.argtypes = [vp, vp, vp, ci, ci]
+    L.bembel_rhs.argtypes = [vp, ci, C.POINTER(dbl), ci, ci, vp]
+    L.bembel_solve.argtypes = [vp, vp, vp, ci, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]
+    L.bembel_eval.argtypes = [vp, vp, i64, vp, ci, ci, vp]
+    for n in EXPORTED:
+        if n not in ("bembel_opts_default", "bembel_solve_opts_default", "bembel_last_error",
+                     "bembel_kernel_launches"):
+            getattr(L, n).restype = ci
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow=()):
+    if rc != BEMBEL_OK and rc not in allow:
+        raise BembelError(rc, lib().bembel_last_error().decode())
+    return rc
+
+
+def _ptr(t) -> int:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+class Geometry:
+    """Owning wrapper of a bembel_geom handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bembel_geom_destroy(self.handle)
+            self.handle = None
+
+
+class Operator:
+    """Owning wrapper of a bembel_op handle (keeps its geometry alive)."""
+
+    def __init__(self, handle, geom: Geometry, op: int):
+        self.handle = handle
+        self.geom = geom
+        self.op = op
+
+    @property
+    def complex(self) -> bool:
+        return self.op == BEMBEL_HELMHOLTZ_SL
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bembel_op_destroy(self.handle)
+            self.handle = None
+
+
+def bembel_opts_default() -> Opts:
+    o = Opts()
+    lib().bembel_opts_default(C.byref(o))
+    return o
+
+
+def bembel_solve_opts_default() -> SolveOpts:
+    o = SolveOpts()
+    lib().bembel_solve_opts_default(C.byref(o))
+    return o
+
+
+def bembel_geom_create(kind: int = BEMBEL_GEOM_SPHERE6, coeffs=None, amplitude: float = 0.1) -> Geometry:
+    d = GeomDesc()
+    d.kind = kind
+    keep = None
+    if coeffs is not None:
+        keep = np.ascontiguousarray(coeffs, dtype=np.float64)
+        d.n_coeffs = keep.size
+        d.coeffs = keep.ctypes.data_as(C.POINTER(C.c_double))
+    d.amplitude = amplitude
+    h = C.c_void_p()
+    _check(lib().bembel_geom_create(C.byref(d), C.byref(h)))
+    return Geometry(h)
+
+
+def bembel_assemble(geom: Geometry, op: int, k: complex, level: int, p: int, q: int, opts: Opts | None = None,
+                    **overrides) -> Operator:
+    o = opts if opts is not None else bembel_opts_default()
+    for key, v in overrides.items():
+        setattr(o, key, v)
+    h = C.c_void_p()
+    k = complex(k)
+    _check(lib().bembel_assemble(geom.handle, op, k.real, k.imag, level, p, q, C.byref(o), C.byref(h)))
+    return Operator(h, geom, op)
+
+
+def bembel_ndofs(op: Operator) -> int:
+    n = C.c_int64()
+    _check(lib().bembel_ndofs(op.handle, C.byref(n)))
+    return n.value
+
+
+def bembel_op_info_get(op: Operator) -> dict:
+    inf = OpInfo()
+    _check(lib().bembel_op_info_get(op.handle, C.byref(inf)))
+    out = {f: getattr(inf, f) for f, _ in OpInfo._fields_}
+    out["phase_ms"] = list(inf.phase_ms)
+    return out
+
+
+def bembel_kernel_launches() -> int:
+    return int(lib().bembel_kernel_launches())
+
+
+def bembel_matvec(op: Operator, x, y, nrhs: int = 1, fp32: bool = False) -> None:
+    _check(lib().bembel_matvec(op.handle, _ptr(x), _ptr(y), nrhs, int(bool(fp32))))
+
+
+def bembel_rhs(op: Operator, kind: int, params, b, g: int = 6) -> None:
+    prm = np.ascontiguousarray(np.atleast_2d(params), dtype=np.float64)
+    _check(lib().bembel_rhs(op.handle, kind, prm.ctypes.data_as(C.POINTER(C.c_double)), prm.shape[0], g, _ptr(b)))
+
+
+def bembel_solve(op: Operator, b, x, nrhs: int = 1, solve_opts: SolveOpts | None = None, **overrides) -> dict:
+    so = solve_opts if solve_opts is not None else bembel_solve_opts_default()
+    for key, v in overrides.items():
+        setattr(so, key, v)
+    info = SolveInfo()
+    rc = _check(lib().bembel_solve(op.handle, _ptr(b), _ptr(x), nrhs, C.byref(so), C.byref(info)),
+                allow=(BEMBEL_ENOTCONV,))
+    out = {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+    out["converged"] = rc == BEMBEL_OK
+    return out
+
+
+def bembel_eval(op: Operator, pts, rho, out, nrhs: int = 1, g: int = 6) -> None:
+    _check(lib().bembel_eval(op.handle, _ptr(pts), pts.shape[0], _ptr(rho), nrhs, g, _ptr(out)))

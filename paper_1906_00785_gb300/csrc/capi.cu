@@ -1,0 +1,293 @@
+// capi.cu - extern "C" entry points declared in include/bembel.h.
+//
+// Every entry point catches the library's internal errors and turns them into
+// status codes plus a thread-local message; no exception crosses the ABI.
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "op.h"
+
+namespace bembel {
+
+namespace {
+thread_local std::string g_last_error;
+
+struct LibError : std::exception {
+  int code;
+  std::string msg;
+  LibError(int c, std::string m) : code(c), msg(std::move(m)) {}
+  const char* what() const noexcept override { return msg.c_str(); }
+};
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const LibError& e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return BEMBEL_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return BEMBEL_EINVAL;
+  }
+}
+
+void free_op(Op* o) {
+  if (!o) return;
+  void* ptrs[] = {o->d_far_ptr, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
+                  o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
+                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_nodes, o->d_scratch, o->d_bj};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto* p : o->d_pairs)
+    if (p) cudaFree(p);
+  delete o;
+}
+
+double factorial(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+}  // namespace
+
+void fail(int code, const std::string& msg) { throw LibError(code, msg); }
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? BEMBEL_ENOMEM : BEMBEL_ECUDA;
+    throw LibError(code, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+static std::atomic<long long> g_launches{0};
+
+void launched(const char* what) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  launched(what);
+}
+
+long long launches_total() { return g_launches.load(); }
+
+void* dev_alloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw LibError(BEMBEL_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+}  // namespace bembel
+
+using namespace bembel;
+
+extern "C" {
+
+void bembel_opts_default(bembel_opts* o) {
+  if (!o) return;
+  o->eta = 1.6;
+  o->leaf_level = -1;
+  o->g_regular = 4;
+  o->g_singular = 5;
+  o->precision = BEMBEL_PREC_FP64;
+  o->stream = nullptr;
+}
+
+void bembel_solve_opts_default(bembel_solve_opts* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->restart = 30;
+  o->max_iter = 1000;
+  o->precond = BEMBEL_PRECOND_NONE;
+  o->refine = 1;
+}
+
+const char* bembel_last_error(void) { return g_last_error.c_str(); }
+
+int64_t bembel_kernel_launches(void) { return launches_total(); }
+
+int bembel_geom_create(const bembel_geom_desc* desc, bembel_geom** out) {
+  return guarded([&] {
+    if (!desc || !out) fail(BEMBEL_EINVAL, "geom_create: NULL argument");
+    auto* g = new GeomHandle();
+    std::memset(&g->g, 0, sizeof(Geom));
+    if (desc->kind == BEMBEL_GEOM_SPHERE6) {
+      g->g.kind = kSphere6;
+    } else if (desc->kind == BEMBEL_GEOM_PERTURBED_SPHERE) {
+      if (desc->n_coeffs != 24 || !desc->coeffs) {
+        delete g;
+        fail(BEMBEL_EINVAL, "geom_create: perturbed sphere needs 24 coefficients (l = 1..4)");
+      }
+      g->g.kind = kPerturbedSphere;
+      for (int l = 1; l <= 4; ++l)
+        for (int m = -l; m <= l; ++m) {
+          const int idx = l * l - 1 + l + m;
+          const int am = m < 0 ? -m : m;
+          double nlm = std::sqrt((2 * l + 1) / (4 * M_PI) * factorial(l - am) / factorial(l + am));
+          if (m != 0) nlm *= std::sqrt(2.0);
+          g->g.w[idx] = desc->amplitude * desc->coeffs[idx] * nlm;
+        }
+    } else {
+      delete g;
+      fail(BEMBEL_EINVAL, "geom_create: unknown geometry kind");
+    }
+    *out = reinterpret_cast<bembel_geom*>(g);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_geom_destroy(bembel_geom* g) {
+  delete reinterpret_cast<GeomHandle*>(g);
+  return BEMBEL_OK;
+}
+
+int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q, const bembel_opts* o,
+                    bembel_op** out) {
+  Op* res = nullptr;
+  const int rc = guarded([&] {
+    if (!g || !out) fail(BEMBEL_EINVAL, "assemble: NULL argument");
+    if (op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE operator is not implemented");
+    if (op != BEMBEL_LAPLACE_SL && op != BEMBEL_HELMHOLTZ_SL) fail(BEMBEL_EINVAL, "assemble: unknown operator");
+    if (level < 0 || level > 10) fail(BEMBEL_EINVAL, "assemble: level must be in [0, 10]");
+    if (p < 0 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: degree p must be in [0, 2]");
+    if (q < 0 || q > kMaxQ) fail(BEMBEL_EINVAL, "assemble: q must be in [0, 8]");
+    bembel_opts opts;
+    bembel_opts_default(&opts);
+    if (o) opts = *o;
+    if (opts.g_regular < 1 || opts.g_regular > kMaxG || opts.g_singular < 1 || opts.g_singular > kMaxG)
+      fail(BEMBEL_EINVAL, "assemble: Gauss orders must be in [1, 10]");
+    if (opts.precision != BEMBEL_PREC_FP64 && opts.precision != BEMBEL_PREC_MIXED)
+      fail(BEMBEL_EINVAL, "assemble: unknown precision");
+    if (q > 0 && !(opts.eta > 0)) fail(BEMBEL_EINVAL, "assemble: eta must be positive");
+    res = new Op();
+    res->geom = reinterpret_cast<GeomHandle*>(g)->g;
+    res->op = op;
+    res->cplx = op == BEMBEL_HELMHOLTZ_SL;
+    res->kre = res->cplx ? k_re : 0.0;
+    res->kim = res->cplx ? k_im : 0.0;
+    res->L = level;
+    res->d = p;
+    res->q = q;
+    res->leaf = opts.leaf_level < 0 ? (level > 0 ? level - 1 : 0) : opts.leaf_level;
+    if (res->leaf > level) fail(BEMBEL_EINVAL, "assemble: leaf_level above level");
+    res->opts = opts;
+    res->g_reg = opts.g_regular;
+    res->g_sing = opts.g_singular;
+    res->stream = static_cast<cudaStream_t>(opts.stream);
+    int dev = 0;
+    cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    cudaEvent_t e0, e1;
+    cuda_check(cudaEventCreate(&e0), "event");
+    cuda_check(cudaEventCreate(&e1), "event");
+    const auto th0 = std::chrono::steady_clock::now();
+    build_structure(*res);
+    res->info.setup_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+    cuda_check(cudaEventRecord(e0, res->stream), "event record");
+    run_assembly_kernels(*res);
+    cuda_check(cudaEventRecord(e1, res->stream), "event record");
+    cuda_check(cudaEventSynchronize(e1), "assembly sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    res->info.assemble_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = reinterpret_cast<bembel_op*>(res);
+    return BEMBEL_OK;
+  });
+  if (rc != BEMBEL_OK && res) {
+    free_op(res);
+    if (out) *out = nullptr;
+  }
+  return rc;
+}
+
+int bembel_op_destroy(bembel_op* op) {
+  Op* o = reinterpret_cast<Op*>(op);
+  if (o) cudaStreamSynchronize(o->stream);
+  free_op(o);
+  return BEMBEL_OK;
+}
+
+int bembel_ndofs(const bembel_op* op, int64_t* n) {
+  return guarded([&] {
+    if (!op || !n) fail(BEMBEL_EINVAL, "ndofs: NULL argument");
+    *n = reinterpret_cast<const Op*>(op)->ndofs;
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_op_info_get(const bembel_op* op, bembel_op_info* info) {
+  return guarded([&] {
+    if (!op || !info) fail(BEMBEL_EINVAL, "op_info: NULL argument");
+    *info = reinterpret_cast<const Op*>(op)->info;
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32) {
+  return guarded([&] {
+    if (!op || !x_dev || !y_dev) fail(BEMBEL_EINVAL, "matvec: NULL argument");
+    if (nrhs < 1) fail(BEMBEL_EINVAL, "matvec: nrhs must be >= 1");
+    if (x_dev == y_dev) fail(BEMBEL_EINVAL, "matvec: x and y must not overlap");
+    const Op* o = reinterpret_cast<const Op*>(op);
+    matvec_device(*o, x_dev, y_dev, nrhs, fp32 != 0, o->stream);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, int g, void* b_dev) {
+  return guarded([&] {
+    if (!op || !params || !b_dev) fail(BEMBEL_EINVAL, "rhs: NULL argument");
+    if (nrhs < 1) fail(BEMBEL_EINVAL, "rhs: nrhs must be >= 1");
+    if (kind != BEMBEL_RHS_POINT_SOURCE && kind != BEMBEL_RHS_PLANE_WAVE) fail(BEMBEL_EINVAL, "rhs: unknown kind");
+    if (g < 1 || g > kMaxG) fail(BEMBEL_EINVAL, "rhs: g must be in [1, 10]");
+    rhs_device(*reinterpret_cast<const Op*>(op), kind, params, nrhs, g, b_dev);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, const bembel_solve_opts* so,
+                 bembel_solve_info* info) {
+  return guarded([&] {
+    if (!op || !b_dev || !x_dev) fail(BEMBEL_EINVAL, "solve: NULL argument");
+    if (nrhs < 1) fail(BEMBEL_EINVAL, "solve: nrhs must be >= 1");
+    bembel_solve_opts o;
+    bembel_solve_opts_default(&o);
+    if (so) o = *so;
+    if (o.restart < 1 || o.restart > 200 || o.max_iter < 1 || !(o.tol > 0))
+      fail(BEMBEL_EINVAL, "solve: restart in [1, 200], max_iter >= 1, tol > 0 required");
+    if (o.precond != BEMBEL_PRECOND_NONE) fail(BEMBEL_EUNSUPPORTED, "solve: preconditioner not implemented");
+    const int rc = solve_gmres(*reinterpret_cast<const Op*>(op), b_dev, x_dev, nrhs, o, info);
+    if (rc == BEMBEL_ENOTCONV) g_last_error = "solve: GMRES reached max_iter before the tolerance";
+    return rc;
+  });
+}
+
+int bembel_eval(const bembel_op* op, const double* pts_dev, int64_t npts, const void* rho_dev, int nrhs, int g,
+                void* out_dev) {
+  return guarded([&] {
+    if (!op || !pts_dev || !rho_dev || !out_dev) fail(BEMBEL_EINVAL, "eval: NULL argument");
+    if (npts < 1 || nrhs < 1) fail(BEMBEL_EINVAL, "eval: npts and nrhs must be >= 1");
+    if (npts > (1LL << 31) - 1 || nrhs > 65535) fail(BEMBEL_EINVAL, "eval: npts or nrhs too large");
+    if (g < 1 || g > kMaxG) fail(BEMBEL_EINVAL, "eval: g must be in [1, 10]");
+    eval_device(*reinterpret_cast<const Op*>(op), pts_dev, npts, rho_dev, nrhs, g, out_dev);
+    return BEMBEL_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// op.h - internal operator state of the single-layer BEM library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bembel.h"
+#include "common.cuh"
+
+namespace bembel {
+
+// One element pair of the near field.  e < f, or e == f for identical pairs.
+// code: bits 0-1 kind (0 regular, 1 identical, 2 edge, 3 vertex), bits 2-4
+// canonical map of e, bits 5-7 canonical map of f (see apply_cmap).
+// off1: offset of entry (row i of e, col j of f) = off1 + j * nld + i in the
+// near-field storage; off2 likewise for the mirrored block (row j of f, col i
+// of e) = off2 + i * nld + j, or -1 when the pair is its own mirror.
+struct PairRec {
+  int e, f;
+  int code, pad;
+  long long off1, off2;
+};
+
+enum PairKind { kRegular = 0, kIdentical = 1, kEdge = 2, kVertex = 3 };
+
+struct Op {
+  Geom geom{};
+  int op = 0;          // bembel_op_kind
+  bool cplx = false;   // Helmholtz
+  double kre = 0, kim = 0;
+  int L = 0, d = 0, q = 0, leaf = 0;
+  int nloc = 1, n1 = 1, nel1 = 1, q2 = 0;
+  int m = 1;           // elements per leaf side
+  int nld = 1;         // local dofs per leaf cluster (m*m*nloc)
+  int64_t nelem = 0, ndofs = 0, nlocal = 0, nleaf = 0;
+  double h = 1.0;      // element side in the parameter square
+  bembel_opts opts{};
+  cudaStream_t stream = nullptr;
+
+  // cluster tree (levels 0..leaf), global cluster id = lvl_off[l] + patch*4^l + morton
+  std::vector<int64_t> lvl_off;
+  int64_t nclusters = 0;
+
+  // far field: CSR over target cluster ids
+  int64_t nfar = 0;
+  long long* d_far_ptr = nullptr;  // nclusters + 1
+  int* d_far_src = nullptr;        // source cluster id per block
+  int* d_far_tgt = nullptr;        // target cluster id per block
+  double* d_K = nullptr;           // nfar * q2 * q2 (x2 complex), entry (a, b) at b*q2 + a
+  float* d_K32 = nullptr;
+
+  // near field: CSR over leaf clusters, blocks nld x nld, entry (i, j) at j*nld + i
+  int64_t nnear = 0;
+  long long* d_near_ptr = nullptr;  // nleaf + 1
+  int* d_near_col = nullptr;
+  double* d_N = nullptr;
+  float* d_N32 = nullptr;
+
+  // element-pair lists by kind
+  PairRec* d_pairs[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t npairs[4] = {0, 0, 0, 0};
+
+  // geometry-independent matrices
+  double* d_V = nullptr;   // nld x q2, entry (i, a) at i*q2 + a
+  double* d_T = nullptr;   // 4 x q2 x q2, child c entry (a', a) at c*q2*q2 + a'*q2 + a
+  float* d_V32 = nullptr;
+  float* d_T32 = nullptr;
+  double* d_ex = nullptr;  // 1-D Bezier extraction: (i*(d+1) + j)*(d+1) + k
+
+  // quadrature tabulation (A1)
+  int g_reg = 4, g_sing = 5;
+  double* d_Xq = nullptr;  // nelem * g_reg^2 * 3
+  double* d_BW = nullptr;  // g_reg^2 * nloc: w_p h^2 B_k(u_p)
+  double* d_gauss = nullptr;  // singular rule: g_sing nodes then weights
+  double* d_nodes = nullptr;  // nclusters * q2 * 3 cluster interpolation points
+
+  // matvec scratch (grown on demand), FP64 and FP32 views share the bytes
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+
+  // block-Jacobi preconditioner: inverses of the near-field diagonal blocks
+  double* d_bj = nullptr;
+
+  bembel_op_info info{};
+};
+
+struct GeomHandle {
+  Geom g;
+};
+
+// setup.cu
+void build_structure(Op& o);            // topology, trees, pairs, moments (host) + uploads
+// quad.cu
+void run_assembly_kernels(Op& o);       // tabulation, near field, coupling
+// h2mv.cu
+void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
+void ensure_scratch(Op& o, size_t bytes);
+// element-local layout: dof-major, nrhs (x2 complex) real columns contiguous
+void gather_to_local(const Op& o, const double* x, double* xl, int nrhs, cudaStream_t s);
+void scatter_to_global(const Op& o, const double* yl, double* y, int nrhs, cudaStream_t s);
+// solve.cu
+int solve_gmres(const Op& o, const void* b, void* x, int nrhs, const bembel_solve_opts& so, bembel_solve_info* info);
+void rhs_device(const Op& o, int kind, const double* params, int nrhs, int g, void* b);
+void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, int nrhs, int g, void* out);
+
+// error plumbing (capi.cu)
+struct Error {
+  int code;
+  std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+// check the launch that was just issued and count it
+void launched(const char* what);
+void* dev_alloc(size_t bytes);
+void dev_free(void* p);
+
+}  // namespace bembel

@@ -1,0 +1,421 @@
+// quad.cu - assembly kernels (FP64).
+//
+// A_ij = int int G(gamma(s), gamma(t)) phi_hat_i(s) phi_hat_j(t) ds dt on element
+// pairs (Sec. 2 conforming Galerkin scheme; App. E 2-form Piola lift, so no
+// surface measure appears), with
+//   Laplace   G = 1/(4 pi r)                 (App. B, LS)
+//   Helmholtz G = exp(-i kappa r)/(4 pi r)    (App. B, HS), kappa complex.
+// * k_tabulate: gamma at the tensor Gauss points of every element.
+// * k_near_regular: separated near-field pairs, tensor Gauss g x g per element.
+// * k_near_singular<KIND>: identical / common-edge / common-vertex pairs with the
+//   Duffy-type regularising transforms (Sec. 2, [SS97]): 8 / 6 / 4 sub-domains
+//   of g^4 Gauss points each, sub-domains and variables as described per KIND
+//   in duffy_point().
+// * k_coupling: far-field coupling K_ab = G(gamma(x_a^tau), gamma(x_b^sigma))
+//   at the cluster Chebyshev points (Sec. 2, interpolation on the unit square).
+#include "op.h"
+
+namespace bembel {
+
+namespace {
+
+constexpr int kWarps = 4;  // warps per block in the pair kernels
+
+__device__ __forceinline__ void kernel_value(bool cplx, double r2, double kre, double kim, double& gr, double& gi) {
+  const double rinv = rsqrt(r2);
+  if (!cplx) {
+    gr = rinv;
+    gi = 0.0;
+  } else {
+    // exp(-i kappa r) = exp(kim r) (cos(kre r) - i sin(kre r))
+    const double r = r2 * rinv;
+    double sn, cs;
+    sincos(kre * r, &sn, &cs);
+    const double a = (kim != 0.0 ? exp(kim * r) : 1.0) * rinv;
+    gr = a * cs;
+    gi = -a * sn;
+  }
+}
+
+__global__ void k_tabulate(Geom g, int L, int64_t nelem, int G, const double* __restrict__ gx, double h,
+                           double* __restrict__ Xq) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int G2 = G * G;
+  if (id >= nelem * G2) return;
+  const int64_t e = id / G2;
+  const int p = int(id % G2);
+  const int64_t per = int64_t(1) << (2 * L);
+  uint32_t i1, i2;
+  morton_decode(uint32_t(e % per), i1, i2);
+  double x[3];
+  gamma_eval(g, int(e / per), (i1 + gx[p % G]) * h, (i2 + gx[p / G]) * h, x);
+  Xq[id * 3 + 0] = x[0];
+  Xq[id * 3 + 1] = x[1];
+  Xq[id * 3 + 2] = x[2];
+}
+
+// Warp per separated pair: u_p[j] = sum_q G(x_p, y_q) BW[q][j] per point p of
+// e, then block[i][j] = sum_p BW[p][i] u_p[j] / (4 pi).
+template <int D, bool CPLX>
+__global__ void __launch_bounds__(32 * kWarps) k_near_regular(const PairRec* __restrict__ pairs, int64_t npairs,
+                                                              const double* __restrict__ Xq,
+                                                              const double* __restrict__ BWg, int G2, double kre,
+                                                              double kim, double* __restrict__ N, int nld) {
+  constexpr int NL = (D + 1) * (D + 1);
+  constexpr int C = CPLX ? 2 : 1;
+  extern __shared__ double sh[];
+  double* BW = sh;                                        // G2 * NL
+  double* ubuf = sh + G2 * NL + (threadIdx.x >> 5) * G2 * NL * C;  // per warp
+  for (int i = threadIdx.x; i < G2 * NL; i += blockDim.x) BW[i] = BWg[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int S = G2 <= 16 ? 2 : 1;      // lanes per point p
+  const int P = 32 / S;                // points handled per sweep
+  const int half = lane / P;
+  const int qlen = (G2 + S - 1) / S;
+  for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < npairs; w += (int64_t)gridDim.x * kWarps) {
+    const PairRec pr = pairs[w];
+    const double* xe = Xq + (int64_t)pr.e * G2 * 3;
+    const double* xf = Xq + (int64_t)pr.f * G2 * 3;
+    for (int p0 = 0; p0 < G2; p0 += P) {
+      const int p = p0 + (lane % P);
+      double ur[NL], ui[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) ur[j] = ui[j] = 0.0;
+      if (p < G2) {
+        const double x0 = xe[p * 3], x1 = xe[p * 3 + 1], x2 = xe[p * 3 + 2];
+        const int qb = half * qlen, qe = min(G2, qb + qlen);
+        for (int qq = qb; qq < qe; ++qq) {
+          const double d0 = x0 - xf[qq * 3], d1 = x1 - xf[qq * 3 + 1], d2 = x2 - xf[qq * 3 + 2];
+          double gr, gi;
+          kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+#pragma unroll
+          for (int j = 0; j < NL; ++j) {
+            ur[j] = fma(gr, BW[qq * NL + j], ur[j]);
+            if (CPLX) ui[j] = fma(gi, BW[qq * NL + j], ui[j]);
+          }
+        }
+      }
+      if (S == 2) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          ur[j] += __shfl_down_sync(0xffffffffu, ur[j], P);
+          if (CPLX) ui[j] += __shfl_down_sync(0xffffffffu, ui[j], P);
+        }
+      }
+      if (lane < P && p < G2) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          ubuf[(p * NL + j) * C] = ur[j];
+          if (CPLX) ubuf[(p * NL + j) * C + 1] = ui[j];
+        }
+      }
+    }
+    __syncwarp();
+    for (int ij = lane; ij < NL * NL; ij += 32) {
+      const int i = ij % NL, j = ij / NL;
+      double ar = 0.0, ai = 0.0;
+      for (int p = 0; p < G2; ++p) {
+        ar = fma(BW[p * NL + i], ubuf[(p * NL + j) * C], ar);
+        if (CPLX) ai = fma(BW[p * NL + i], ubuf[(p * NL + j) * C + 1], ai);
+      }
+      ar *= kInv4Pi;
+      ai *= kInv4Pi;
+      const long long o1 = pr.off1 + (long long)j * nld + i;
+      N[o1 * C] = ar;
+      if (CPLX) N[o1 * C + 1] = ai;
+      if (pr.off2 >= 0) {
+        const long long o2 = pr.off2 + (long long)i * nld + j;
+        N[o2 * C] = ar;
+        if (CPLX) N[o2 * C + 1] = ai;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Point of a Duffy rule in canonical position.  x = (x0, x1, x2, x3) are the
+// Gauss variables in [0,1]^4, sub the sub-domain.  Returns (s1, s2, t1, t2) and
+// the Jacobian factor.
+//  KIND 1 (identical): z = t - s in quadrant (sg1, sg2) = (+-1, +-1) from sub & 3,
+//     triangle sub >> 2: (a, b) = (xi, xi eta) or (xi eta, xi); |z| = (a, b);
+//     s_k = max(0, -z_k) + u_k (1 - |z_k|), t = s + z; Jacobian xi (1-a)(1-b).
+//  KIND 2 (common edge {s1 = 0} = {t1 = 0}): sign of z = t2 - s2 from sub / 3,
+//     pyramid c = sub % 3 puts xi on coordinate c of (s1, t1, |z|), the others
+//     xi eta1, xi eta2; s2 = max(0, -z) + u (1 - |z|); Jacobian xi^2 (1 - |z|).
+//  KIND 3 (common vertex s = t = 0): pyramid c = sub puts xi on coordinate c of
+//     (s1, s2, t1, t2), the others xi eta1..3; Jacobian xi^3.
+template <int KIND>
+__device__ __forceinline__ double duffy_point(int sub, double x0, double x1, double x2, double x3, double& s1,
+                                              double& s2, double& t1, double& t2) {
+  const double xi = x0;
+  if (KIND == kIdentical) {
+    const double a = (sub >> 2) == 0 ? xi : xi * x1;
+    const double b = (sub >> 2) == 0 ? xi * x1 : xi;
+    const double z1 = (sub & 1) ? -a : a;
+    const double z2 = (sub & 2) ? -b : b;
+    s1 = fmax(0.0, -z1) + x2 * (1.0 - a);
+    s2 = fmax(0.0, -z2) + x3 * (1.0 - b);
+    t1 = s1 + z1;
+    t2 = s2 + z2;
+    return xi * (1.0 - a) * (1.0 - b);
+  } else if (KIND == kEdge) {
+    // (s1, t1, |z|) = xi at position c, (xi eta1, xi eta2) in order elsewhere
+    const int c = sub % 3;
+    const double e1 = xi * x1, e2 = xi * x2;
+    s1 = c == 0 ? xi : e1;
+    t1 = c == 0 ? e1 : (c == 1 ? xi : e2);
+    const double az = c == 2 ? xi : e2;
+    const double z = (sub < 3) ? az : -az;
+    s2 = fmax(0.0, -z) + x3 * (1.0 - az);
+    t2 = s2 + z;
+    return xi * xi * (1.0 - az);
+  } else {
+    const double e1 = xi * x1, e2 = xi * x2, e3 = xi * x3;
+    s1 = sub == 0 ? xi : e1;
+    s2 = sub == 0 ? e1 : (sub == 1 ? xi : e2);
+    t1 = sub <= 1 ? e2 : (sub == 2 ? xi : e3);
+    t2 = sub <= 2 ? e3 : xi;
+    return xi * xi * xi;
+  }
+}
+
+// Warp per touching pair; lanes stride over the nsub * g^4 rule points and
+// accumulate the (D+1)^2 x (D+1)^2 block in registers, reduced over the warp.
+template <int D, bool CPLX, int KIND>
+__global__ void __launch_bounds__(32 * kWarps) k_near_singular(const PairRec* __restrict__ pairs, int64_t npairs,
+                                                               Geom geom, int L, int G,
+                                                               const double* __restrict__ gauss, double kre,
+                                                               double kim, double* __restrict__ N, int nld) {
+  constexpr int D1 = D + 1;
+  constexpr int NL = D1 * D1;
+  constexpr int C = CPLX ? 2 : 1;
+  constexpr int NSUB = KIND == kIdentical ? 8 : (KIND == kEdge ? 6 : 4);
+  __shared__ double gx[kMaxG], gw[kMaxG];
+  if (threadIdx.x < G) {
+    gx[threadIdx.x] = gauss[threadIdx.x];
+    gw[threadIdx.x] = gauss[G + threadIdx.x];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int G2 = G * G, G4 = G2 * G2;
+  const int npts = NSUB * G4;
+  const int64_t per = int64_t(1) << (2 * L);
+  const double h = ldexp(1.0, -L);
+  for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < npairs; w += (int64_t)gridDim.x * kWarps) {
+    const PairRec pr = pairs[w];
+    const int pe = int(pr.e / per), pf = int(pr.f / per);
+    uint32_t e1, e2, f1, f2;
+    morton_decode(uint32_t(pr.e % per), e1, e2);
+    morton_decode(uint32_t(pr.f % per), f1, f2);
+    const int ce = (pr.code >> 2) & 7, cf = (pr.code >> 5) & 7;
+    double ar[NL * NL], ai[NL * NL];
+#pragma unroll
+    for (int k = 0; k < NL * NL; ++k) ar[k] = ai[k] = 0.0;
+    for (int idx = lane; idx < npts; idx += 32) {
+      const int sub = idx / G4;
+      int rem = idx - sub * G4;
+      const int i0 = rem % G;
+      rem /= G;
+      const int i1 = rem % G;
+      rem /= G;
+      const int i2 = rem % G;
+      const int i3 = rem / G;
+      double s1, s2, t1, t2;
+      const double jac = duffy_point<KIND>(sub, gx[i0], gx[i1], gx[i2], gx[i3], s1, s2, t1, t2);
+      const double wt = jac * gw[i0] * gw[i1] * gw[i2] * gw[i3];
+      double ls1, ls2, lt1, lt2;
+      apply_cmap(ce, s1, s2, ls1, ls2);
+      apply_cmap(cf, t1, t2, lt1, lt2);
+      double x[3], y[3];
+      gamma_eval(geom, pe, (e1 + ls1) * h, (e2 + ls2) * h, x);
+      gamma_eval(geom, pf, (f1 + lt1) * h, (f2 + lt2) * h, y);
+      const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+      double gr, gi;
+      kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+      gr *= wt;
+      gi *= wt;
+      double bs1[D1], bs2[D1], bt1[D1], bt2[D1];
+      bernstein<D>(ls1, bs1);
+      bernstein<D>(ls2, bs2);
+      bernstein<D>(lt1, bt1);
+      bernstein<D>(lt2, bt2);
+#pragma unroll
+      for (int i = 0; i < NL; ++i) {
+        const double bi = bs1[i % D1] * bs2[i / D1];
+        const double wr = gr * bi, wi = gi * bi;
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const double bj = bt1[j % D1] * bt2[j / D1];
+          ar[i * NL + j] = fma(wr, bj, ar[i * NL + j]);
+          if (CPLX) ai[i * NL + j] = fma(wi, bj, ai[i * NL + j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NL * NL; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
+        if (CPLX) ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], o);
+      }
+    }
+    const double sc = kInv4Pi * h * h * h * h;
+#pragma unroll
+    for (int k = 0; k < NL * NL; ++k) {
+      if ((k & 31) != lane) continue;
+      const int i = k / NL, j = k % NL;
+      const long long o1 = pr.off1 + (long long)j * nld + i;
+      N[o1 * C] = ar[k] * sc;
+      if (CPLX) N[o1 * C + 1] = ai[k] * sc;
+      if (pr.off2 >= 0) {
+        const long long o2 = pr.off2 + (long long)i * nld + j;
+        N[o2 * C] = ar[k] * sc;
+        if (CPLX) N[o2 * C + 1] = ai[k] * sc;
+      }
+    }
+  }
+}
+
+// Thread per coupling entry: K[blk][b][a] = G(node_a(target), node_b(source)) / (4 pi).
+template <bool CPLX>
+__global__ void k_coupling(const int* __restrict__ tgt, const int* __restrict__ src, int64_t nfar,
+                           const double* __restrict__ nodes, int q2, double kre, double kim, double* __restrict__ K) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)q2 * q2;
+  if (id >= nfar * per) return;
+  const int64_t blk = id / per;
+  const int r = int(id % per);
+  const int b = r / q2, a = r % q2;
+  const double* xa = nodes + ((int64_t)tgt[blk] * q2 + a) * 3;
+  const double* xb = nodes + ((int64_t)src[blk] * q2 + b) * 3;
+  const double d0 = xa[0] - xb[0], d1 = xa[1] - xb[1], d2 = xa[2] - xb[2];
+  double gr, gi;
+  kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+  if (CPLX) {
+    K[id * 2] = gr * kInv4Pi;
+    K[id * 2 + 1] = gi * kInv4Pi;
+  } else {
+    K[id] = gr * kInv4Pi;
+  }
+}
+
+template <typename T>
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = float(a[i]);
+}
+
+int grid_for(int64_t work, int per_block) {
+  int64_t g = (work + per_block - 1) / per_block;
+  return int(std::min<int64_t>(std::max<int64_t>(g, 1), 1 << 30));
+}
+
+template <int D, bool CPLX>
+void launch_pairs(Op& o, cudaEvent_t* ev) {
+  const cudaStream_t s = o.stream;
+  const int G2 = o.g_reg * o.g_reg;
+  const int NL = (D + 1) * (D + 1);
+  const int threads = 32 * kWarps;
+  if (o.npairs[kRegular] > 0) {
+    const size_t shm = sizeof(double) * (G2 * NL + kWarps * G2 * NL * (CPLX ? 2 : 1));
+    if (shm > 48 * 1024)
+      cuda_check(cudaFuncSetAttribute(k_near_regular<D, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm)),
+                 "smem attr");
+    const int grid = int(std::min<int64_t>((o.npairs[kRegular] + kWarps - 1) / kWarps, 152 * 64));
+    k_near_regular<D, CPLX><<<grid, threads, shm, s>>>(o.d_pairs[kRegular], o.npairs[kRegular], o.d_Xq, o.d_BW,
+                                                       G2, o.kre, o.kim, o.d_N, o.nld);
+    launched("k_near_regular");
+  }
+  cuda_check(cudaEventRecord(ev[2], s), "event");
+  const double* gs = o.d_gauss + o.g_reg;
+  auto grid_of = [](int64_t n) { return int(std::min<int64_t>((n + kWarps - 1) / kWarps, 152 * 64)); };
+  if (o.npairs[kIdentical] > 0) {
+    k_near_singular<D, CPLX, kIdentical><<<grid_of(o.npairs[kIdentical]), threads, 0, s>>>(
+        o.d_pairs[kIdentical], o.npairs[kIdentical], o.geom, o.L, o.g_sing, gs, o.kre, o.kim, o.d_N, o.nld);
+    launched("k_near_singular identical");
+  }
+  cuda_check(cudaEventRecord(ev[3], s), "event");
+  if (o.npairs[kEdge] > 0) {
+    k_near_singular<D, CPLX, kEdge><<<grid_of(o.npairs[kEdge]), threads, 0, s>>>(
+        o.d_pairs[kEdge], o.npairs[kEdge], o.geom, o.L, o.g_sing, gs, o.kre, o.kim, o.d_N, o.nld);
+    launched("k_near_singular edge");
+  }
+  cuda_check(cudaEventRecord(ev[4], s), "event");
+  if (o.npairs[kVertex] > 0) {
+    k_near_singular<D, CPLX, kVertex><<<grid_of(o.npairs[kVertex]), threads, 0, s>>>(
+        o.d_pairs[kVertex], o.npairs[kVertex], o.geom, o.L, o.g_sing, gs, o.kre, o.kim, o.d_N, o.nld);
+    launched("k_near_singular vertex");
+  }
+  cuda_check(cudaEventRecord(ev[5], s), "event");
+}
+
+}  // namespace
+
+void run_assembly_kernels(Op& o) {
+  const cudaStream_t s = o.stream;
+  const int C = o.cplx ? 2 : 1;
+  // phase events: 0 tabulation, 1 regular, 2 identical, 3 edge, 4 vertex, 5 coupling, 6 FP32 copies
+  cudaEvent_t ev[8];
+  for (auto& e : ev) cuda_check(cudaEventCreate(&e), "event");
+  // outputs first, so that no allocation falls between the phase events
+  const int64_t nN = o.nnear * (int64_t)o.nld * o.nld * C;
+  const int64_t nK = o.nfar * (int64_t)o.q2 * o.q2;
+  o.d_Xq = static_cast<double*>(dev_alloc(sizeof(double) * o.nelem * o.g_reg * o.g_reg * 3));
+  o.d_N = static_cast<double*>(dev_alloc(sizeof(double) * std::max<int64_t>(nN, 1)));
+  if (nK > 0) o.d_K = static_cast<double*>(dev_alloc(sizeof(double) * nK * C));
+  if (o.opts.precision == BEMBEL_PREC_MIXED) {
+    o.d_N32 = static_cast<float*>(dev_alloc(sizeof(float) * std::max<int64_t>(nN, 1)));
+    if (nK > 0) o.d_K32 = static_cast<float*>(dev_alloc(sizeof(float) * nK * C));
+  }
+  cuda_check(cudaEventRecord(ev[0], s), "event");
+  // A1: tabulation of gamma at the regular Gauss points
+  {
+    const int64_t n = o.nelem * o.g_reg * o.g_reg;
+    k_tabulate<<<grid_for(n, 256), 256, 0, s>>>(o.geom, o.L, o.nelem, o.g_reg, o.d_gauss, o.h, o.d_Xq);
+    launched("k_tabulate");
+  }
+  cuda_check(cudaEventRecord(ev[1], s), "event");
+  // A4 + A5: near field
+  switch (o.d * 2 + (o.cplx ? 1 : 0)) {
+    case 0: launch_pairs<0, false>(o, ev); break;
+    case 1: launch_pairs<0, true>(o, ev); break;
+    case 2: launch_pairs<1, false>(o, ev); break;
+    case 3: launch_pairs<1, true>(o, ev); break;
+    case 4: launch_pairs<2, false>(o, ev); break;
+    default: launch_pairs<2, true>(o, ev); break;
+  }
+  // A6: coupling
+  if (o.nfar > 0) {
+    const int64_t n = nK;
+    if (o.cplx)
+      k_coupling<true><<<grid_for(n, 256), 256, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre,
+                                                        o.kim, o.d_K);
+    else
+      k_coupling<false><<<grid_for(n, 256), 256, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre,
+                                                         o.kim, o.d_K);
+    launched("k_coupling");
+  }
+  cuda_check(cudaEventRecord(ev[6], s), "event");
+  // FP32 copies for the mixed-precision inner solves
+  if (o.opts.precision == BEMBEL_PREC_MIXED) {
+    k_to_f32<float><<<1024, 256, 0, s>>>(o.d_N, o.d_N32, nN);
+    launched("k_to_f32");
+    if (o.nfar > 0) {
+      const int64_t n = nK * C;
+      k_to_f32<float><<<1024, 256, 0, s>>>(o.d_K, o.d_K32, n);
+      launched("k_to_f32");
+    }
+  }
+  cuda_check(cudaEventRecord(ev[7], s), "event");
+  cuda_check(cudaEventSynchronize(ev[7]), "assembly sync");
+  for (int i = 0; i < 7; ++i) {
+    float ms = 0.f;
+    cuda_check(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]), "event time");
+    o.info.phase_ms[i] = ms;
+  }
+  o.info.phase_ms[7] = 0.0;
+  for (auto& e : ev) cudaEventDestroy(e);
+}
+
+}  // namespace bembel

@@ -1,0 +1,276 @@
+// rhs_eval.cu - load vectors (Sec. 4.4) and potential evaluation (Sec. 4.7).
+//
+// Load vector: b_i = int_Gamma g phi_i = int_square g(gamma(s)) phi_hat_i(s) ds
+// (2-form Piola lift of App. E), tensor Gauss with g x g points per element,
+// accumulated per element in the Bernstein basis and mapped to the B-spline
+// dofs with the transposed Bezier extraction.
+// Potential: u(x) = sum_j rho_j int_square G(x, gamma(t)) phi_hat_j(t) dt with
+// G of (LS) / (HS); the density is gathered to the elements, its values at the
+// Gauss points (times weights) formed once, then a direct sum over all
+// element points per evaluation point.
+#include <vector>
+
+#include "op.h"
+
+namespace bembel {
+
+namespace {
+
+// b_loc[(e*nloc + k)*ncol + r*C + comp] = sum_p w_p h^2 B_k(u_p) g_r(gamma(s_p))
+template <int D, bool CPLX>
+__global__ void k_rhs_local(Geom geom, int L, int64_t nelem, int G, const double* __restrict__ gx,
+                            const double* __restrict__ gw, int kind, const double* __restrict__ params, int nrhs,
+                            double kre, double kim, double* __restrict__ bl) {
+  constexpr int D1 = D + 1, NL = D1 * D1;
+  const int C = CPLX ? 2 : 1;
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nelem * nrhs) return;
+  const int64_t e = id / nrhs;
+  const int r = int(id % nrhs);
+  const int64_t per = int64_t(1) << (2 * L);
+  const int patch = int(e / per);
+  uint32_t i1, i2;
+  morton_decode(uint32_t(e % per), i1, i2);
+  const double h = ldexp(1.0, -L);
+  const double p0 = params[3 * r], p1 = params[3 * r + 1], p2 = params[3 * r + 2];
+  double ar[NL], ai[NL];
+  for (int k = 0; k < NL; ++k) ar[k] = ai[k] = 0.0;
+  for (int b = 0; b < G; ++b)
+    for (int a = 0; a < G; ++a) {
+      double x[3];
+      gamma_eval(geom, patch, (i1 + gx[a]) * h, (i2 + gx[b]) * h, x);
+      double vr, vi;
+      if (kind == BEMBEL_RHS_POINT_SOURCE) {
+        const double d0 = x[0] - p0, d1 = x[1] - p1, d2 = x[2] - p2;
+        const double rr = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        if (CPLX) {
+          double sn, cs;
+          sincos(kre * rr, &sn, &cs);
+          const double am = exp(kim * rr) / rr;
+          vr = am * cs;
+          vi = -am * sn;
+        } else {
+          vr = 1.0 / rr;
+          vi = 0.0;
+        }
+      } else {
+        const double ph = p0 * x[0] + p1 * x[1] + p2 * x[2];
+        double sn, cs;
+        sincos(kre * ph, &sn, &cs);
+        const double am = exp(kim * ph);
+        vr = am * cs;
+        vi = -am * sn;
+      }
+      double b1[D1], b2[D1];
+      bernstein<D>(gx[a], b1);
+      bernstein<D>(gx[b], b2);
+      const double w = gw[a] * gw[b] * h * h;
+      for (int k = 0; k < NL; ++k) {
+        const double bk = w * b1[k % D1] * b2[k / D1];
+        ar[k] += bk * vr;
+        ai[k] += bk * vi;
+      }
+    }
+  const int ncol = nrhs * C;
+  for (int k = 0; k < NL; ++k) {
+    bl[(e * NL + k) * ncol + r * C] = ar[k];
+    if (CPLX) bl[(e * NL + k) * ncol + r * C + 1] = ai[k];
+  }
+}
+
+// rq[(e*G2 + p)*ncol + col] = w_p h^2 sum_k B_k(u_p) rho_loc[(e*nloc + k)*ncol + col]
+template <int D>
+__global__ void k_density_points(const double* __restrict__ rl, int64_t nelem, int G, const double* __restrict__ gx,
+                                 const double* __restrict__ gw, double h, int ncol, double* __restrict__ rq) {
+  constexpr int D1 = D + 1, NL = D1 * D1;
+  const int G2 = G * G;
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nelem * G2 * ncol) return;
+  const int col = int(id % ncol);
+  const int p = int((id / ncol) % G2);
+  const int64_t e = id / ((int64_t)ncol * G2);
+  double b1[D1], b2[D1];
+  bernstein<D>(gx[p % G], b1);
+  bernstein<D>(gx[p / G], b2);
+  double acc = 0.0;
+  for (int k = 0; k < NL; ++k) acc += b1[k % D1] * b2[k / D1] * rl[(e * NL + k) * ncol + col];
+  rq[id] = acc * gw[p % G] * gw[p / G] * h * h;
+}
+
+// Block per (evaluation point, rhs): u = sum over element points G(x, y) rq / (4 pi).
+template <bool CPLX>
+__global__ void k_potential(const double* __restrict__ pts, int64_t npts, const double* __restrict__ Y,
+                            const double* __restrict__ rq, int64_t nsrc, int nrhs, double kre, double kim,
+                            double* __restrict__ out) {
+  const int64_t ip = blockIdx.x;
+  const int r = blockIdx.y;
+  const int C = CPLX ? 2 : 1;
+  const int ncol = nrhs * C;
+  const double x0 = pts[ip * 3], x1 = pts[ip * 3 + 1], x2 = pts[ip * 3 + 2];
+  double sr = 0.0, si = 0.0;
+  for (int64_t k = threadIdx.x; k < nsrc; k += blockDim.x) {
+    const double d0 = x0 - Y[k * 3], d1 = x1 - Y[k * 3 + 1], d2 = x2 - Y[k * 3 + 2];
+    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const double rinv = rsqrt(r2);
+    const double rhr = rq[k * ncol + r * C];
+    if (CPLX) {
+      const double rhi = rq[k * ncol + r * C + 1];
+      const double rr = r2 * rinv;
+      double sn, cs;
+      sincos(kre * rr, &sn, &cs);
+      const double am = exp(kim * rr) * rinv;
+      const double gr = am * cs, gi = -am * sn;
+      sr += gr * rhr - gi * rhi;
+      si += gr * rhi + gi * rhr;
+    } else {
+      sr += rinv * rhr;
+    }
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sr;
+    red[1][threadIdx.x >> 5] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+    }
+    out[((int64_t)r * npts + ip) * C] = a * kInv4Pi;
+    if (CPLX) out[((int64_t)r * npts + ip) * C + 1] = b * kInv4Pi;
+  }
+}
+
+__global__ void k_tab_points(Geom g, int L, int64_t nelem, int G, const double* __restrict__ gx, double h,
+                             double* __restrict__ Y) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int G2 = G * G;
+  if (id >= nelem * G2) return;
+  const int64_t e = id / G2;
+  const int p = int(id % G2);
+  const int64_t per = int64_t(1) << (2 * L);
+  uint32_t i1, i2;
+  morton_decode(uint32_t(e % per), i1, i2);
+  gamma_eval(g, int(e / per), (i1 + gx[p % G]) * h, (i2 + gx[p / G]) * h, &Y[id * 3]);
+}
+
+void gauss_table(int G, double* d_buf, cudaStream_t s) {
+  // Gauss-Legendre nodes/weights on [0,1] by Newton on P_G, uploaded as [x..., w...]
+  std::vector<double> t(2 * G);
+  for (int i = 0; i < G; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (G + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= G; ++k) {
+        const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (G == 1) p0 = 1.0;
+      dp = G * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= G; ++k) {
+      const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (G == 1) p0 = 1.0;
+    dp = G * (z * p1 - p0) / (z * z - 1.0);
+    t[G - 1 - i] = 0.5 * (1.0 - z);
+    t[G + G - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+  cuda_check(cudaMemcpyAsync(d_buf, t.data(), sizeof(double) * 2 * G, cudaMemcpyHostToDevice, s), "gauss upload");
+  cuda_check(cudaStreamSynchronize(s), "gauss sync");
+}
+
+struct Buf {
+  void* p;
+  explicit Buf(size_t n) : p(dev_alloc(n)) {}
+  ~Buf() { dev_free(p); }
+};
+
+}  // namespace
+
+void rhs_device(const Op& o, int kind, const double* params, int nrhs, int G, void* b) {
+  const cudaStream_t s = o.stream;
+  const int C = o.cplx ? 2 : 1;
+  Buf gt(sizeof(double) * 2 * G), pr(sizeof(double) * 3 * nrhs), bl(sizeof(double) * o.nlocal * nrhs * C);
+  gauss_table(G, static_cast<double*>(gt.p), s);
+  cuda_check(cudaMemcpyAsync(pr.p, params, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, s), "params");
+  const double* gx = static_cast<double*>(gt.p);
+  const double* gw = gx + G;
+  const int64_t n = o.nelem * nrhs;
+  const int tb = 128;
+  const int grid = int((n + tb - 1) / tb);
+  double* blp = static_cast<double*>(bl.p);
+  const double* pp = static_cast<double*>(pr.p);
+#define BEMBEL_RHS(D, CP) \
+  k_rhs_local<D, CP><<<grid, tb, 0, s>>>(o.geom, o.L, o.nelem, G, gx, gw, kind, pp, nrhs, o.kre, o.kim, blp)
+  switch (o.d * 2 + (o.cplx ? 1 : 0)) {
+    case 0: BEMBEL_RHS(0, false); break;
+    case 1: BEMBEL_RHS(0, true); break;
+    case 2: BEMBEL_RHS(1, false); break;
+    case 3: BEMBEL_RHS(1, true); break;
+    case 4: BEMBEL_RHS(2, false); break;
+    default: BEMBEL_RHS(2, true); break;
+  }
+#undef BEMBEL_RHS
+  launched("k_rhs_local");
+  scatter_to_global(o, blp, static_cast<double*>(b), nrhs, s);
+  cuda_check(cudaStreamSynchronize(s), "rhs sync");
+}
+
+void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, int nrhs, int G, void* out) {
+  const cudaStream_t s = o.stream;
+  const int C = o.cplx ? 2 : 1;
+  const int ncol = nrhs * C;
+  const int G2 = G * G;
+  Buf gt(sizeof(double) * 2 * G), rl(sizeof(double) * o.nlocal * ncol), rq(sizeof(double) * o.nelem * G2 * ncol),
+      Y(sizeof(double) * o.nelem * G2 * 3);
+  gauss_table(G, static_cast<double*>(gt.p), s);
+  const double* gx = static_cast<double*>(gt.p);
+  const double* gw = gx + G;
+  gather_to_local(o, static_cast<const double*>(rho), static_cast<double*>(rl.p), nrhs, s);
+  const int64_t nq = o.nelem * G2;
+  k_tab_points<<<int((nq + 255) / 256), 256, 0, s>>>(o.geom, o.L, o.nelem, G, gx, o.h, static_cast<double*>(Y.p));
+  launched("kernel");
+  const int64_t nd = nq * ncol;
+  switch (o.d) {
+    case 0:
+      k_density_points<0><<<int((nd + 255) / 256), 256, 0, s>>>(static_cast<double*>(rl.p), o.nelem, G, gx, gw, o.h,
+                                                                 ncol, static_cast<double*>(rq.p));
+      launched("kernel");
+      break;
+    case 1:
+      k_density_points<1><<<int((nd + 255) / 256), 256, 0, s>>>(static_cast<double*>(rl.p), o.nelem, G, gx, gw, o.h,
+                                                                 ncol, static_cast<double*>(rq.p));
+      launched("kernel");
+      break;
+    default:
+      k_density_points<2><<<int((nd + 255) / 256), 256, 0, s>>>(static_cast<double*>(rl.p), o.nelem, G, gx, gw, o.h,
+                                                                 ncol, static_cast<double*>(rq.p));
+      launched("kernel");
+      break;
+  }
+  dim3 grid((unsigned)npts, (unsigned)nrhs);
+  if (o.cplx)
+    k_potential<true><<<grid, 256, 0, s>>>(pts, npts, static_cast<double*>(Y.p), static_cast<double*>(rq.p), nq,
+                                           nrhs, o.kre, o.kim, static_cast<double*>(out));
+  else
+    k_potential<false><<<grid, 256, 0, s>>>(pts, npts, static_cast<double*>(Y.p), static_cast<double*>(rq.p), nq,
+                                            nrhs, o.kre, o.kim, static_cast<double*>(out));
+  launched("eval kernels");
+  cuda_check(cudaStreamSynchronize(s), "eval sync");
+}
+
+}  // namespace bembel

@@ -1,0 +1,66 @@
+"""CPU checks of the C ABI library: it loads and exports every entry point
+include/bembel.h declares (no compute calls without a GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_1906_00785_gb300", "libbembel.so")
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(bembel_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    if not os.path.exists(LIB):
+        from paper_1906_00785_gb300 import build
+
+        build.build()
+    return LIB
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (bembel_\w+)", out))
+    declared = declared_functions()
+    assert declared, "no declarations found"
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_reports_errors(built_lib):
+    import ctypes
+
+    import paper_1906_00785_gb300 as bem
+
+    L = bem.lib()
+    for n in declared_functions():
+        assert hasattr(L, n)
+    # argument validation happens before any device work
+    o = bem.bembel_opts_default()
+    assert abs(o.eta - 1.6) < 1e-15 and o.leaf_level == -1
+    so = bem.bembel_solve_opts_default()
+    assert so.tol == 1e-8 and so.restart == 30
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_geom_create(kind=7)
+    assert ei.value.code == bem.BEMBEL_EINVAL
+    with pytest.raises(bem.BembelError):
+        bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=[1.0, 2.0])
+    g = bem.bembel_geom_create()
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_assemble(g, bem.BEMBEL_MAXWELL_SL, 4.0, 2, 2, 0)
+    assert ei.value.code == bem.BEMBEL_EUNSUPPORTED
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_assemble(g, bem.BEMBEL_LAPLACE_SL, 0.0, 2, 3, 0)
+    assert ei.value.code == bem.BEMBEL_EINVAL
+    assert L.bembel_ndofs(None, ctypes.byref(ctypes.c_int64())) == bem.BEMBEL_EINVAL

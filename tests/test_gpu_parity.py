@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (FP64 path, same quadrature rules and H^2 readings on both sides, so
+differences are rounding only): matrix entries 1e-12 relative to the largest
+entry; H^2 matvec rows 1e-12; solutions 1e-9 (solved to 1e-13 on the GPU,
+direct solve in the oracle; the condition numbers here are below 1e3).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1906_00785_gb300 as bem
+from inputs import ball_points, random_vector
+from oracle.galerkin import Assembler, potential, rhs
+from oracle.geometry import Sphere6
+from oracle.h2 import H2Oracle, block_tree
+from oracle.space import S2Space
+
+pytestmark = pytest.mark.gpu
+LAP, HEL = bem.BEMBEL_LAPLACE_SL, bem.BEMBEL_HELMHOLTZ_SL
+
+
+@pytest.fixture(scope="module")
+def geom():
+    return bem.bembel_geom_create(bem.BEMBEL_GEOM_SPHERE6)
+
+
+def gpu_matrix(op, n):
+    dt = torch.complex128 if op.complex else torch.float64
+    eye = torch.eye(n, dtype=dt, device="cuda")
+    out = torch.empty_like(eye)
+    bem.bembel_matvec(op, eye, out, n)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().T
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("L,d,op,k", [(2, 0, "laplace", 0.0), (2, 1, "laplace", 0.0), (1, 2, "laplace", 0.0),
+                                      (2, 1, "helmholtz", 2.0 + 0.3j), (0, 1, "laplace", 0.0)])
+def test_dense_matrix_parity(geom, L, d, op, k):
+    gop = bem.bembel_assemble(geom, LAP if op == "laplace" else HEL, k, L, d, 0, g_regular=4, g_singular=5)
+    sp = S2Space(Sphere6(), L, d)
+    A_ref = Assembler(sp, op, k, 4, 5).dense()
+    A = gpu_matrix(gop, sp.ndofs)
+    assert rel_err(A, A_ref) < 1e-12
+
+
+@pytest.mark.parametrize("L,d,q,op,k,leaf", [(3, 1, 4, "laplace", 0.0, 2), (3, 0, 3, "laplace", 0.0, 1),
+                                             (3, 2, 4, "helmholtz", 1.5, 2), (4, 0, 2, "laplace", 0.0, 3)])
+def test_h2_matrix_parity(geom, L, d, q, op, k, leaf):
+    gop = bem.bembel_assemble(geom, LAP if op == "laplace" else HEL, k, L, d, q, g_regular=3, g_singular=4,
+                              leaf_level=leaf, eta=1.6)
+    sp = S2Space(Sphere6(), L, d)
+    h2 = H2Oracle(sp, op, k, q=q, eta=1.6, leaf_level=leaf, g_reg=3, g_sing=4)
+    info = bem.bembel_op_info_get(gop)
+    assert info["n_far_blocks"] == len(h2.far) and info["n_near_blocks"] == len(h2.near)
+    assert info["n_far_blocks"] > 0
+    A = gpu_matrix(gop, sp.ndofs)
+    assert rel_err(A, h2.dense()) < 1e-12
+
+
+def test_block_counts_level6(geom):
+    """Far/near block counts of the level-6 workload (leaf level 5, eta 1.6)."""
+    far, near, _ = block_tree(Sphere6(), 5, 1.6)
+    gop = bem.bembel_assemble(geom, LAP, 0.0, 6, 1, 4, leaf_level=5)
+    info = bem.bembel_op_info_get(gop)
+    assert info["n_far_blocks"] == len(far) and info["n_near_blocks"] == len(near)
+    assert info["n_pairs_identical"] == 24576
+    assert info["n_pairs_edge"] == 98304 // 2 and info["n_pairs_vertex"] == 98280 // 2
+
+
+def test_h2_rows_full_size(geom):
+    """Sampled rows of A~ x at the full level-6, degree-1, q=4 workload."""
+    sp = S2Space(Sphere6(), 6, 1)
+    gop = bem.bembel_assemble(geom, LAP, 0.0, 6, 1, 4, leaf_level=5, g_regular=4, g_singular=5)
+    n = bem.bembel_ndofs(gop)
+    assert n == sp.ndofs == 25350
+    x = random_vector(n, 2)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    bem.bembel_matvec(gop, xt, y, 1)
+    y = y.cpu().numpy()
+    rows = np.random.default_rng(9).choice(n, 6, replace=False)
+    h2 = H2Oracle(sp, "laplace", q=4, eta=1.6, leaf_level=5, g_reg=4, g_sing=5)
+    ref = h2.apply_rows(x, rows)
+    np.testing.assert_allclose(y[rows], ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
+
+
+def test_multi_rhs_equals_columns(geom):
+    gop = bem.bembel_assemble(geom, HEL, 3.0, 3, 1, 4, leaf_level=2)
+    n = bem.bembel_ndofs(gop)
+    X = torch.from_numpy(random_vector(n, 4, nrhs=5, complex_=True).T.copy()).cuda()
+    Y = torch.empty_like(X)
+    bem.bembel_matvec(gop, X, Y, 5)
+    for r in range(5):
+        y1 = torch.empty_like(X[r])
+        bem.bembel_matvec(gop, X[r].contiguous(), y1, 1)
+        assert torch.max(torch.abs(y1 - Y[r])) <= 1e-13 * torch.max(torch.abs(Y[r]))
+
+
+def test_config1_dense_laplace_end_to_end(geom):
+    """Dense Laplace, level 3, degree 0: load vector, GMRES, potential."""
+    x0 = np.array([0.0, 0.0, 2.0])
+    sp = S2Space(Sphere6(), 3, 0)
+    gop = bem.bembel_assemble(geom, LAP, 0.0, 3, 0, 0, g_regular=4, g_singular=5)
+    n = bem.bembel_ndofs(gop)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    bem.bembel_rhs(gop, bem.BEMBEL_RHS_POINT_SOURCE, x0[None, :], b, g=6)
+    b_ref = rhs(sp, lambda x: 1.0 / np.linalg.norm(x - x0, axis=1), g=6)
+    np.testing.assert_allclose(b.cpu().numpy(), b_ref, rtol=1e-13, atol=1e-16)
+    A_ref = Assembler(sp, "laplace", 0.0, 4, 5).dense()
+    rho = torch.empty_like(b)
+    info = bem.bembel_solve(gop, b, rho, 1, tol=1e-13)
+    assert info["converged"] and info["rel_residual"] <= 1e-13
+    rho_ref = np.linalg.solve(A_ref, b_ref)
+    assert rel_err(rho.cpu().numpy(), rho_ref) < 1e-9
+    pts = ball_points(100, 0.5, 1)
+    u = torch.empty(100, dtype=torch.float64, device="cuda")
+    bem.bembel_eval(gop, torch.from_numpy(pts).cuda(), rho, u, 1, g=6)
+    u_ref = potential(sp, rho_ref, pts, "laplace", g=6)
+    np.testing.assert_allclose(u.cpu().numpy(), u_ref, rtol=1e-9)
+    exact = 1.0 / np.linalg.norm(pts - x0, axis=1)
+    assert np.max(np.abs(u.cpu().numpy() - exact) / exact) < 5e-4
+
+
+def test_helmholtz_solve_and_eval_parity(geom):
+    k = 2.0
+    src = np.array([0.1, -0.2, 0.15])
+    sp = S2Space(Sphere6(), 2, 1)
+    gop = bem.bembel_assemble(geom, HEL, k, 2, 1, 0)
+    n = bem.bembel_ndofs(gop)
+    b = torch.empty(n, dtype=torch.complex128, device="cuda")
+    bem.bembel_rhs(gop, bem.BEMBEL_RHS_POINT_SOURCE, src[None, :], b, g=6)
+    r = lambda x: np.linalg.norm(x - src, axis=1)  # noqa: E731
+    b_ref = rhs(sp, lambda x: np.exp(-1j * k * r(x)) / r(x), g=6, dtype=complex)
+    np.testing.assert_allclose(b.cpu().numpy(), b_ref, rtol=1e-12, atol=1e-15)
+    x = torch.empty_like(b)
+    info = bem.bembel_solve(gop, b, x, 1, tol=1e-13)
+    assert info["converged"]
+    A_ref = Assembler(sp, "helmholtz", k, 4, 5).dense()
+    x_ref = np.linalg.solve(A_ref, b_ref)
+    assert rel_err(x.cpu().numpy(), x_ref) < 1e-9
+    pts = np.array([[3.0, 0.0, 0.0], [0.0, -2.5, 1.0]])
+    u = torch.empty(2, dtype=torch.complex128, device="cuda")
+    bem.bembel_eval(gop, torch.from_numpy(pts).cuda(), x, u, 1, g=6)
+    np.testing.assert_allclose(u.cpu().numpy(), potential(sp, x_ref, pts, "helmholtz", k, g=6), rtol=1e-9)
+
+
+def test_plane_wave_rhs_batch(geom):
+    k = 2.0
+    sp = S2Space(Sphere6(), 2, 2)
+    gop = bem.bembel_assemble(geom, HEL, k, 2, 2, 0)
+    dirs = np.array([[0, 0, 1.0], [1.0, 0, 0], [0.6, 0.8, 0]])
+    b = torch.empty((3, sp.ndofs), dtype=torch.complex128, device="cuda")
+    bem.bembel_rhs(gop, bem.BEMBEL_RHS_PLANE_WAVE, dirs, b, g=5)
+    for r in range(3):
+        ref = rhs(sp, lambda x: np.exp(-1j * k * (x @ dirs[r])), g=5, dtype=complex)
+        np.testing.assert_allclose(b[r].cpu().numpy(), ref, rtol=1e-12, atol=1e-15)
+
+
+def test_mixed_precision_solution(geom):
+    gop64 = bem.bembel_assemble(geom, LAP, 0.0, 4, 1, 4)
+    gopmx = bem.bembel_assemble(geom, LAP, 0.0, 4, 1, 4, precision=bem.BEMBEL_PREC_MIXED)
+    n = bem.bembel_ndofs(gop64)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    bem.bembel_rhs(gop64, bem.BEMBEL_RHS_POINT_SOURCE, np.array([[0.0, 0.0, 2.0]]), b)
+    x64, xmx = torch.empty_like(b), torch.empty_like(b)
+    i64 = bem.bembel_solve(gop64, b, x64, 1, tol=1e-10)
+    imx = bem.bembel_solve(gopmx, b, xmx, 1, tol=1e-10)
+    assert i64["converged"] and imx["converged"] and imx["refinements"] >= 1
+    assert (torch.linalg.norm(xmx - x64) / torch.linalg.norm(x64)).item() < 1e-6
+
+
+def test_invalid_arguments(geom):
+    gop = bem.bembel_assemble(geom, LAP, 0.0, 1, 0, 0)
+    x = torch.zeros(24, dtype=torch.float64, device="cuda")
+    with pytest.raises(bem.BembelError):
+        bem.bembel_matvec(gop, x, x, 1)  # aliasing
+    with pytest.raises(bem.BembelError):
+        bem.bembel_matvec(gop, x, torch.empty_like(x), 0)
+    with pytest.raises(bem.BembelError):
+        bem.bembel_matvec(gop, x, torch.empty_like(x), 1, fp32=True)  # FP64 operator has no FP32 copy
+    out = bem.bembel_solve(gop, x, torch.empty_like(x), 1)  # zero right-hand side
+    assert out["converged"] and out["iterations"] == 0
