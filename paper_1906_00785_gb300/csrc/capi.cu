@@ -4,6 +4,8 @@
 // status codes plus a thread-local message; no exception crosses the ABI.
 #include <atomic>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <stdexcept>
@@ -68,10 +70,23 @@ void cuda_check(cudaError_t e, const char* what) {
 }
 
 static std::atomic<long long> g_launches{0};
+// BEMBEL_SYNC_DEBUG=1 synchronises after every launch and logs progress to stderr.
+static const bool g_sync_debug = std::getenv("BEMBEL_SYNC_DEBUG") != nullptr;
+
+void debug_mark(const char* what) {
+  if (g_sync_debug) {
+    std::fprintf(stderr, "[bembel] %s\n", what);
+    std::fflush(stderr);
+  }
+}
 
 void launched(const char* what) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  launched(what);
+  cuda_check(cudaGetLastError(), what);
+  if (g_sync_debug) {
+    debug_mark(what);
+    cuda_check(cudaDeviceSynchronize(), what);
+  }
 }
 
 long long launches_total() { return g_launches.load(); }
@@ -189,14 +204,18 @@ int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level,
     res->g_sing = opts.g_singular;
     res->stream = static_cast<cudaStream_t>(opts.stream);
     int dev = 0;
+    debug_mark("assemble: cudaGetDevice");
     cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     cudaEvent_t e0, e1;
+    debug_mark("assemble: events");
     cuda_check(cudaEventCreate(&e0), "event");
     cuda_check(cudaEventCreate(&e1), "event");
+    debug_mark("assemble: build_structure");
     const auto th0 = std::chrono::steady_clock::now();
     build_structure(*res);
     res->info.setup_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+    debug_mark("assemble: kernels");
     cuda_check(cudaEventRecord(e0, res->stream), "event record");
     run_assembly_kernels(*res);
     cuda_check(cudaEventRecord(e1, res->stream), "event record");

@@ -115,6 +115,8 @@ struct Error {
 void cuda_check(cudaError_t e, const char* what);
 // check the launch that was just issued and count it
 void launched(const char* what);
+// progress marker on stderr when BEMBEL_SYNC_DEBUG is set
+void debug_mark(const char* what);
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
 

@@ -187,6 +187,7 @@ void build_structure(Op& o) {
     }
   }
 
+  debug_mark("setup: cluster balls on levels 0..leaf");
   // ---- cluster balls on levels 0..leaf -----------------------------------------
   o.lvl_off.assign(o.leaf + 2, 0);
   for (int l = 0; l <= o.leaf; ++l) o.lvl_off[l + 1] = o.lvl_off[l] + 6 * (int64_t(1) << (2 * l));
@@ -214,6 +215,7 @@ void build_structure(Op& o) {
     }
   }
 
+  debug_mark("setup: block tree");
   // ---- block tree ------------------------------------------------------------------
   std::vector<std::pair<int, int>> far, near;  // global cluster ids (target, source)
   {
@@ -274,6 +276,7 @@ void build_structure(Op& o) {
   o.d_near_ptr = upload(nptr);
   o.d_near_col = upload(ncol);
 
+  debug_mark("setup: element pairs of the near field");
   // ---- element pairs of the near field --------------------------------------------
   auto block_index = [&](int64_t t, int64_t s) -> long long {
     const auto b = ncol.begin() + nptr[t], en = ncol.begin() + nptr[t + 1];
@@ -340,6 +343,7 @@ void build_structure(Op& o) {
     o.d_pairs[k] = upload(lists[k]);
   }
 
+  debug_mark("setup: Bezier extraction");
   // ---- Bezier extraction (1-D, per element index) ----------------------------------
   {
     const int n = d + 1;
@@ -358,6 +362,7 @@ void build_structure(Op& o) {
     o.d_ex = upload(ex);
   }
 
+  debug_mark("setup: moments and transfers");
   // ---- moments and transfers (geometry independent) --------------------------------
   if (o.q > 0) {
     const int q = o.q, q2 = o.q2;
@@ -422,6 +427,7 @@ void build_structure(Op& o) {
     o.d_nodes = upload(nodes);
   }
 
+  debug_mark("setup: quadrature tables");
   // ---- quadrature tables -------------------------------------------------------------
   {
     std::vector<double> gx, gw;
@@ -444,6 +450,7 @@ void build_structure(Op& o) {
     o.d_gauss = upload(rg);  // [g_reg nodes][g_sing nodes][g_sing weights]
   }
 
+  debug_mark("setup: report");
   // ---- report -------------------------------------------------------------------------
   bembel_op_info& in = o.info;
   in.ndofs = o.ndofs;
