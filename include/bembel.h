@@ -190,6 +190,36 @@ int bembel_op_info_get(const bembel_op* op, bembel_op_info* info);
  * Errors: EINVAL (NULL, nrhs < 1), ENOMEM, ECUDA. */
 int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
 
+/* y = A x like bembel_matvec, but without allocating anything.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc themselves or through us -- for example code whose device memory
+ * is owned by its own pool allocator (a framework's caching allocator that has
+ * reserved the free memory, so an outside cudaMalloc fails or fragments it),
+ * code on a latency-critical path that cannot afford the device-wide
+ * synchronisation cudaMalloc and cudaFree may imply, or code that must keep
+ * this library to a fixed, known memory footprint.  The operator (made by
+ * bembel_assemble) and the x and y buffers are still the caller's inputs and
+ * outputs, exactly as for bembel_matvec.
+ * Scratch: a fixed array of 8 MiB compiled into the library as device memory;
+ * every GPU that loads the library holds it until the process exits.  A
+ * product needs (2 * nlocal + 2 * n_clusters * q^2) * nrhs values (x2 for
+ * complex operators, 8 bytes each in FP64, 4 in FP32; counts from
+ * bembel_op_info_get); larger requests are rejected with BEMBEL_EINVAL and a
+ * message giving the size needed -- use bembel_matvec for them.  The level-6,
+ * degree-1, q = 4 Laplace operator needs 3.7 MB per right-hand side.
+ * The first call on each device looks up the array's device address (one
+ * cudaGetSymbolAddress with that device current) and caches it; make that
+ * first call before any stream capture.  Every call uses the same array and
+ * leaves its contents behind; each call writes every scratch value before
+ * reading it, so nothing carries over.  Calls that overlap on the GPU (on
+ * different streams, from different threads, or from different operators)
+ * race on the array and give wrong results: order them on one stream or
+ * synchronise between them.
+ * Arguments, layouts and the fp32 flag are those of bembel_matvec.
+ * Errors: EINVAL (NULL, nrhs < 1, aliasing, scratch too small, fp32 on an FP64
+ * operator), ECUDA. */
+int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
+
 /* Load vectors b_i = int_Gamma g phi_i (Sec. 4.4) for nrhs data functions of
  * the given kind (enum bembel_rhs_kind), with params (host, 3 doubles per rhs).
  * b_dev: device, column-major ndofs x nrhs, FP64 (complex for Helmholtz).

@@ -27,6 +27,7 @@ EXPORTED = [
     "bembel_opts_default", "bembel_solve_opts_default", "bembel_last_error", "bembel_geom_create",
     "bembel_geom_destroy", "bembel_assemble", "bembel_op_destroy", "bembel_ndofs", "bembel_op_info_get",
     "bembel_matvec", "bembel_rhs", "bembel_solve", "bembel_eval", "bembel_kernel_launches",
+    "bembel_matvec_noalloc",
 ]
 
 
@@ -91,6 +92,7 @@ def lib():
     L.bembel_ndofs.argtypes = [vp, C.POINTER(i64)]
     L.bembel_op_info_get.argtypes = [vp, C.POINTER(OpInfo)]
     L.bembel_matvec.argtypes = [vp, vp, vp, ci, ci]
+    L.bembel_matvec_noalloc.argtypes = [vp, vp, vp, ci, ci]
     L.bembel_rhs.argtypes = [vp, ci, C.POINTER(dbl), ci, ci, vp]
     L.bembel_solve.argtypes = [vp, vp, vp, ci, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]
     L.bembel_eval.argtypes = [vp, vp, i64, vp, ci, ci, vp]
@@ -203,6 +205,11 @@ def bembel_kernel_launches() -> int:
 
 def bembel_matvec(op: Operator, x, y, nrhs: int = 1, fp32: bool = False) -> None:
     _check(lib().bembel_matvec(op.handle, _ptr(x), _ptr(y), nrhs, int(bool(fp32))))
+
+
+def bembel_matvec_noalloc(op: Operator, x, y, nrhs: int = 1, fp32: bool = False) -> None:
+    """y = A x using the library's fixed device scratch (no allocation; see include/bembel.h)."""
+    _check(lib().bembel_matvec_noalloc(op.handle, _ptr(x), _ptr(y), nrhs, int(bool(fp32))))
 
 
 def bembel_rhs(op: Operator, kind: int, params, b, g: int = 6) -> None:

@@ -269,6 +269,17 @@ int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs,
   });
 }
 
+int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32) {
+  return guarded([&] {
+    if (!op || !x_dev || !y_dev) fail(BEMBEL_EINVAL, "matvec_noalloc: NULL argument");
+    if (nrhs < 1) fail(BEMBEL_EINVAL, "matvec_noalloc: nrhs must be >= 1");
+    if (x_dev == y_dev) fail(BEMBEL_EINVAL, "matvec_noalloc: x and y must not overlap");
+    const Op* o = reinterpret_cast<const Op*>(op);
+    matvec_noalloc(*o, x_dev, y_dev, nrhs, fp32 != 0, o->stream);
+    return BEMBEL_OK;
+  });
+}
+
 int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, int g, void* b_dev) {
   return guarded([&] {
     if (!op || !params || !b_dev) fail(BEMBEL_EINVAL, "rhs: NULL argument");

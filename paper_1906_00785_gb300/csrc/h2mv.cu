@@ -13,6 +13,9 @@
 // contiguous; real moment/transfer/extraction matrices act on complex vectors
 // as on pairs of real columns.  Instantiated for double (FP64 path) and float
 // (inner solves of the mixed-precision path).
+#include <mutex>
+#include <string>
+
 #include "op.h"
 
 namespace bembel {
@@ -217,11 +220,11 @@ __global__ void k_leaf_near(const long long* __restrict__ ptr, const int* __rest
 
 template <typename T>
 void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const T* K, const T* N, const T* V,
-                 const T* Tm) {
+                 const T* Tm, void* scratch) {
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
   const int q2 = o.q2;
-  T* base = static_cast<T*>(o.d_scratch);
+  T* base = static_cast<T*>(scratch);
   T* xl = base;
   T* yl = xl + o.nlocal * ncol;
   T* xh = yl + o.nlocal * ncol;
@@ -295,11 +298,59 @@ void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cud
   if (fp32) {
     if (!o.d_N32) fail(BEMBEL_EINVAL, "FP32 matvec needs an operator assembled with precision MIXED");
     matvec_impl<float>(o, static_cast<const float*>(x), static_cast<float*>(y), nrhs, s, o.d_K32, o.d_N32, o.d_V32,
-                       o.d_T32);
+                       o.d_T32, o.d_scratch);
   } else {
     matvec_impl<double>(o, static_cast<const double*>(x), static_cast<double*>(y), nrhs, s, o.d_K, o.d_N, o.d_V,
-                        o.d_T);
+                        o.d_T, o.d_scratch);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Matvec without allocation.  The scratch lives in this file-scope device
+// array instead of operator-owned cudaMalloc memory; every GPU that loads the
+// library holds it until the process exits.  Host code cannot use the array's
+// name as a device address, so its address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and cached.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+void* noalloc_scratch_address() {
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "matvec_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) fail(BEMBEL_EINVAL, "matvec_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "matvec_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  return g_noalloc_ptr[dev];
+}
+}  // namespace
+
+size_t matvec_noalloc_limit() { return kNoAllocScratchBytes; }
+
+void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s) {
+  const size_t need = matvec_scratch_bytes(o, nrhs, fp32);
+  if (need > kNoAllocScratchBytes)
+    fail(BEMBEL_EINVAL, "matvec_noalloc: this operator and nrhs need " + std::to_string(need) +
+                            " bytes of scratch; the fixed buffer holds " + std::to_string(kNoAllocScratchBytes) +
+                            " bytes (use bembel_matvec)");
+  if (fp32 && !o.d_N32) fail(BEMBEL_EINVAL, "FP32 matvec needs an operator assembled with precision MIXED");
+  // every scratch element is written before it is read, so nothing is cleared
+  void* scratch = noalloc_scratch_address();
+  if (fp32)
+    matvec_impl<float>(o, static_cast<const float*>(x), static_cast<float*>(y), nrhs, s, o.d_K32, o.d_N32, o.d_V32,
+                       o.d_T32, scratch);
+  else
+    matvec_impl<double>(o, static_cast<const double*>(x), static_cast<double*>(y), nrhs, s, o.d_K, o.d_N, o.d_V,
+                        o.d_T, scratch);
 }
 
 void ensure_scratch(Op& o, size_t bytes) {

@@ -98,6 +98,10 @@ void run_assembly_kernels(Op& o);       // tabulation, near field, coupling
 // h2mv.cu
 void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
 void ensure_scratch(Op& o, size_t bytes);
+size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32);
+// same product with the fixed file-scope scratch of h2mv.cu; allocates nothing
+void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
+size_t matvec_noalloc_limit();
 // element-local layout: dof-major, nrhs (x2 complex) real columns contiguous
 void gather_to_local(const Op& o, const double* x, double* xl, int nrhs, cudaStream_t s);
 void scatter_to_global(const Op& o, const double* yl, double* y, int nrhs, cudaStream_t s);
