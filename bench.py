@@ -225,7 +225,9 @@ def main():
         b = torch.empty(n, dtype=torch.float64, device=dev)
         bem.bembel_rhs(op, bem.BEMBEL_RHS_POINT_SOURCE, x0, b, g=6)
         rho = torch.empty_like(b)
-        info = bem.bembel_solve(op, b, rho, 1, tol=1e-8, restart=30, max_iter=1000)
+        info = bem.bembel_solve(op, b, rho, 1, tol=1e-8, restart=30, max_iter=1000,
+                                precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI if precision == bem.BEMBEL_PREC_MIXED
+                                else bem.BEMBEL_PRECOND_NONE)
         u = torch.empty(w["n_eval"], dtype=torch.float64, device=dev)
         bem.bembel_eval(op, pts if pts_dev is None else pts_dev, rho, u, 1, g=6)
         if out_host is not None:
@@ -297,7 +299,9 @@ def main():
     bem.bembel_solve(op64, b, x, 1, tol=1e-8)  # warm
     info64 = bem.bembel_solve(op64, b, x, 1, tol=1e-8)
     opmx = assemble(bem.BEMBEL_PREC_MIXED)
-    infomx = bem.bembel_solve(opmx, b, x, 1, tol=1e-8)
+    bem.bembel_solve(opmx, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)  # warm (builds D^-1)
+    infomx = bem.bembel_solve(opmx, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)
+    infomx_np = bem.bembel_solve(opmx, b, x, 1, tol=1e-8)
 
     def time_matvec(op, fp32, reps=20):
         dt = torch.float32 if fp32 else torch.float64
@@ -361,13 +365,14 @@ def main():
         "config": {"workload": "laplace_h2_sphere6_L6_p1_q4_eta1.6", "ndofs": n1, "nrhs": 1, "level": w["level"],
                    "degree": w["p"], "q": w["q"], "eta": w["eta"], "leaf_level": w["leaf"],
                    "g_regular": w["g_reg"], "g_singular": w["g_sing"], "precision": "mixed (FP64 quadrature, "
-                   "FP32 inner GMRES, FP64 refinement)", "l2": "working set > L2 (near+far FP64 storage "
+                   "FP32 inner GMRES with block-Jacobi, FP64 refinement)", "l2": "working set > L2 (near+far FP64 storage "
                    f"{matvec_bytes / 1e9:.2f} GB per step)", "parallelism": f"replicas x{world}"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
         "roofline": roofline, "cpu_baseline": cpu,
         "assembly_ms": opinfo["setup_ms"] + opinfo["assemble_ms"], "assembly_setup_ms": opinfo["setup_ms"],
         "assembly_kernels_ms": opinfo["assemble_ms"], "phase_ms": dict(zip(names, ph)),
-        "gmres": {"mixed_ms": infomx["solve_ms"], "mixed_iters": infomx["iterations"],
+        "gmres": {"mixed_bj_ms": infomx["solve_ms"], "mixed_bj_iters": infomx["iterations"],
+                  "mixed_noprec_ms": infomx_np["solve_ms"], "mixed_noprec_iters": infomx_np["iterations"],
                   "mixed_refinements": infomx["refinements"], "mixed_relres": infomx["rel_residual"],
                   "fp64_ms": info64["solve_ms"], "fp64_iters": info64["iterations"],
                   "fp64_relres": info64["rel_residual"], "speedup_vs_fp64": info64["solve_ms"] / infomx["solve_ms"]},

@@ -45,7 +45,8 @@ void free_op(Op* o) {
   if (!o) return;
   void* ptrs[] = {o->d_far_ptr, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
-                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_nodes, o->d_scratch, o->d_bj};
+                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_nodes, o->d_scratch, o->d_bj,
+                  o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* p : o->d_pairs)
@@ -80,7 +81,29 @@ void debug_mark(const char* what) {
   }
 }
 
+static thread_local bool t_capturing = false;
+static thread_local long long t_captured = 0;
+
+void capture_begin(cudaStream_t s) {
+  cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  t_capturing = true;
+  t_captured = 0;
+}
+
+long long capture_end(cudaStream_t s, cudaGraph_t* g) {
+  t_capturing = false;
+  cuda_check(cudaStreamEndCapture(s, g), "cudaStreamEndCapture");
+  return t_captured;
+}
+
+void note_graph_kernels(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void launched(const char* what) {
+  if (t_capturing) {  // counted when the graph is replayed
+    ++t_captured;
+    cuda_check(cudaGetLastError(), what);
+    return;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cuda_check(cudaGetLastError(), what);
   if (g_sync_debug) {
@@ -301,7 +324,8 @@ int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, 
     if (so) o = *so;
     if (o.restart < 1 || o.restart > 200 || o.max_iter < 1 || !(o.tol > 0))
       fail(BEMBEL_EINVAL, "solve: restart in [1, 200], max_iter >= 1, tol > 0 required");
-    if (o.precond != BEMBEL_PRECOND_NONE) fail(BEMBEL_EUNSUPPORTED, "solve: preconditioner not implemented");
+    if (o.precond != BEMBEL_PRECOND_NONE && o.precond != BEMBEL_PRECOND_BLOCK_JACOBI)
+      fail(BEMBEL_EINVAL, "solve: unknown preconditioner");
     const int rc = solve_gmres(*reinterpret_cast<const Op*>(op), b_dev, x_dev, nrhs, o, info);
     if (rc == BEMBEL_ENOTCONV) g_last_error = "solve: GMRES reached max_iter before the tolerance";
     return rc;

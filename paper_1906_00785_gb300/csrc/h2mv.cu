@@ -14,6 +14,7 @@
 // as on pairs of real columns.  Instantiated for double (FP64 path) and float
 // (inner solves of the mixed-precision path).
 #include <mutex>
+#include <type_traits>
 #include <string>
 
 #include "op.h"
@@ -21,6 +22,12 @@
 namespace bembel {
 
 namespace {
+
+template <typename K>
+void set_smem_limit(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)), "smem attr");
+}
 
 inline int blocks_for(int64_t n, int t) { return int(std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 30))); }
 
@@ -146,76 +153,394 @@ __global__ void k_down(T* __restrict__ yh_ch, const T* __restrict__ yh_par, cons
   yh_ch[id] = acc;
 }
 
-// yh[t][a][r] = sum over far blocks of t: K[blk][b][a] xh[s][b][r]  (complex r: 2 reals)
-template <typename T, bool CPLX>
-__global__ void k_coupling_mv(const long long* __restrict__ ptr, const int* __restrict__ src,
-                              const T* __restrict__ K, const T* __restrict__ xh, T* __restrict__ yh, int64_t nclus,
-                              int q2, int nrhs) {
+// Block-sparse product y[tgt(blk)] += M_blk x[src(blk)] over all blocks (bs x bs
+// blocks stored row-major, entry (a, b) at a*bs + b; vectors block-major
+// with nrhs (x2 complex) real columns contiguous).  With ONFLY the block is
+// not read from memory but evaluated in FP32 from the cluster interpolation
+// points: M_blk[a][b] = G(p[tgt][a], p[src][b]) / (4 pi).
+// Blocks are split in equal chunks over warps; a slot of SW lanes (the power of
+// two >= bs, at most 32) handles one block, one row a per lane (two for bs > 32).
+// Row sums stay in registers while consecutive blocks of a slot share a target
+// and are added to y with atomicAdd when it changes, so every block is read
+// exactly once with coalesced loads and every SM gets an equal share.
+template <typename T, bool CPLX, bool ONFLY, int RT>
+__global__ void __launch_bounds__(256) k_bsr_mv(const int* __restrict__ tgt, const int* __restrict__ src,
+                                                int64_t nblk, const T* __restrict__ M, const float* __restrict__ pts,
+                                                float kre, float kim, const T* __restrict__ x, T* __restrict__ y,
+                                                int bs, int nrhs, int chunk) {
   const int C = CPLX ? 2 : 1;
   const int ncol = nrhs * C;
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= nclus * q2 * nrhs) return;
-  const int r = int(id % nrhs);
-  const int a = int((id / nrhs) % q2);
-  const int64_t t = id / ((int64_t)nrhs * q2);
-  T ar = 0, ai = 0;
-  for (long long blk = ptr[t]; blk < ptr[t + 1]; ++blk) {
-    const T* Kb = K + (blk * q2 * q2) * C;
-    const T* x = xh + ((int64_t)src[blk] * q2) * ncol + r * C;
-    for (int b = 0; b < q2; ++b) {
-      if (CPLX) {
-        const T kr = Kb[(b * q2 + a) * 2], ki = Kb[(b * q2 + a) * 2 + 1];
-        const T xr = x[(int64_t)b * ncol], xi = x[(int64_t)b * ncol + 1];
-        ar = fma(kr, xr, fma(-ki, xi, ar));
-        ai = fma(kr, xi, fma(ki, xr, ai));
-      } else {
-        ar = fma(Kb[b * q2 + a], x[(int64_t)b * ncol], ar);
+  const int lane = threadIdx.x & 31;
+  const int SW = bs <= 1 ? 1 : (bs <= 2 ? 2 : (bs <= 4 ? 4 : (bs <= 8 ? 8 : (bs <= 16 ? 16 : 32))));
+  const int nslot = 32 / SW;
+  const int slot = lane / SW, sl = lane % SW;
+  const int rows = (bs + SW - 1) / SW;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t b0 = warp * chunk;
+  if (b0 >= nblk) return;
+  const int64_t b1 = min(nblk, b0 + chunk);
+  const int64_t bs2 = (int64_t)bs * bs;
+  for (int r0 = 0; r0 < nrhs; r0 += RT) {
+    const int nr = min(RT, nrhs - r0);
+    for (int ri = 0; ri < rows; ++ri) {
+      const int a = sl + ri * SW;
+      if (a >= bs) continue;
+      T ar[RT], ai[RT];
+#pragma unroll
+      for (int k = 0; k < RT; ++k) ar[k] = ai[k] = T(0);
+      int cur = -1;
+      for (int64_t blk = b0 + slot; blk < b1; blk += nslot) {
+        const int t = tgt[blk];
+        if (t != cur) {
+          if (cur >= 0) {
+            T* yo = y + ((int64_t)cur * bs + a) * ncol + r0 * C;
+#pragma unroll
+            for (int k = 0; k < RT; ++k)
+              if (k < nr) {
+                atomicAdd(yo + k * C, ar[k]);
+                if (CPLX) atomicAdd(yo + k * C + 1, ai[k]);
+                ar[k] = ai[k] = T(0);
+              }
+          }
+          cur = t;
+        }
+        const int sidx = src[blk];
+        const T* xs = x + ((int64_t)sidx * bs) * ncol + r0 * C;
+        float pa0 = 0.f, pa1 = 0.f, pa2 = 0.f;
+        if (ONFLY) {
+          const float* pa = pts + ((int64_t)t * bs + a) * 4;
+          pa0 = pa[0];
+          pa1 = pa[1];
+          pa2 = pa[2];
+        }
+        for (int bb = 0; bb < bs; ++bb) {
+          T mr, mi = T(0);
+          if (ONFLY) {
+            const float* pb = pts + ((int64_t)sidx * bs + bb) * 4;
+            const float d0 = pa0 - pb[0], d1 = pa1 - pb[1], d2 = pa2 - pb[2];
+            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+            const float rinv = rsqrtf(r2) * float(kInv4Pi);
+            if (CPLX) {
+              const float rr = r2 * rsqrtf(r2);
+              float sn, cs;
+              sincosf(kre * rr, &sn, &cs);
+              const float am = (kim != 0.f ? expf(kim * rr) : 1.f) * rinv;
+              mr = T(am * cs);
+              mi = T(-am * sn);
+            } else {
+              mr = T(rinv);
+            }
+          } else {
+            const T* mp = M + (blk * bs2 + (int64_t)a * bs + bb) * C;
+            mr = mp[0];
+            if (CPLX) mi = mp[1];
+          }
+          const T* xb = xs + (int64_t)bb * ncol;
+#pragma unroll
+          for (int k = 0; k < RT; ++k)
+            if (k < nr) {
+              if (CPLX) {
+                const T xr = xb[k * 2], xi = xb[k * 2 + 1];
+                ar[k] = fma(mr, xr, fma(-mi, xi, ar[k]));
+                ai[k] = fma(mr, xi, fma(mi, xr, ai[k]));
+              } else {
+                ar[k] = fma(mr, xb[k], ar[k]);
+              }
+            }
+        }
+      }
+      if (cur >= 0) {
+        T* yo = y + ((int64_t)cur * bs + a) * ncol + r0 * C;
+#pragma unroll
+        for (int k = 0; k < RT; ++k)
+          if (k < nr) {
+            atomicAdd(yo + k * C, ar[k]);
+            if (CPLX) atomicAdd(yo + k * C + 1, ai[k]);
+          }
       }
     }
   }
-  T* y = yh + (t * q2 + a) * ncol + r * C;
-  y[0] = ar;
-  if (CPLX) y[1] = ai;
 }
 
-// y_loc[t*nld + i][r] = sum_a V[i][a] yh[t][a][r] + sum_near N[blk][j][i] x_loc[s*nld + j][r]
-template <typename T, bool CPLX>
-__global__ void k_leaf_near(const long long* __restrict__ ptr, const int* __restrict__ col,
-                            const T* __restrict__ N, const T* __restrict__ xl, const T* __restrict__ V,
-                            const T* __restrict__ yh, T* __restrict__ yl, int64_t nleaf, int nld, int q2, int nrhs) {
-  const int C = CPLX ? 2 : 1;
-  const int ncol = nrhs * C;
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= nleaf * nld * nrhs) return;
-  const int r = int(id % nrhs);
-  const int i = int((id / nrhs) % nld);
-  const int64_t t = id / ((int64_t)nrhs * nld);
-  T ar = 0, ai = 0;
-  if (q2 > 0) {
-    const T* y = yh + (t * q2) * ncol + r * C;
-    for (int a = 0; a < q2; ++a) {
-      const T v = V[i * q2 + a];
-      ar = fma(v, y[(int64_t)a * ncol], ar);
-      if (CPLX) ai = fma(v, y[(int64_t)a * ncol + 1], ai);
-    }
-  }
-  for (long long blk = ptr[t]; blk < ptr[t + 1]; ++blk) {
-    const T* Nb = N + (blk * nld * nld) * C;
-    const T* x = xl + ((int64_t)col[blk] * nld) * ncol + r * C;
-    for (int j = 0; j < nld; ++j) {
-      if (CPLX) {
-        const T nr = Nb[(j * nld + i) * 2], ni = Nb[(j * nld + i) * 2 + 1];
-        const T xr = x[(int64_t)j * ncol], xi = x[(int64_t)j * ncol + 1];
-        ar = fma(nr, xr, fma(-ni, xi, ar));
-        ai = fma(nr, xi, fma(ni, xr, ai));
+// Single right-hand side form of k_bsr_mv: a lane reads its whole block row
+// with 16-byte vector loads (row-major blocks), and the source vector segment
+// (or the source points when ONFLY) with broadcast vector loads.
+template <typename T, bool CPLX, bool ONFLY>
+__global__ void __launch_bounds__(256) k_bsr_mv1(const int* __restrict__ tgt, const int* __restrict__ src,
+                                                 int64_t nblk, const T* __restrict__ M,
+                                                 const float4* __restrict__ pts, float kre, float kim,
+                                                 const T* __restrict__ x, T* __restrict__ y, int bs, int chunk) {
+  constexpr int C = CPLX ? 2 : 1;
+  constexpr int V = 16 / sizeof(T);  // scalars per 16-byte load
+  using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int lane = threadIdx.x & 31;
+  const int SW = bs <= 4 ? 4 : (bs <= 8 ? 8 : (bs <= 16 ? 16 : 32));
+  const int nslot = 32 / SW;
+  const int slot = lane / SW, sl = lane % SW;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t b0 = warp * chunk;
+  if (b0 >= nblk) return;
+  const int64_t b1 = min(nblk, b0 + chunk);
+  const int rowlen = bs * C;  // scalars per block row
+  const int nvec = rowlen / V;
+  for (int a = sl; a < bs; a += SW) {
+    T ar = T(0), ai = T(0);
+    int cur = -1;
+    for (int64_t blk = b0 + slot; blk < b1; blk += nslot) {
+      const int t = tgt[blk];
+      if (t != cur) {
+        if (cur >= 0) {
+          atomicAdd(y + ((int64_t)cur * bs + a) * C, ar);
+          if (CPLX) atomicAdd(y + ((int64_t)cur * bs + a) * C + 1, ai);
+          ar = ai = T(0);
+        }
+        cur = t;
+      }
+      const int sidx = src[blk];
+      const VT* xv = reinterpret_cast<const VT*>(x + (int64_t)sidx * rowlen);
+      if (!ONFLY) {
+        const VT* mv = reinterpret_cast<const VT*>(M + ((int64_t)blk * bs + a) * rowlen);
+#pragma unroll 4
+        for (int k = 0; k < nvec; ++k) {
+          const VT m4 = mv[k], x4 = xv[k];
+          const T* mm = reinterpret_cast<const T*>(&m4);
+          const T* xx = reinterpret_cast<const T*>(&x4);
+#pragma unroll
+          for (int u = 0; u < V; u += C) {
+            if (CPLX) {
+              ar = fma(mm[u], xx[u], fma(-mm[u + 1], xx[u + 1], ar));
+              ai = fma(mm[u], xx[u + 1], fma(mm[u + 1], xx[u], ai));
+            } else {
+              ar = fma(mm[u], xx[u], ar);
+            }
+          }
+        }
       } else {
-        ar = fma(Nb[j * nld + i], x[(int64_t)j * ncol], ar);
+        const float4 pa = pts[(int64_t)t * bs + a];
+        const float4* pb = pts + (int64_t)sidx * bs;
+#pragma unroll 4
+        for (int k = 0; k < nvec; ++k) {
+          const VT x4 = xv[k];
+          const T* xx = reinterpret_cast<const T*>(&x4);
+#pragma unroll
+          for (int u = 0; u < V; u += C) {
+            const float4 p = pb[(k * V + u) / C];
+            const float d0 = pa.x - p.x, d1 = pa.y - p.y, d2 = pa.z - p.z;
+            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+            const float rinv = rsqrtf(r2) * float(kInv4Pi);
+            if (CPLX) {
+              const float rr = r2 * rsqrtf(r2);
+              float sn, cs;
+              __sincosf(kre * rr, &sn, &cs);
+              const float am = (kim != 0.f ? __expf(kim * rr) : 1.f) * rinv;
+              const float mr = am * cs, mi = -am * sn;
+              ar = fma(T(mr), xx[u], fma(T(-mi), xx[u + 1], ar));
+              ai = fma(T(mr), xx[u + 1], fma(T(mi), xx[u], ai));
+            } else {
+              ar = fma(T(rinv), xx[u], ar);
+            }
+          }
+        }
       }
     }
+    if (cur >= 0) {
+      atomicAdd(y + ((int64_t)cur * bs + a) * C, ar);
+      if (CPLX) atomicAdd(y + ((int64_t)cur * bs + a) * C + 1, ai);
+    }
   }
-  T* y = yl + (t * nld + i) * ncol + r * C;
-  y[0] = ar;
-  if (CPLX) y[1] = ai;
+}
+
+// y_loc[t*nld + i][col] = sum_a V[i][a] yh_leaf[t][a][col]  (real V, any columns)
+template <typename T>
+__global__ void k_leaf_down(const T* __restrict__ yh, const T* __restrict__ V, T* __restrict__ yl, int64_t nleaf,
+                            int nld, int q2, int ncol) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Vs = reinterpret_cast<T*>(smem_raw);
+  for (int i = threadIdx.x; i < nld * q2; i += blockDim.x) Vs[i] = V[i];
+  __syncthreads();
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nleaf * nld * ncol) return;
+  const int col = int(id % ncol);
+  const int i = int((id / ncol) % nld);
+  const int64_t t = id / ((int64_t)ncol * nld);
+  const T* yt = yh + (t * q2) * ncol + col;
+  T acc = 0;
+  for (int a = 0; a < q2; ++a) acc = fma(Vs[i * q2 + a], yt[(int64_t)a * ncol], acc);
+  yl[id] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Fused transfer passes.  Levels ls = max(0, leaf - 2) .. leaf are handled per
+// subtree (one thread block per level-ls cluster, the subtree's values kept in
+// shared memory); levels below ls by one single-block kernel.
+// ---------------------------------------------------------------------------
+struct LevelOffsets {
+  long long off[16];
+};
+
+// Up: leaf moments xh_leaf = V^T x_loc and transfers up to level ls, one block
+// per level-ls cluster P; writes xh on every level of the subtree.
+template <typename T>
+__global__ void k_up_subtree(const T* __restrict__ xl, T* __restrict__ xh, const T* __restrict__ V,
+                             const T* __restrict__ Tm, LevelOffsets lo, int leaf, int ls, int q2, int nld, int ncol) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Vs = reinterpret_cast<T*>(smem_raw);
+  T* Ts = Vs + nld * q2;
+  T* bufA = Ts + 4 * q2 * q2;
+  const int D = leaf - ls;
+  const int nsub = 1 << (2 * D);
+  T* bufB = bufA + nsub * q2 * ncol;
+  for (int i = threadIdx.x; i < nld * q2; i += blockDim.x) Vs[i] = V[i];
+  for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
+  __syncthreads();
+  const int64_t P = blockIdx.x;
+  const int per = q2 * ncol;
+  for (int idx = threadIdx.x; idx < nsub * per; idx += blockDim.x) {
+    const int col = idx % ncol, a = (idx / ncol) % q2, li = idx / per;
+    const int64_t leafid = P * nsub + li;
+    const T* x = xl + leafid * nld * ncol + col;
+    T acc = 0;
+    for (int i = 0; i < nld; ++i) acc = fma(Vs[i * q2 + a], x[(int64_t)i * ncol], acc);
+    bufA[idx] = acc;
+    xh[(lo.off[leaf] + leafid) * per + a * ncol + col] = acc;
+  }
+  __syncthreads();
+  T* cur = bufA;
+  T* nxt = bufB;
+  int ncur = nsub;
+  for (int l = leaf - 1; l >= ls; --l) {
+    const int npar = ncur >> 2;
+    for (int idx = threadIdx.x; idx < npar * per; idx += blockDim.x) {
+      const int col = idx % ncol, a = (idx / ncol) % q2, pi = idx / per;
+      T acc = 0;
+      for (int c = 0; c < 4; ++c) {
+        const T* xc = cur + (4 * pi + c) * per + col;
+        const T* Tc = Ts + c * q2 * q2;
+        for (int ap = 0; ap < q2; ++ap) acc = fma(Tc[ap * q2 + a], xc[ap * ncol], acc);
+      }
+      nxt[idx] = acc;
+      xh[(lo.off[l] + P * npar + pi) * per + a * ncol + col] = acc;
+    }
+    __syncthreads();
+    T* t = cur;
+    cur = nxt;
+    nxt = t;
+    ncur = npar;
+  }
+}
+
+// Up on levels ls-1 .. 0 (single block, global values).
+template <typename T>
+__global__ void k_up_top(T* __restrict__ xh, const T* __restrict__ Tm, LevelOffsets lo, int ls, int q2, int ncol) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ts = reinterpret_cast<T*>(smem_raw);
+  for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
+  __syncthreads();
+  const int per = q2 * ncol;
+  for (int l = ls - 1; l >= 0; --l) {
+    const int np = 6 << (2 * l);
+    for (int idx = threadIdx.x; idx < np * per; idx += blockDim.x) {
+      const int col = idx % ncol, a = (idx / ncol) % q2, pi = idx / per;
+      T acc = 0;
+      for (int c = 0; c < 4; ++c) {
+        const T* xc = xh + (lo.off[l + 1] + 4 * (int64_t)pi + c) * per + col;
+        const T* Tc = Ts + c * q2 * q2;
+        for (int ap = 0; ap < q2; ++ap) acc = fma(Tc[ap * q2 + a], xc[ap * ncol], acc);
+      }
+      xh[(lo.off[l] + pi) * per + a * ncol + col] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Down on levels 1 .. ls (single block): yh_c += T_c yh_parent.
+template <typename T>
+__global__ void k_down_top(T* __restrict__ yh, const T* __restrict__ Tm, LevelOffsets lo, int ls, int q2, int ncol) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ts = reinterpret_cast<T*>(smem_raw);
+  for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
+  __syncthreads();
+  const int per = q2 * ncol;
+  for (int l = 1; l <= ls; ++l) {
+    const int nc = 6 << (2 * l);
+    for (int idx = threadIdx.x; idx < nc * per; idx += blockDim.x) {
+      const int col = idx % ncol, ap = (idx / ncol) % q2, ci = idx / per;
+      const T* Tc = Ts + (ci & 3) * q2 * q2 + ap * q2;
+      const T* y = yh + (lo.off[l - 1] + (ci >> 2)) * per + col;
+      T acc = yh[(lo.off[l] + ci) * per + ap * ncol + col];
+      for (int a = 0; a < q2; ++a) acc = fma(Tc[a], y[a * ncol], acc);
+      yh[(lo.off[l] + ci) * per + ap * ncol + col] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Down from level ls to the leaves and the leaf evaluation y_loc = V yh_leaf,
+// one block per level-ls cluster (intermediate levels stay in shared memory).
+template <typename T>
+__global__ void k_down_subtree(const T* __restrict__ yh, T* __restrict__ yl, const T* __restrict__ V,
+                               const T* __restrict__ Tm, LevelOffsets lo, int leaf, int ls, int q2, int nld,
+                               int ncol) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Vs = reinterpret_cast<T*>(smem_raw);
+  T* Ts = Vs + nld * q2;
+  T* bufA = Ts + 4 * q2 * q2;
+  const int D = leaf - ls;
+  const int nsub = 1 << (2 * D);
+  T* bufB = bufA + nsub * q2 * ncol;
+  for (int i = threadIdx.x; i < nld * q2; i += blockDim.x) Vs[i] = V[i];
+  for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
+  const int64_t P = blockIdx.x;
+  const int per = q2 * ncol;
+  for (int idx = threadIdx.x; idx < per; idx += blockDim.x) bufA[idx] = yh[(lo.off[ls] + P) * per + idx];
+  __syncthreads();
+  T* cur = bufA;
+  T* nxt = bufB;
+  int ncur = 1;
+  for (int l = ls + 1; l <= leaf; ++l) {
+    const int nch = ncur * 4;
+    for (int idx = threadIdx.x; idx < nch * per; idx += blockDim.x) {
+      const int col = idx % ncol, ap = (idx / ncol) % q2, ci = idx / per;
+      const T* Tc = Ts + (ci & 3) * q2 * q2 + ap * q2;
+      const T* y = cur + (ci >> 2) * per + col;
+      T acc = yh[(lo.off[l] + P * nch + ci) * per + ap * ncol + col];
+      for (int a = 0; a < q2; ++a) acc = fma(Tc[a], y[a * ncol], acc);
+      nxt[idx] = acc;
+    }
+    __syncthreads();
+    T* t = cur;
+    cur = nxt;
+    nxt = t;
+    ncur = nch;
+  }
+  // leaves of this subtree: y_loc = V yh_leaf
+  for (int idx = threadIdx.x; idx < nsub * nld * ncol; idx += blockDim.x) {
+    const int col = idx % ncol, i = (idx / ncol) % nld, li = idx / (nld * ncol);
+    const T* y = cur + li * per + col;
+    T acc = 0;
+    for (int a = 0; a < q2; ++a) acc = fma(Vs[i * q2 + a], y[a * ncol], acc);
+    yl[((P * nsub + li) * nld + i) * (int64_t)ncol + col] = acc;
+  }
+}
+
+template <typename T, bool CPLX, bool ONFLY>
+void launch_bsr(const int* tgt, const int* src, int64_t nblk, const T* M, const float* pts, float kre, float kim,
+                const T* x, T* y, int bs, int nrhs, cudaStream_t s) {
+  if (nblk == 0) return;
+  const int chunk = 32;
+  const int64_t warps = (nblk + chunk - 1) / chunk;
+  const int threads = 256;
+  const int grid = int((warps * 32 + threads - 1) / threads);
+  const int C = CPLX ? 2 : 1;
+  const bool vec_ok = (bs * C * sizeof(T)) % 16 == 0 && bs >= 4 && bs <= 64;
+  if (nrhs == 1 && vec_ok)
+    k_bsr_mv1<T, CPLX, ONFLY><<<grid, threads, 0, s>>>(tgt, src, nblk, M, reinterpret_cast<const float4*>(pts), kre,
+                                                        kim, x, y, bs, chunk);
+  else if (nrhs == 1)
+    k_bsr_mv<T, CPLX, ONFLY, 1><<<grid, threads, 0, s>>>(tgt, src, nblk, M, pts, kre, kim, x, y, bs, nrhs, chunk);
+  else
+    k_bsr_mv<T, CPLX, ONFLY, 4><<<grid, threads, 0, s>>>(tgt, src, nblk, M, pts, kre, kim, x, y, bs, nrhs, chunk);
+  launched("k_bsr_mv");
 }
 
 template <typename T>
@@ -224,6 +549,7 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
   const int q2 = o.q2;
+  const bool fp32 = sizeof(T) == 4;
   T* base = static_cast<T*>(scratch);
   T* xl = base;
   T* yl = xl + o.nlocal * ncol;
@@ -231,43 +557,81 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
   T* yh = xh + o.nclusters * q2 * ncol;
   const int tb = 256;
   k_gather<T><<<blocks_for(o.nlocal * ncol, tb), tb, 0, s>>>(x, xl, o.d_ex, o.L, o.d, o.n1, o.ndofs, o.nlocal, ncol, C);
-  launched("kernel");
+  launched("k_gather");
   if (q2 > 0) {
     const int64_t leaf_off = o.lvl_off[o.leaf];
-    k_leaf_up<T><<<blocks_for(o.nleaf * q2 * ncol, tb), tb, sizeof(T) * o.nld * q2, s>>>(
-        xl, xh + leaf_off * q2 * ncol, V, o.nleaf, o.nld, q2, ncol);
-    launched("kernel");
+    const int ls = std::max(0, o.leaf - 2);
+    const int nsub = 1 << (2 * (o.leaf - ls));
+    const size_t sub_shm = sizeof(T) * ((size_t)o.nld * q2 + 4 * q2 * q2 + 2 * (size_t)nsub * q2 * ncol);
     const size_t tsh = sizeof(T) * 4 * q2 * q2;
-    for (int l = o.leaf - 1; l >= 0; --l) {
-      const int64_t np = o.lvl_off[l + 1] - o.lvl_off[l];
-      k_up<T><<<blocks_for(np * q2 * ncol, tb), tb, tsh, s>>>(xh + o.lvl_off[l] * q2 * ncol,
-                                                               xh + o.lvl_off[l + 1] * q2 * ncol, Tm, np, q2, ncol);
-      launched("kernel");
+    const bool fused = sub_shm <= 96 * 1024 && o.leaf < 15;
+    LevelOffsets lo{};
+    for (int l = 0; l <= std::min(o.leaf, 14); ++l) lo.off[l] = o.lvl_off[l];
+    if (fused) {
+      set_smem_limit(k_up_subtree<T>, sub_shm);
+      set_smem_limit(k_down_subtree<T>, sub_shm);
+      const int nsubtrees = int(o.lvl_off[ls + 1] - o.lvl_off[ls]);
+      k_up_subtree<T><<<nsubtrees, 256, sub_shm, s>>>(xl, xh, V, Tm, lo, o.leaf, ls, q2, o.nld, ncol);
+      launched("k_up_subtree");
+      if (ls > 0) {
+        k_up_top<T><<<1, 1024, tsh, s>>>(xh, Tm, lo, ls, q2, ncol);
+        launched("k_up_top");
+      }
+    } else {
+      k_leaf_up<T><<<blocks_for(o.nleaf * q2 * ncol, tb), tb, sizeof(T) * o.nld * q2, s>>>(
+          xl, xh + leaf_off * q2 * ncol, V, o.nleaf, o.nld, q2, ncol);
+      launched("k_leaf_up");
+      for (int l = o.leaf - 1; l >= 0; --l) {
+        const int64_t np = o.lvl_off[l + 1] - o.lvl_off[l];
+        k_up<T><<<blocks_for(np * q2 * ncol, tb), tb, tsh, s>>>(xh + o.lvl_off[l] * q2 * ncol,
+                                                                 xh + o.lvl_off[l + 1] * q2 * ncol, Tm, np, q2, ncol);
+        launched("k_up");
+      }
     }
-    if (o.cplx)
-      k_coupling_mv<T, true><<<blocks_for(o.nclusters * q2 * nrhs, tb), tb, 0, s>>>(o.d_far_ptr, o.d_far_src, K, xh,
-                                                                                    yh, o.nclusters, q2, nrhs);
-    else
-      k_coupling_mv<T, false><<<blocks_for(o.nclusters * q2 * nrhs, tb), tb, 0, s>>>(o.d_far_ptr, o.d_far_src, K,
-                                                                                     xh, yh, o.nclusters, q2, nrhs);
-      launched("kernel");
-    for (int l = 1; l <= o.leaf; ++l) {
-      const int64_t nc = o.lvl_off[l + 1] - o.lvl_off[l];
-      k_down<T><<<blocks_for(nc * q2 * ncol, tb), tb, tsh, s>>>(yh + o.lvl_off[l] * q2 * ncol,
-                                                                 yh + o.lvl_off[l - 1] * q2 * ncol, Tm, nc, q2, ncol);
-      launched("kernel");
+    cuda_check(cudaMemsetAsync(yh, 0, sizeof(T) * o.nclusters * q2 * ncol, s), "yh clear");
+    // FP32: coupling evaluated on the fly from the cluster points; FP64: stored coupling
+    if (o.cplx) {
+      if (fp32)
+        launch_bsr<T, true, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, float(o.kre),
+                                  float(o.kim), xh, yh, q2, nrhs, s);
+      else
+        launch_bsr<T, true, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s);
+    } else {
+      if (fp32)
+        launch_bsr<T, false, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, 0.f, 0.f, xh, yh, q2,
+                                   nrhs, s);
+      else
+        launch_bsr<T, false, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s);
     }
+    if (fused) {
+      if (ls > 0) {
+        k_down_top<T><<<1, 1024, tsh, s>>>(yh, Tm, lo, ls, q2, ncol);
+        launched("k_down_top");
+      }
+      const int nsubtrees = int(o.lvl_off[ls + 1] - o.lvl_off[ls]);
+      k_down_subtree<T><<<nsubtrees, 256, sub_shm, s>>>(yh, yl, V, Tm, lo, o.leaf, ls, q2, o.nld, ncol);
+      launched("k_down_subtree");
+    } else {
+      for (int l = 1; l <= o.leaf; ++l) {
+        const int64_t nc = o.lvl_off[l + 1] - o.lvl_off[l];
+        k_down<T><<<blocks_for(nc * q2 * ncol, tb), tb, tsh, s>>>(yh + o.lvl_off[l] * q2 * ncol,
+                                                                   yh + o.lvl_off[l - 1] * q2 * ncol, Tm, nc, q2,
+                                                                   ncol);
+        launched("k_down");
+      }
+      k_leaf_down<T><<<blocks_for(o.nleaf * o.nld * ncol, tb), tb, sizeof(T) * o.nld * q2, s>>>(
+          yh + leaf_off * q2 * ncol, V, yl, o.nleaf, o.nld, q2, ncol);
+      launched("k_leaf_down");
+    }
+  } else {
+    cuda_check(cudaMemsetAsync(yl, 0, sizeof(T) * o.nlocal * ncol, s), "yl clear");
   }
-  const T* yh_leaf = q2 > 0 ? yh + o.lvl_off[o.leaf] * q2 * ncol : nullptr;
   if (o.cplx)
-    k_leaf_near<T, true><<<blocks_for(o.nleaf * o.nld * nrhs, tb), tb, 0, s>>>(
-        o.d_near_ptr, o.d_near_col, N, xl, V, yh_leaf, yl, o.nleaf, o.nld, q2, nrhs);
+    launch_bsr<T, true, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
   else
-    k_leaf_near<T, false><<<blocks_for(o.nleaf * o.nld * nrhs, tb), tb, 0, s>>>(
-        o.d_near_ptr, o.d_near_col, N, xl, V, yh_leaf, yl, o.nleaf, o.nld, q2, nrhs);
-    launched("kernel");
+    launch_bsr<T, false, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
   k_scatter<T><<<blocks_for(o.ndofs * ncol, tb), tb, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
-  launched("matvec kernels");
+  launched("k_scatter");
 }
 
 }  // namespace
@@ -351,6 +715,35 @@ void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cu
   else
     matvec_impl<double>(o, static_cast<const double*>(x), static_cast<double*>(y), nrhs, s, o.d_K, o.d_N, o.d_V,
                         o.d_T, scratch);
+}
+
+namespace {
+template <typename T>
+void precond_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const T* Dinv) {
+  const int C = o.cplx ? 2 : 1;
+  const int ncol = nrhs * C;
+  T* xl = static_cast<T*>(o.d_scratch);
+  T* yl = xl + o.nlocal * ncol;
+  const int tb = 256;
+  k_gather<T><<<blocks_for(o.nlocal * ncol, tb), tb, 0, s>>>(x, xl, o.d_ex, o.L, o.d, o.n1, o.ndofs, o.nlocal, ncol, C);
+  launched("k_gather");
+  cuda_check(cudaMemsetAsync(yl, 0, sizeof(T) * o.nlocal * ncol, s), "yl clear");
+  if (o.cplx)
+    launch_bsr<T, true, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
+  else
+    launch_bsr<T, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
+  k_scatter<T><<<blocks_for(o.ndofs * ncol, tb), tb, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
+  launched("k_scatter");
+}
+}  // namespace
+
+void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s) {
+  if (!o.d_bj) fail(BEMBEL_EINVAL, "block-Jacobi preconditioner not set up");
+  ensure_scratch(const_cast<Op&>(o), matvec_scratch_bytes(o, nrhs, fp32));
+  if (fp32)
+    precond_impl<float>(o, static_cast<const float*>(x), static_cast<float*>(y), nrhs, s, o.d_bj32);
+  else
+    precond_impl<double>(o, static_cast<const double*>(x), static_cast<double*>(y), nrhs, s, o.d_bj);
 }
 
 void ensure_scratch(Op& o, size_t bytes) {

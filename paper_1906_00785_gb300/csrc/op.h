@@ -15,9 +15,10 @@ namespace bembel {
 // One element pair of the near field.  e < f, or e == f for identical pairs.
 // code: bits 0-1 kind (0 regular, 1 identical, 2 edge, 3 vertex), bits 2-4
 // canonical map of e, bits 5-7 canonical map of f (see apply_cmap).
-// off1: offset of entry (row i of e, col j of f) = off1 + j * nld + i in the
-// near-field storage; off2 likewise for the mirrored block (row j of f, col i
-// of e) = off2 + i * nld + j, or -1 when the pair is its own mirror.
+// off1: offset of entry (row i of e, col j of f) = off1 + i * nld + j in the
+// near-field storage (row-major blocks); off2 likewise for the mirrored block
+// (row j of f, col i of e) = off2 + j * nld + i, or -1 when the pair is its own
+// mirror.
 struct PairRec {
   int e, f;
   int code, pad;
@@ -49,13 +50,14 @@ struct Op {
   long long* d_far_ptr = nullptr;  // nclusters + 1
   int* d_far_src = nullptr;        // source cluster id per block
   int* d_far_tgt = nullptr;        // target cluster id per block
-  double* d_K = nullptr;           // nfar * q2 * q2 (x2 complex), entry (a, b) at b*q2 + a
+  double* d_K = nullptr;           // nfar * q2 * q2 (x2 complex), row-major: entry (a, b) at a*q2 + b
   float* d_K32 = nullptr;
 
-  // near field: CSR over leaf clusters, blocks nld x nld, entry (i, j) at j*nld + i
+  // near field: CSR over leaf clusters, blocks nld x nld, row-major: entry (i, j) at i*nld + j
   int64_t nnear = 0;
   long long* d_near_ptr = nullptr;  // nleaf + 1
   int* d_near_col = nullptr;
+  int* d_near_tgt = nullptr;       // target leaf per block
   double* d_N = nullptr;
   float* d_N32 = nullptr;
 
@@ -76,13 +78,17 @@ struct Op {
   double* d_BW = nullptr;  // g_reg^2 * nloc: w_p h^2 B_k(u_p)
   double* d_gauss = nullptr;  // singular rule: g_sing nodes then weights
   double* d_nodes = nullptr;  // nclusters * q2 * 3 cluster interpolation points
+  float* d_nodes32 = nullptr; // FP32 copy (x, y, z, 0) per point for the on-the-fly FP32 coupling
 
   // matvec scratch (grown on demand), FP64 and FP32 views share the bytes
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
 
   // block-Jacobi preconditioner: inverses of the near-field diagonal blocks
-  double* d_bj = nullptr;
+  double* d_bj = nullptr;         // nleaf * nld * nld (x2 complex), leaf order, column-major blocks
+  float* d_bj32 = nullptr;
+  int* d_diag_blk = nullptr;      // near-field block index of the diagonal block of each leaf
+  int* d_leaf_ids = nullptr;      // 0 .. nleaf-1 (target = source list of the block diagonal)
 
   bembel_op_info info{};
 };
@@ -102,6 +108,10 @@ size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32);
 // same product with the fixed file-scope scratch of h2mv.cu; allocates nothing
 void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
 size_t matvec_noalloc_limit();
+// y = E^T D^-1 E x (block-Jacobi), uses the matvec scratch
+void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
+// precond.cu
+void precond_setup(Op& o);
 // element-local layout: dof-major, nrhs (x2 complex) real columns contiguous
 void gather_to_local(const Op& o, const double* x, double* xl, int nrhs, cudaStream_t s);
 void scatter_to_global(const Op& o, const double* yl, double* y, int nrhs, cudaStream_t s);
@@ -121,6 +131,11 @@ void cuda_check(cudaError_t e, const char* what);
 void launched(const char* what);
 // progress marker on stderr when BEMBEL_SYNC_DEBUG is set
 void debug_mark(const char* what);
+// stream capture of a CUDA graph on this thread; capture_end returns the
+// number of kernels captured (launch accounting adds them per replay)
+void capture_begin(cudaStream_t s);
+long long capture_end(cudaStream_t s, cudaGraph_t* g);
+void note_graph_kernels(long long n);
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
 

@@ -121,11 +121,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_regular(const PairRec* __r
       }
       ar *= kInv4Pi;
       ai *= kInv4Pi;
-      const long long o1 = pr.off1 + (long long)j * nld + i;
+      const long long o1 = pr.off1 + (long long)i * nld + j;
       N[o1 * C] = ar;
       if (CPLX) N[o1 * C + 1] = ai;
       if (pr.off2 >= 0) {
-        const long long o2 = pr.off2 + (long long)i * nld + j;
+        const long long o2 = pr.off2 + (long long)j * nld + i;
         N[o2 * C] = ar;
         if (CPLX) N[o2 * C + 1] = ai;
       }
@@ -265,11 +265,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_singular(const PairRec* __
     for (int k = 0; k < NL * NL; ++k) {
       if ((k & 31) != lane) continue;
       const int i = k / NL, j = k % NL;
-      const long long o1 = pr.off1 + (long long)j * nld + i;
+      const long long o1 = pr.off1 + (long long)i * nld + j;
       N[o1 * C] = ar[k] * sc;
       if (CPLX) N[o1 * C + 1] = ai[k] * sc;
       if (pr.off2 >= 0) {
-        const long long o2 = pr.off2 + (long long)i * nld + j;
+        const long long o2 = pr.off2 + (long long)j * nld + i;
         N[o2 * C] = ar[k] * sc;
         if (CPLX) N[o2 * C + 1] = ai[k] * sc;
       }
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_singular(const PairRec* __
   }
 }
 
-// Thread per coupling entry: K[blk][b][a] = G(node_a(target), node_b(source)) / (4 pi).
+// Thread per coupling entry: K[blk][a][b] = G(node_a(target), node_b(source)) / (4 pi).
 template <bool CPLX>
 __global__ void k_coupling(const int* __restrict__ tgt, const int* __restrict__ src, int64_t nfar,
                            const double* __restrict__ nodes, int q2, double kre, double kim, double* __restrict__ K) {
@@ -286,7 +286,7 @@ __global__ void k_coupling(const int* __restrict__ tgt, const int* __restrict__ 
   if (id >= nfar * per) return;
   const int64_t blk = id / per;
   const int r = int(id % per);
-  const int b = r / q2, a = r % q2;
+  const int a = r / q2, b = r % q2;  // row-major block: entry (a, b) at a*q2 + b
   const double* xa = nodes + ((int64_t)tgt[blk] * q2 + a) * 3;
   const double* xb = nodes + ((int64_t)src[blk] * q2 + b) * 3;
   const double d0 = xa[0] - xb[0], d1 = xa[1] - xb[1], d2 = xa[2] - xb[2];
@@ -366,7 +366,6 @@ void run_assembly_kernels(Op& o) {
   if (nK > 0) o.d_K = static_cast<double*>(dev_alloc(sizeof(double) * nK * C));
   if (o.opts.precision == BEMBEL_PREC_MIXED) {
     o.d_N32 = static_cast<float*>(dev_alloc(sizeof(float) * std::max<int64_t>(nN, 1)));
-    if (nK > 0) o.d_K32 = static_cast<float*>(dev_alloc(sizeof(float) * nK * C));
   }
   cuda_check(cudaEventRecord(ev[0], s), "event");
   // A1: tabulation of gamma at the regular Gauss points
@@ -401,11 +400,6 @@ void run_assembly_kernels(Op& o) {
   if (o.opts.precision == BEMBEL_PREC_MIXED) {
     k_to_f32<float><<<1024, 256, 0, s>>>(o.d_N, o.d_N32, nN);
     launched("k_to_f32");
-    if (o.nfar > 0) {
-      const int64_t n = nK * C;
-      k_to_f32<float><<<1024, 256, 0, s>>>(o.d_K, o.d_K32, n);
-      launched("k_to_f32");
-    }
   }
   cuda_check(cudaEventRecord(ev[7], s), "event");
   cuda_check(cudaEventSynchronize(ev[7]), "assembly sync");

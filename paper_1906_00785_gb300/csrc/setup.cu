@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <array>
 #include <cstring>
+#include <thread>
 #include <unordered_map>
 
 #include "op.h"
@@ -142,6 +143,97 @@ struct KeyHash {
   }
 };
 
+int num_threads(int64_t n) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  return int(std::max<int64_t>(1, std::min<int64_t>({(int64_t)hw, (int64_t)16, (n + 255) / 256})));
+}
+
+// Run fn(thread, begin, end) on nth contiguous ranges of [0, n).
+template <typename F>
+void parallel_for_t(int64_t n, int nth, F fn) {
+  if (nth <= 1) {
+    fn(0, 0, n);
+    return;
+  }
+  std::vector<std::thread> ths;
+  for (int t = 0; t < nth; ++t) {
+    const int64_t a = n * t / nth, b = n * (t + 1) / nth;
+    ths.emplace_back([&fn, t, a, b] { fn(t, a, b); });
+  }
+  for (auto& th : ths) th.join();
+}
+
+template <typename F>
+void parallel_for(int64_t n, F fn) {
+  parallel_for_t(n, num_threads(n), [&](int, int64_t a, int64_t b) { fn(a, b); });
+}
+
+// Element pairs of the near field: thread per (near block, element slot) with
+// target <= source (and pe <= pf on diagonal blocks).  Shared physical corners
+// give the pair kind and the canonical map of each element (see apply_cmap):
+// common edge: A, B = the two shared corners in the first element's corner
+// order, D2 runs A -> B; common vertex: A = the shared corner, D1 along the
+// first local axis.  Pass 0 counts per kind, pass 1 writes the records.
+__global__ void k_build_pairs(const long long* __restrict__ nptr, const int* __restrict__ ncol,
+                              const int* __restrict__ ntgt, int64_t nnear, const int* __restrict__ cid, int m2,
+                              int nloc, int nld, int pass, unsigned long long* __restrict__ cnt, PairRec* out0,
+                              PairRec* out1, PairRec* out2, PairRec* out3) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nnear * (int64_t)m2 * m2) return;
+  const int64_t blk = id / ((int64_t)m2 * m2);
+  const int slot = int(id % ((int64_t)m2 * m2));
+  const int pe = slot / m2, pf = slot % m2;
+  const int t = ntgt[blk], sc = ncol[blk];
+  if (t > sc || (t == sc && pf < pe)) return;
+  const int64_t e = (int64_t)t * m2 + pe, f = (int64_t)sc * m2 + pf;
+  int se[4], sf[4], ns = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      if (cid[e * 4 + a] == cid[f * 4 + b]) {
+        se[ns] = a;
+        sf[ns] = b;
+        ++ns;
+      }
+  int kind, me = 0, mf = 0;
+  if (ns == 0) {
+    kind = kRegular;
+  } else if (ns == 4) {
+    kind = kIdentical;
+  } else if (ns == 2) {
+    kind = kEdge;
+    me = se[0] | ((((se[0] ^ se[1]) & 1) ? 1 : 0) << 2);
+    mf = sf[0] | ((((sf[0] ^ sf[1]) & 1) ? 1 : 0) << 2);
+  } else {
+    kind = kVertex;  // ns == 1 (3 shared corners cannot occur on a conforming mesh)
+    me = se[0];
+    mf = sf[0];
+  }
+  if (pass == 0) {
+    atomicAdd(&cnt[kind], 1ull);
+    return;
+  }
+  // mirror block (sc, t) by binary search in row sc
+  long long lo = nptr[sc], hi = nptr[sc + 1] - 1;
+  while (lo < hi) {
+    const long long mid = (lo + hi) / 2;
+    if (ncol[mid] < t)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  const long long blk2 = (long long)nld * nld;
+  PairRec pr;
+  pr.e = int(e);
+  pr.f = int(f);
+  pr.code = kind | (me << 2) | (mf << 5);
+  pr.pad = 0;
+  pr.off1 = blk * blk2 + (long long)(pe * nloc) * nld + pf * nloc;
+  pr.off2 = (e == f) ? -1 : lo * blk2 + (long long)(pf * nloc) * nld + pe * nloc;
+  const unsigned long long slot_out = atomicAdd(&cnt[kind], 1ull);
+  PairRec* out = kind == 0 ? out0 : (kind == 1 ? out1 : (kind == 2 ? out2 : out3));
+  out[slot_out] = pr;
+}
+
 }  // namespace
 
 void build_structure(Op& o) {
@@ -159,31 +251,32 @@ void build_structure(Op& o) {
   o.nld = o.m * o.m * o.nloc;
   o.q2 = o.q * o.q;
   o.nleaf = 6 * (int64_t(1) << (2 * o.leaf));
+  const int m2 = o.m * o.m;
+  const int nld = o.nld, nloc = o.nloc;
+  const long long blk2 = (long long)nld * nld;
 
   // ---- element corner ids (physical matching, App. D) --------------------------
   std::vector<long long> cid(o.nelem * 4);
   {
+    // corner positions in parallel, then ids by matching rounded positions
+    std::vector<std::array<long long, 3>> keys(o.nelem * 4);
+    parallel_for(o.nelem, [&](int64_t e0, int64_t e1) {
+      for (int64_t e = e0; e < e1; ++e) {
+        const int patch = int(e / per_patch);
+        uint32_t i1, i2;
+        morton_decode(uint32_t(e % per_patch), i1, i2);
+        for (int c = 0; c < 4; ++c) {
+          double x[3];
+          gamma_eval(o.geom, patch, (i1 + (c & 1)) * o.h, (i2 + (c >> 1)) * o.h, x);
+          for (int k = 0; k < 3; ++k) keys[e * 4 + c][k] = llround(x[k] * 1e9);
+        }
+      }
+    });
     std::unordered_map<std::array<long long, 3>, long long, KeyHash> table;
     table.reserve(o.nelem * 2);
-    for (int64_t e = 0; e < o.nelem; ++e) {
-      const int patch = int(e / per_patch);
-      uint32_t i1, i2;
-      morton_decode(uint32_t(e % per_patch), i1, i2);
-      for (int c = 0; c < 4; ++c) {
-        double x[3];
-        gamma_eval(o.geom, patch, (i1 + (c & 1)) * o.h, (i2 + (c >> 1)) * o.h, x);
-        std::array<long long, 3> key;
-        for (int k = 0; k < 3; ++k) key[k] = llround(x[k] * 1e9);
-        auto it = table.find(key);
-        long long id;
-        if (it == table.end()) {
-          id = (long long)table.size();
-          table.emplace(key, id);
-        } else {
-          id = it->second;
-        }
-        cid[e * 4 + c] = id;
-      }
+    for (int64_t k = 0; k < o.nelem * 4; ++k) {
+      auto it = table.emplace(keys[k], (long long)table.size()).first;
+      cid[k] = it->second;
     }
   }
 
@@ -193,154 +286,164 @@ void build_structure(Op& o) {
   for (int l = 0; l <= o.leaf; ++l) o.lvl_off[l + 1] = o.lvl_off[l] + 6 * (int64_t(1) << (2 * l));
   o.nclusters = o.lvl_off[o.leaf + 1];
   std::vector<Ball> balls(o.nclusters);
-  for (int l = 0; l <= o.leaf; ++l) {
-    const int64_t nper = int64_t(1) << (2 * l);
-    const double H = std::ldexp(1.0, -l);
-    for (int64_t c = 0; c < 6 * nper; ++c) {
+  std::vector<int> clevel(o.nclusters);
+  for (int l = 0; l <= o.leaf; ++l)
+    for (int64_t c = o.lvl_off[l]; c < o.lvl_off[l + 1]; ++c) clevel[c] = l;
+  parallel_for(o.nclusters, [&](int64_t c0, int64_t c1) {
+    for (int64_t gc = c0; gc < c1; ++gc) {
+      const int l = clevel[gc];
+      const int64_t nper = int64_t(1) << (2 * l);
+      const int64_t c = gc - o.lvl_off[l];
+      const double H = std::ldexp(1.0, -l);
       const int patch = int(c / nper);
       uint32_t j1, j2;
       morton_decode(uint32_t(c % nper), j1, j2);
-      Ball b;
-      gamma_eval(o.geom, patch, (j1 + 0.5) * H, (j2 + 0.5) * H, b.c);
+      Ball bl;
+      gamma_eval(o.geom, patch, (j1 + 0.5) * H, (j2 + 0.5) * H, bl.c);
       double r = 0.0;
       for (int k2 = 0; k2 <= 8; ++k2)
         for (int k1 = 0; k1 <= 8; ++k1) {
           double x[3];
           gamma_eval(o.geom, patch, (j1 + k1 / 8.0) * H, (j2 + k2 / 8.0) * H, x);
-          const double dx = x[0] - b.c[0], dy = x[1] - b.c[1], dz = x[2] - b.c[2];
+          const double dx = x[0] - bl.c[0], dy = x[1] - bl.c[1], dz = x[2] - bl.c[2];
           r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz));
         }
-      b.r = r;
-      balls[o.lvl_off[l] + c] = b;
+      bl.r = r;
+      balls[gc] = bl;
     }
-  }
+  });
 
   debug_mark("setup: block tree");
-  // ---- block tree ------------------------------------------------------------------
-  std::vector<std::pair<int, int>> far, near;  // global cluster ids (target, source)
+  // ---- block tree, level by level ------------------------------------------------
+  // The candidate sources of a target are the children of the non-admissible
+  // sources of its parent (all patches on level 0), visited in increasing order,
+  // so the far lists come out in CSR order by target id without sorting.
+  const bool compress = o.q > 0;
+  auto admissible = [&](int t, int sc) {
+    if (!compress) return false;
+    const Ball &bt = balls[t], &bs = balls[sc];
+    const double dx = bt.c[0] - bs.c[0], dy = bt.c[1] - bs.c[1], dz = bt.c[2] - bs.c[2];
+    const double dist = std::max(0.0, std::sqrt(dx * dx + dy * dy + dz * dz) - bt.r - bs.r);
+    return 2.0 * std::max(bt.r, bs.r) <= o.opts.eta * dist;
+  };
+  std::vector<long long> fptr(o.nclusters + 1, 0);
+  std::vector<int> fsrc;
+  std::vector<long long> nptr;
+  std::vector<int> ncol;
   {
-    const bool compress = o.q > 0;
-    std::vector<std::pair<int, int>> stack;
-    for (int p = 0; p < 6; ++p)
-      for (int r = 0; r < 6; ++r) stack.push_back({p, r});
-    while (!stack.empty()) {
-      auto [t, s] = stack.back();
-      stack.pop_back();
-      int lev = 0;
-      while (t >= o.lvl_off[lev + 1]) ++lev;
-      bool adm = false;
-      if (compress) {
-        const Ball &bt = balls[t], &bs = balls[s];
-        const double dx = bt.c[0] - bs.c[0], dy = bt.c[1] - bs.c[1], dz = bt.c[2] - bs.c[2];
-        const double dist = std::max(0.0, std::sqrt(dx * dx + dy * dy + dz * dz) - bt.r - bs.r);
-        adm = 2.0 * std::max(bt.r, bs.r) <= o.opts.eta * dist;
+    // non-admissible lists of the previous level (CSR over its targets, source ids global)
+    std::vector<long long> pptr = {0};
+    std::vector<int> pcol;
+    for (int l = 0; l <= o.leaf; ++l) {
+      const int64_t t0 = o.lvl_off[l], nt = o.lvl_off[l + 1] - t0;
+      const int nth = num_threads(nt);
+      std::vector<std::vector<int>> tf(nth), tn(nth);          // per-thread far / non-admissible sources
+      std::vector<std::vector<long long>> cf(nth), cn(nth);    // per-target counts
+      parallel_for_t(nt, nth, [&](int th, int64_t a, int64_t b2) {
+        for (int64_t i = a; i < b2; ++i) {
+          const int t = int(t0 + i);
+          long long nf = 0, nn = 0;
+          auto visit = [&](int sc) {
+            if (admissible(t, sc)) {
+              tf[th].push_back(sc);
+              ++nf;
+            } else {
+              tn[th].push_back(sc);
+              ++nn;
+            }
+          };
+          if (l == 0) {
+            for (int p = 0; p < 6; ++p) visit(p);
+          } else {
+            const int64_t par = (i >> 2);  // parent index within level l-1
+            for (long long k = pptr[par]; k < pptr[par + 1]; ++k) {
+              const int64_t sl = pcol[k] - o.lvl_off[l - 1];
+              for (int c = 0; c < 4; ++c) visit(int(o.lvl_off[l] + 4 * sl + c));
+            }
+          }
+          cf[th].push_back(nf);
+          cn[th].push_back(nn);
+        }
+      });
+      std::vector<long long> nptr_l(nt + 1, 0);
+      std::vector<int> ncol_l;
+      int64_t i = 0;
+      for (int th = 0; th < nth; ++th) {
+        for (size_t k = 0; k < cf[th].size(); ++k, ++i) {
+          fptr[t0 + i + 1] = cf[th][k];
+          nptr_l[i + 1] = nptr_l[i] + cn[th][k];
+        }
+        fsrc.insert(fsrc.end(), tf[th].begin(), tf[th].end());
+        ncol_l.insert(ncol_l.end(), tn[th].begin(), tn[th].end());
       }
-      if (adm) {
-        far.push_back({t, s});
-      } else if (lev == o.leaf) {
-        near.push_back({t, s});
-      } else {
-        const int64_t tl = t - o.lvl_off[lev], sl = s - o.lvl_off[lev];
-        for (int ct = 0; ct < 4; ++ct)
-          for (int cs = 0; cs < 4; ++cs)
-            stack.push_back({int(o.lvl_off[lev + 1] + 4 * tl + ct), int(o.lvl_off[lev + 1] + 4 * sl + cs)});
-      }
+      pptr.swap(nptr_l);
+      pcol.swap(ncol_l);
     }
+    // leaf-level non-admissible pairs are the near field (leaf-local ids)
+    const int64_t leaf_off = o.lvl_off[o.leaf];
+    nptr = pptr;
+    ncol.resize(pcol.size());
+    for (size_t k = 0; k < pcol.size(); ++k) ncol[k] = int(pcol[k] - leaf_off);
   }
-  std::sort(far.begin(), far.end());
-  std::sort(near.begin(), near.end());
-  o.nfar = (int64_t)far.size();
-  o.nnear = (int64_t)near.size();
-
+  for (int64_t c = 0; c < o.nclusters; ++c) fptr[c + 1] += fptr[c];
+  o.nfar = (int64_t)fsrc.size();
+  o.nnear = (int64_t)ncol.size();
   {
-    std::vector<long long> ptr(o.nclusters + 1, 0);
-    std::vector<int> src(o.nfar), tgt(o.nfar);
-    for (int64_t i = 0; i < o.nfar; ++i) {
-      ptr[far[i].first + 1]++;
-      src[i] = far[i].second;
-      tgt[i] = far[i].first;
-    }
-    for (int64_t c = 0; c < o.nclusters; ++c) ptr[c + 1] += ptr[c];
-    o.d_far_ptr = upload(ptr);
-    o.d_far_src = upload(src);
+    std::vector<int> tgt(o.nfar);
+    for (int64_t c = 0; c < o.nclusters; ++c)
+      for (long long k = fptr[c]; k < fptr[c + 1]; ++k) tgt[k] = int(c);
+    o.d_far_ptr = upload(fptr);
+    o.d_far_src = upload(fsrc);
     o.d_far_tgt = upload(tgt);
   }
-  std::vector<long long> nptr(o.nleaf + 1, 0);
-  std::vector<int> ncol(o.nnear);
-  const int64_t leaf_off = o.lvl_off[o.leaf];
-  for (int64_t i = 0; i < o.nnear; ++i) {
-    nptr[near[i].first - leaf_off + 1]++;
-    ncol[i] = int(near[i].second - leaf_off);
-  }
-  for (int64_t c = 0; c < o.nleaf; ++c) nptr[c + 1] += nptr[c];
   o.d_near_ptr = upload(nptr);
   o.d_near_col = upload(ncol);
+  {
+    std::vector<int> diag(o.nleaf, -1), ids(o.nleaf), ntgt(o.nnear);
+    for (int64_t t = 0; t < o.nleaf; ++t) {
+      ids[t] = int(t);
+      for (long long k = nptr[t]; k < nptr[t + 1]; ++k) {
+        ntgt[k] = int(t);
+        if (ncol[k] == t) diag[t] = int(k);
+      }
+      if (diag[t] < 0) fail(BEMBEL_EINVAL, "near field lacks a diagonal block");
+    }
+    o.d_diag_blk = upload(diag);
+    o.d_leaf_ids = upload(ids);
+    o.d_near_tgt = upload(ntgt);
+  }
 
   debug_mark("setup: element pairs of the near field");
-  // ---- element pairs of the near field --------------------------------------------
-  auto block_index = [&](int64_t t, int64_t s) -> long long {
-    const auto b = ncol.begin() + nptr[t], en = ncol.begin() + nptr[t + 1];
-    auto it = std::lower_bound(b, en, int(s));
-    if (it == en || *it != s) fail(BEMBEL_EINVAL, "block tree is not symmetric");
-    return (long long)(it - ncol.begin());
-  };
-  const int m2 = o.m * o.m;
-  const int nld = o.nld, nloc = o.nloc;
-  const long long blk2 = (long long)nld * nld;
-  std::vector<PairRec> lists[4];
-  for (int64_t i = 0; i < o.nnear; ++i) {
-    const int64_t t = near[i].first - leaf_off, s = near[i].second - leaf_off;
-    if (t > s) continue;
-    const long long b1 = i, b2 = block_index(s, t);
-    for (int pe = 0; pe < m2; ++pe) {
-      const int64_t e = t * m2 + pe;
-      for (int pf = (t == s ? pe : 0); pf < m2; ++pf) {
-        const int64_t f = s * m2 + pf;
-        const long long* ce = &cid[e * 4];
-        const long long* cf = &cid[f * 4];
-        int shared_e[4], shared_f[4], ns = 0;
-        for (int a = 0; a < 4; ++a)
-          for (int b = 0; b < 4; ++b)
-            if (ce[a] == cf[b]) {
-              shared_e[ns] = a;
-              shared_f[ns] = b;
-              ++ns;
-            }
-        PairRec pr;
-        pr.e = int(e);
-        pr.f = int(f);
-        pr.pad = 0;
-        pr.off1 = b1 * blk2 + (long long)(pf * nloc) * nld + pe * nloc;
-        pr.off2 = (e == f) ? -1 : b2 * blk2 + (long long)(pe * nloc) * nld + pf * nloc;
-        int kind, me = 0, mf = 0;
-        if (ns == 0) {
-          kind = kRegular;
-        } else if (ns == 4) {
-          kind = kIdentical;
-        } else if (ns == 2) {
-          kind = kEdge;
-          // A = first shared corner of e, B = second; D2 runs A -> B, D1 is the other axis.
-          const int ae = shared_e[0], be = shared_e[1];
-          const int af = shared_f[0], bf = shared_f[1];
-          const int ax_e = ((ae ^ be) & 1) ? 1 : 0;  // A->B along axis 0 => D1 along axis 1
-          const int ax_f = ((af ^ bf) & 1) ? 1 : 0;
-          me = ae | (ax_e << 2);
-          mf = af | (ax_f << 2);
-        } else if (ns == 1) {
-          kind = kVertex;
-          me = shared_e[0];
-          mf = shared_f[0];
-        } else {
-          fail(BEMBEL_EINVAL, "elements share 3 corners: mesh is not conforming (App. D)");
+  // ---- element pairs of the near field (classified on the device) -----------------
+  {
+    std::vector<int> cid32(cid.begin(), cid.end());
+    int* d_cid = upload(cid32);
+    unsigned long long* d_cnt = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * 4));
+    const int64_t work = o.nnear * (int64_t)m2 * m2;
+    const int tb = 256;
+    const int grid = int(std::max<int64_t>(1, (work + tb - 1) / tb));
+    PairRec* outs[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned long long cnt[4];
+    for (int pass = 0; pass < 2; ++pass) {
+      cuda_check(cudaMemset(d_cnt, 0, sizeof(unsigned long long) * 4), "pair counters");
+      k_build_pairs<<<grid, tb>>>(o.d_near_ptr, o.d_near_col, o.d_near_tgt, o.nnear, d_cid, m2, o.nloc, o.nld,
+                                   pass, d_cnt, outs[0], outs[1], outs[2], outs[3]);
+      launched("k_build_pairs");
+      cuda_check(cudaMemcpy(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost), "pair counts");
+      if (pass == 0)
+        for (int k = 0; k < 4; ++k) {
+          o.npairs[k] = (int64_t)cnt[k];
+          outs[k] = static_cast<PairRec*>(dev_alloc(sizeof(PairRec) * std::max<int64_t>(1, o.npairs[k])));
         }
-        pr.code = kind | (me << 2) | (mf << 5);
-        lists[kind].push_back(pr);
-      }
     }
-  }
-  for (int k = 0; k < 4; ++k) {
-    o.npairs[k] = (int64_t)lists[k].size();
-    o.d_pairs[k] = upload(lists[k]);
+    for (int k = 0; k < 4; ++k) {
+      if (cnt[k] != (unsigned long long)o.npairs[k]) fail(BEMBEL_EINVAL, "pair list build is inconsistent");
+      o.d_pairs[k] = outs[k];
+    }
+    unsigned long long bad = 0;
+    dev_free(d_cid);
+    dev_free(d_cnt);
+    (void)bad;
   }
 
   debug_mark("setup: Bezier extraction");
@@ -411,20 +514,29 @@ void build_structure(Op& o) {
 
     // cluster interpolation points in R^3
     std::vector<double> nodes((size_t)o.nclusters * q2 * 3);
-    for (int l = 0; l <= o.leaf; ++l) {
-      const int64_t nper = int64_t(1) << (2 * l);
-      const double H = std::ldexp(1.0, -l);
-      for (int64_t c = 0; c < 6 * nper; ++c) {
+    std::vector<double> cheb(q);
+    for (int a = 0; a < q; ++a) cheb[a] = chebyshev01(q, a);
+    parallel_for(o.nclusters, [&](int64_t c0, int64_t c1) {
+      for (int64_t gc = c0; gc < c1; ++gc) {
+        int l = 0;
+        while (gc >= o.lvl_off[l + 1]) ++l;
+        const int64_t nper = int64_t(1) << (2 * l);
+        const int64_t c = gc - o.lvl_off[l];
+        const double H = std::ldexp(1.0, -l);
         const int patch = int(c / nper);
         uint32_t j1, j2;
         morton_decode(uint32_t(c % nper), j1, j2);
         for (int a2 = 0; a2 < q; ++a2)
           for (int a1 = 0; a1 < q; ++a1)
-            gamma_eval(o.geom, patch, (j1 + chebyshev01(q, a1)) * H, (j2 + chebyshev01(q, a2)) * H,
-                       &nodes[(((size_t)(o.lvl_off[l] + c)) * q2 + a1 + q * a2) * 3]);
+            gamma_eval(o.geom, patch, (j1 + cheb[a1]) * H, (j2 + cheb[a2]) * H,
+                       &nodes[((size_t)gc * q2 + a1 + q * a2) * 3]);
       }
-    }
+    });
     o.d_nodes = upload(nodes);
+    std::vector<float> nodes32(nodes.size() / 3 * 4, 0.f);
+    for (size_t k = 0; k < nodes.size() / 3; ++k)
+      for (int c = 0; c < 3; ++c) nodes32[k * 4 + c] = float(nodes[k * 3 + c]);
+    o.d_nodes32 = upload(nodes32);
   }
 
   debug_mark("setup: quadrature tables");

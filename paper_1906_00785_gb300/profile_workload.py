@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--matvecs", type=int, default=3)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--fp32", action="store_true", help="assemble MIXED and time the FP32 matvec")
+    ap.add_argument("--solve", action="store_true", help="also solve a point-charge problem to 1e-8")
+    ap.add_argument("--precond", action="store_true", help="block-Jacobi preconditioner for --solve")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     geom = bem.bembel_geom_create(bem.BEMBEL_GEOM_SPHERE6)
@@ -42,6 +44,13 @@ def main():
         bem.bembel_matvec(op, x, y, a.nrhs, fp32=a.fp32)
     torch.cuda.synchronize()
     info = bem.bembel_op_info_get(op)
+    if a.solve:
+        bdt = torch.complex128 if cplx else torch.float64
+        b = torch.empty(n, dtype=bdt, device="cuda")
+        bem.bembel_rhs(op, bem.BEMBEL_RHS_POINT_SOURCE, [[0.0, 0.0, 2.0]], b)
+        xs = torch.empty_like(b)
+        pc = bem.BEMBEL_PRECOND_BLOCK_JACOBI if a.precond else bem.BEMBEL_PRECOND_NONE
+        info["solve"] = bem.bembel_solve(op, b, xs, 1, tol=1e-8, precond=pc)
     print(json.dumps({k: v for k, v in info.items()}))
 
 

@@ -185,3 +185,47 @@ def test_invalid_arguments(geom):
         bem.bembel_matvec(gop, x, torch.empty_like(x), 1, fp32=True)  # FP64 operator has no FP32 copy
     out = bem.bembel_solve(gop, x, torch.empty_like(x), 1)  # zero right-hand side
     assert out["converged"] and out["iterations"] == 0
+
+
+@pytest.mark.parametrize("op,k,d", [("laplace", 0.0, 1), ("helmholtz", 2.5, 2), ("laplace", 0.0, 0)])
+def test_block_jacobi_solve_parity(geom, op, k, d):
+    """Right block-Jacobi preconditioning changes iterations, not the solution.
+
+    Both solves run to relative residual 1e-13; the solution error is bounded by
+    cond(A) x residual (cond(A) < 1e4 for these operators), so 1e-8.
+    """
+    L = 3
+    sp = S2Space(Sphere6(), L, d)
+    gop = bem.bembel_assemble(geom, LAP if op == "laplace" else HEL, k, L, d, 0)
+    n = bem.bembel_ndofs(gop)
+    dt = torch.complex128 if op == "helmholtz" else torch.float64
+    b = torch.empty(n, dtype=dt, device="cuda")
+    bem.bembel_rhs(gop, bem.BEMBEL_RHS_POINT_SOURCE, np.array([[0.1, 0.2, -0.3]]), b)
+    x0, x1 = torch.empty_like(b), torch.empty_like(b)
+    i0 = bem.bembel_solve(gop, b, x0, 1, tol=1e-13, precond=bem.BEMBEL_PRECOND_NONE)
+    i1 = bem.bembel_solve(gop, b, x1, 1, tol=1e-13, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)
+    assert i0["converged"] and i1["converged"]
+    assert i1["iterations"] < i0["iterations"]
+    A_ref = Assembler(sp, op, k, 4, 5).dense()
+    x_ref = np.linalg.solve(A_ref, b.cpu().numpy())
+    assert rel_err(x1.cpu().numpy(), x_ref) < 1e-8
+    assert rel_err(x0.cpu().numpy(), x_ref) < 1e-8
+
+
+def test_batched_solve_matches_single(geom):
+    gop = bem.bembel_assemble(geom, HEL, 2.0, 3, 1, 4, precision=bem.BEMBEL_PREC_MIXED)
+    n = bem.bembel_ndofs(gop)
+    dirs = np.array([[0, 0, 1.0], [1.0, 0, 0], [0.6, 0.8, 0], [0, -0.6, 0.8]])
+    B = torch.empty((4, n), dtype=torch.complex128, device="cuda")
+    bem.bembel_rhs(gop, bem.BEMBEL_RHS_PLANE_WAVE, dirs, B)
+    X = torch.empty_like(B)
+    info = bem.bembel_solve(gop, B, X, 4, tol=1e-10, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)
+    assert info["converged"] and info["rel_residual"] <= 1e-10
+    for r in range(4):
+        x1 = torch.empty_like(B[r])
+        bem.bembel_solve(gop, B[r].contiguous(), x1, 1, tol=1e-10, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)
+        assert (torch.linalg.norm(x1 - X[r]) / torch.linalg.norm(x1)).item() < 1e-8
+    # residual of the batch checked with the FP64 operator product
+    Y = torch.empty_like(B)
+    bem.bembel_matvec(gop, X, Y, 4)
+    assert (torch.linalg.norm(Y - B) / torch.linalg.norm(B)).item() < 1e-9
