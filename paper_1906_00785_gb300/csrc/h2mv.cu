@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(256) k_bsr_mv1(const int* __restrict__ tgt, co
   const int64_t b1 = min(nblk, b0 + chunk);
   const int rowlen = bs * C;  // scalars per block row
   const int nvec = rowlen / V;
+  const T fscale = ONFLY ? T(kInv4Pi) : T(1);
   for (int a = sl; a < bs; a += SW) {
     T ar = T(0), ai = T(0);
     int cur = -1;
@@ -290,8 +291,8 @@ __global__ void __launch_bounds__(256) k_bsr_mv1(const int* __restrict__ tgt, co
       const int t = tgt[blk];
       if (t != cur) {
         if (cur >= 0) {
-          atomicAdd(y + ((int64_t)cur * bs + a) * C, ar);
-          if (CPLX) atomicAdd(y + ((int64_t)cur * bs + a) * C + 1, ai);
+          atomicAdd(y + ((int64_t)cur * bs + a) * C, ar * fscale);
+          if (CPLX) atomicAdd(y + ((int64_t)cur * bs + a) * C + 1, ai * fscale);
           ar = ai = T(0);
         }
         cur = t;
@@ -327,9 +328,9 @@ __global__ void __launch_bounds__(256) k_bsr_mv1(const int* __restrict__ tgt, co
             const float4 p = pb[(k * V + u) / C];
             const float d0 = pa.x - p.x, d1 = pa.y - p.y, d2 = pa.z - p.z;
             const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            const float rinv = rsqrtf(r2) * float(kInv4Pi);
+            const float rinv = rsqrtf(r2);  // 1/(4 pi) applied when the row sum is flushed
             if (CPLX) {
-              const float rr = r2 * rsqrtf(r2);
+              const float rr = r2 * rinv;
               float sn, cs;
               __sincosf(kre * rr, &sn, &cs);
               const float am = (kim != 0.f ? __expf(kim * rr) : 1.f) * rinv;
@@ -344,8 +345,8 @@ __global__ void __launch_bounds__(256) k_bsr_mv1(const int* __restrict__ tgt, co
       }
     }
     if (cur >= 0) {
-      atomicAdd(y + ((int64_t)cur * bs + a) * C, ar);
-      if (CPLX) atomicAdd(y + ((int64_t)cur * bs + a) * C + 1, ai);
+      atomicAdd(y + ((int64_t)cur * bs + a) * C, ar * fscale);
+      if (CPLX) atomicAdd(y + ((int64_t)cur * bs + a) * C + 1, ai * fscale);
     }
   }
 }
@@ -370,9 +371,9 @@ __global__ void k_leaf_down(const T* __restrict__ yh, const T* __restrict__ V, T
 }
 
 // ---------------------------------------------------------------------------
-// Fused transfer passes.  Levels ls = max(0, leaf - 2) .. leaf are handled per
+// Fused transfer passes.  Levels ls = max(0, leaf - 3) .. leaf are handled per
 // subtree (one thread block per level-ls cluster, the subtree's values kept in
-// shared memory); levels below ls by one single-block kernel.
+// shared memory); the few levels below ls by one small kernel per level.
 // ---------------------------------------------------------------------------
 struct LevelOffsets {
   long long off[16];
@@ -426,52 +427,6 @@ __global__ void k_up_subtree(const T* __restrict__ xl, T* __restrict__ xh, const
     cur = nxt;
     nxt = t;
     ncur = npar;
-  }
-}
-
-// Up on levels ls-1 .. 0 (single block, global values).
-template <typename T>
-__global__ void k_up_top(T* __restrict__ xh, const T* __restrict__ Tm, LevelOffsets lo, int ls, int q2, int ncol) {
-  extern __shared__ unsigned char smem_raw[];
-  T* Ts = reinterpret_cast<T*>(smem_raw);
-  for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
-  __syncthreads();
-  const int per = q2 * ncol;
-  for (int l = ls - 1; l >= 0; --l) {
-    const int np = 6 << (2 * l);
-    for (int idx = threadIdx.x; idx < np * per; idx += blockDim.x) {
-      const int col = idx % ncol, a = (idx / ncol) % q2, pi = idx / per;
-      T acc = 0;
-      for (int c = 0; c < 4; ++c) {
-        const T* xc = xh + (lo.off[l + 1] + 4 * (int64_t)pi + c) * per + col;
-        const T* Tc = Ts + c * q2 * q2;
-        for (int ap = 0; ap < q2; ++ap) acc = fma(Tc[ap * q2 + a], xc[ap * ncol], acc);
-      }
-      xh[(lo.off[l] + pi) * per + a * ncol + col] = acc;
-    }
-    __syncthreads();
-  }
-}
-
-// Down on levels 1 .. ls (single block): yh_c += T_c yh_parent.
-template <typename T>
-__global__ void k_down_top(T* __restrict__ yh, const T* __restrict__ Tm, LevelOffsets lo, int ls, int q2, int ncol) {
-  extern __shared__ unsigned char smem_raw[];
-  T* Ts = reinterpret_cast<T*>(smem_raw);
-  for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
-  __syncthreads();
-  const int per = q2 * ncol;
-  for (int l = 1; l <= ls; ++l) {
-    const int nc = 6 << (2 * l);
-    for (int idx = threadIdx.x; idx < nc * per; idx += blockDim.x) {
-      const int col = idx % ncol, ap = (idx / ncol) % q2, ci = idx / per;
-      const T* Tc = Ts + (ci & 3) * q2 * q2 + ap * q2;
-      const T* y = yh + (lo.off[l - 1] + (ci >> 2)) * per + col;
-      T acc = yh[(lo.off[l] + ci) * per + ap * ncol + col];
-      for (int a = 0; a < q2; ++a) acc = fma(Tc[a], y[a * ncol], acc);
-      yh[(lo.off[l] + ci) * per + ap * ncol + col] = acc;
-    }
-    __syncthreads();
   }
 }
 
@@ -560,7 +515,7 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
   launched("k_gather");
   if (q2 > 0) {
     const int64_t leaf_off = o.lvl_off[o.leaf];
-    const int ls = std::max(0, o.leaf - 2);
+    const int ls = std::max(0, o.leaf - 3);
     const int nsub = 1 << (2 * (o.leaf - ls));
     const size_t sub_shm = sizeof(T) * ((size_t)o.nld * q2 + 4 * q2 * q2 + 2 * (size_t)nsub * q2 * ncol);
     const size_t tsh = sizeof(T) * 4 * q2 * q2;
@@ -573,9 +528,12 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
       const int nsubtrees = int(o.lvl_off[ls + 1] - o.lvl_off[ls]);
       k_up_subtree<T><<<nsubtrees, 256, sub_shm, s>>>(xl, xh, V, Tm, lo, o.leaf, ls, q2, o.nld, ncol);
       launched("k_up_subtree");
-      if (ls > 0) {
-        k_up_top<T><<<1, 1024, tsh, s>>>(xh, Tm, lo, ls, q2, ncol);
-        launched("k_up_top");
+      for (int l = ls - 1; l >= 0; --l) {
+        const int64_t np = o.lvl_off[l + 1] - o.lvl_off[l];
+        k_up<T><<<blocks_for(np * q2 * ncol, 128), 128, tsh, s>>>(xh + o.lvl_off[l] * q2 * ncol,
+                                                                   xh + o.lvl_off[l + 1] * q2 * ncol, Tm, np, q2,
+                                                                   ncol);
+        launched("k_up");
       }
     } else {
       k_leaf_up<T><<<blocks_for(o.nleaf * q2 * ncol, tb), tb, sizeof(T) * o.nld * q2, s>>>(
@@ -604,9 +562,12 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
         launch_bsr<T, false, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s);
     }
     if (fused) {
-      if (ls > 0) {
-        k_down_top<T><<<1, 1024, tsh, s>>>(yh, Tm, lo, ls, q2, ncol);
-        launched("k_down_top");
+      for (int l = 1; l <= ls; ++l) {
+        const int64_t nc = o.lvl_off[l + 1] - o.lvl_off[l];
+        k_down<T><<<blocks_for(nc * q2 * ncol, 128), 128, tsh, s>>>(yh + o.lvl_off[l] * q2 * ncol,
+                                                                     yh + o.lvl_off[l - 1] * q2 * ncol, Tm, nc, q2,
+                                                                     ncol);
+        launched("k_down");
       }
       const int nsubtrees = int(o.lvl_off[ls + 1] - o.lvl_off[ls]);
       k_down_subtree<T><<<nsubtrees, 256, sub_shm, s>>>(yh, yl, V, Tm, lo, o.leaf, ls, q2, o.nld, ncol);

@@ -190,7 +190,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_singular(const PairRec* __
   constexpr int D1 = D + 1;
   constexpr int NL = D1 * D1;
   constexpr int C = CPLX ? 2 : 1;
-  constexpr int NSUB = KIND == kIdentical ? 8 : (KIND == kEdge ? 6 : 4);
+  // identical pairs: the rule is symmetric under s <-> t (quadrant sigma maps to
+  // -sigma with the same weight), so half the sub-domains are integrated and
+  // the block is symmetrised at the end: A = M + M^T.
+  constexpr int NSUB = KIND == kIdentical ? 4 : (KIND == kEdge ? 6 : 4);
   __shared__ double gx[kMaxG], gw[kMaxG];
   if (threadIdx.x < G) {
     gx[threadIdx.x] = gauss[threadIdx.x];
@@ -213,8 +216,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_singular(const PairRec* __
 #pragma unroll
     for (int k = 0; k < NL * NL; ++k) ar[k] = ai[k] = 0.0;
     for (int idx = lane; idx < npts; idx += 32) {
-      const int sub = idx / G4;
-      int rem = idx - sub * G4;
+      const int sub0 = idx / G4;
+      int rem = idx - sub0 * G4;
+      // identical: sub-domains with sigma_1 = +1 only (sub & 1 == 0 -> quadrants (+,+), (+,-))
+      const int sub = KIND == kIdentical ? (((sub0 & 1) << 1) | ((sub0 >> 1) << 2)) : sub0;
       const int i0 = rem % G;
       rem /= G;
       const int i1 = rem % G;
@@ -261,6 +266,19 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_singular(const PairRec* __
       }
     }
     const double sc = kInv4Pi * h * h * h * h;
+    if (KIND == kIdentical) {
+      double tr[NL * NL], ti[NL * NL];
+#pragma unroll
+      for (int k = 0; k < NL * NL; ++k) {
+        tr[k] = ar[k] + ar[(k % NL) * NL + k / NL];
+        if (CPLX) ti[k] = ai[k] + ai[(k % NL) * NL + k / NL];
+      }
+#pragma unroll
+      for (int k = 0; k < NL * NL; ++k) {
+        ar[k] = tr[k];
+        if (CPLX) ai[k] = ti[k];
+      }
+    }
 #pragma unroll
     for (int k = 0; k < NL * NL; ++k) {
       if ((k & 31) != lane) continue;
