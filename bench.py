@@ -33,7 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H² assembly time & matvec GDOF/s; GMRES time-to-1e-8 vs plain FP64 GPU path"
-WORKLOAD = dict(level=6, p=1, q=4, eta=1.6, leaf=5, g_reg=4, g_sing=5, x0=(0.0, 0.0, 2.0), n_eval=100)
+WORKLOAD = dict(level=6, p=1, q=4, eta=1.6, leaf=5, g_reg=4, g_sing=5, quad_tol=1e-6, x0=(0.0, 0.0, 2.0),
+                n_eval=100)
 # FP64 flops per quadrature point (counted from the formulas):
 # regular pair point (x_p, y_q): difference, squared norm, 1/r, 4 (d=1) weighted products
 FLOPS_REG_POINT = {0: 12, 1: 18, 2: 28}
@@ -212,10 +213,19 @@ def main():
     pts = pts_host.to(dev)
     x0 = np.array([w["x0"]])
 
+    # quadrature orders for 1e-6 relative block accuracy, 50x below the q = 4 far-field
+    # interpolation error (~5e-5): autotuned once, cached for the run
+    tuned_opts, tune = bem.bembel_autotune(geom, bem.BEMBEL_LAPLACE_SL, 0.0, w["level"], w["p"],
+                                           quad_tol=w["quad_tol"], far_tol=1e-4, q_max=w["q"], eta=w["eta"],
+                                           leaf_level=w["leaf"], stream=stream.cuda_stream)
+
     def assemble(precision):
-        return bem.bembel_assemble(geom, bem.BEMBEL_LAPLACE_SL, 0.0, w["level"], w["p"], w["q"], eta=w["eta"],
-                                   leaf_level=w["leaf"], g_regular=w["g_reg"], g_singular=w["g_sing"],
-                                   precision=precision, stream=stream.cuda_stream)
+        o = bem.bembel_opts_default()
+        for f in ("g_regular", "g_singular", "g_identical", "g_edge", "g_vertex", "bsr_chunk"):
+            setattr(o, f, getattr(tuned_opts, f))
+        return bem.bembel_assemble(geom, bem.BEMBEL_LAPLACE_SL, 0.0, w["level"], w["p"], w["q"], opts=o,
+                                   eta=w["eta"], leaf_level=w["leaf"], precision=precision,
+                                   stream=stream.cuda_stream)
 
     state = {}
 
@@ -328,11 +338,11 @@ def main():
     ph = opinfo["phase_ms"]
     names = ["tabulation", "near_regular", "singular_identical", "singular_edge", "singular_vertex", "coupling",
              "fp32_copies"]
-    g4 = w["g_sing"] ** 4
-    pts_phase = {"near_regular": opinfo["n_pairs_regular"] * w["g_reg"] ** 4,
-                 "singular_identical": opinfo["n_pairs_identical"] * 8 * g4,
-                 "singular_edge": opinfo["n_pairs_edge"] * 6 * g4,
-                 "singular_vertex": opinfo["n_pairs_vertex"] * 4 * g4}
+    # rule points actually integrated (identical pairs: half of the 8 sub-domains, by symmetry)
+    pts_phase = {"near_regular": opinfo["n_pairs_regular"] * tune["g_regular"] ** 4,
+                 "singular_identical": opinfo["n_pairs_identical"] * 4 * tune["g_identical"] ** 4,
+                 "singular_edge": opinfo["n_pairs_edge"] * 6 * tune["g_edge"] ** 4,
+                 "singular_vertex": opinfo["n_pairs_vertex"] * 4 * tune["g_vertex"] ** 4}
     flops_phase = {k: v * (FLOPS_REG_POINT[w["p"]] if k == "near_regular" else FLOPS_SING_POINT[w["p"]])
                    for k, v in pts_phase.items()}
     dom = max(flops_phase, key=lambda k: ph[names.index(k)])
@@ -364,7 +374,10 @@ def main():
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": "laplace_h2_sphere6_L6_p1_q4_eta1.6", "ndofs": n1, "nrhs": 1, "level": w["level"],
                    "degree": w["p"], "q": w["q"], "eta": w["eta"], "leaf_level": w["leaf"],
-                   "g_regular": w["g_reg"], "g_singular": w["g_sing"], "precision": "mixed (FP64 quadrature, "
+                   "quadrature": f"autotuned for {w['quad_tol']:g} relative block accuracy: regular "
+                                 f"{tune['g_regular']}^2 per element, Duffy {tune['g_identical']}/{tune['g_edge']}/"
+                                 f"{tune['g_vertex']} per variable (identical/edge/vertex)",
+                   "precision": "mixed (FP64 quadrature, "
                    "FP32 inner GMRES with block-Jacobi, FP64 refinement)", "l2": "working set > L2 (near+far FP64 storage "
                    f"{matvec_bytes / 1e9:.2f} GB per step)", "parallelism": f"replicas x{world}"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
@@ -377,6 +390,7 @@ def main():
                   "fp64_ms": info64["solve_ms"], "fp64_iters": info64["iterations"],
                   "fp64_relres": info64["rel_residual"], "speedup_vs_fp64": info64["solve_ms"] / infomx["solve_ms"]},
         "matvec": mv, "potential_max_rel_err": pot_err, "peaks_source": peak_src,
+        "autotune": {k: v for k, v in tune.items()},
     }
     if rank == 0:
         print(json.dumps(line))

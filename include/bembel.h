@@ -92,6 +92,10 @@ typedef struct {
   int leaf_level;    /* quadtree leaf level; -1: max(0, level - 1)                           */
   int g_regular;     /* Gauss points per direction on separated near-field pairs (4)         */
   int g_singular;    /* Gauss points per variable of the Duffy rules (5)                     */
+  int g_identical;   /* per-class overrides of g_singular for identical, common-edge and     */
+  int g_edge;        /* common-vertex pairs; 0 = use g_singular (0)                          */
+  int g_vertex;
+  int bsr_chunk;     /* blocks per warp in the block-sparse products; 0 = 32                 */
   int precision;     /* enum bembel_precision (FP64)                                         */
   void* stream;      /* cudaStream_t used by every call on the operator (NULL: default)      */
 } bembel_opts;
@@ -138,8 +142,20 @@ typedef struct {
   double solve_ms;       /* host wall time of the call                            */
 } bembel_solve_info;
 
-/* Defaults: eta 1.6, leaf_level -1, g_regular 4, g_singular 5, FP64, stream NULL. */
+/* Defaults: eta 1.6, leaf_level -1, g_regular 4, g_singular 5 (no per-class overrides),
+ * FP64, stream NULL. */
 void bembel_opts_default(bembel_opts* o);
+/* Result of bembel_autotune: chosen orders and the estimated errors at them. */
+typedef struct {
+  int g_regular, g_identical, g_edge, g_vertex;  /* Gauss points per variable               */
+  int q;                                          /* interpolation points per direction      */
+  int bsr_chunk;                                  /* fastest chunk of the block products     */
+  double err_regular, err_identical, err_edge, err_vertex; /* max relative block error, sample */
+  double err_far;                                 /* relative error of sampled far blocks    */
+  double chunk_ms[5];                             /* FP64 matvec ms for chunks 8..128         */
+  double tune_ms;                                 /* host wall time of the call              */
+} bembel_tune_report;
+
 /* Defaults: tol 1e-8, restart 30, max_iter 1000, NONE, refine 1. */
 void bembel_solve_opts_default(bembel_solve_opts* o);
 
@@ -173,6 +189,22 @@ int bembel_geom_destroy(bembel_geom* g);
 int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q,
                     const bembel_opts* o, bembel_op** out);
 int bembel_op_destroy(bembel_op* op);
+
+/* Choose quadrature orders, the interpolation order q and the block-product
+ * chunk for an operator (the paper fixes none of them).  For each pair kind
+ * (separated near pairs, identical, common edge, common vertex) a sample of the
+ * kind's element pairs is integrated on the device at Gauss orders 2, 3, ...
+ * against order 10; the first order with worst relative block difference
+ * <= quad_tol is chosen.  q is the smallest in [2, q_max] for which sampled
+ * leaf-level far blocks V K V^T (Sec. 2 interpolation) differ from a converged
+ * Gauss integration by <= far_tol (relative Frobenius norm).  The chunk is the
+ * fastest of 8..128 for the FP64 matvec.  inout (options used for the sampling
+ * assembly: eta, leaf level, stream) receives g_regular, g_identical, g_edge,
+ * g_vertex, g_singular and bsr_chunk; rep (may be NULL) receives the choices,
+ * q and the error estimates.  Assembles and releases one operator internally.
+ * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED. */
+int bembel_autotune(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
+                    double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep);
 
 /* Number of global dofs (rows = cols of the Galerkin matrix, Sec. 4.5 rows()/cols()). */
 int bembel_ndofs(const bembel_op* op, int64_t* n);

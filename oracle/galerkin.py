@@ -30,15 +30,18 @@ def green(op: str, kappa: complex, x: np.ndarray, y: np.ndarray) -> np.ndarray:
     raise ValueError(op)
 
 
-def pair_rule(kind: str, g_reg: int, g_sing: int):
+def pair_rule(kind: str, g_reg: int, g_sing):
+    """Rule for a pair kind; g_sing is one order for all Duffy rules or a triple
+    (identical, edge, vertex)."""
+    gi, ge, gv = (g_sing, g_sing, g_sing) if isinstance(g_sing, int) else tuple(g_sing)
     if kind == "regular":
         return Q.rule_regular(g_reg)
     if kind == "identical":
-        return Q.rule_identical(g_sing)
+        return Q.rule_identical(gi)
     if kind == "edge":
-        return Q.rule_edge(g_sing)
+        return Q.rule_edge(ge)
     if kind == "vertex":
-        return Q.rule_vertex(g_sing)
+        return Q.rule_vertex(gv)
     raise ValueError(kind)
 
 

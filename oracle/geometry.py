@@ -56,3 +56,60 @@ class Sphere6:
             de = 2.0 * e
             cols.append((de - g * np.sum(g * de, axis=-1, keepdims=True)) / n)
         return np.stack(cols, axis=-1)
+
+
+def real_harmonic(l: int, m: int, x: np.ndarray) -> np.ndarray:
+    """Real orthonormal spherical harmonic Y_lm at unit vectors x (..., 3), without the
+    Condon-Shortley phase: N_l|m| P_l^|m|(cos theta) {sqrt2 cos(m phi), 1, sqrt2 sin(|m| phi)}
+    with N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).  scipy's lpmv includes the phase (-1)^m,
+    which is removed here."""
+    from math import factorial
+
+    from scipy.special import lpmv
+
+    x = np.asarray(x, dtype=float)
+    ct = np.clip(x[..., 2], -1.0, 1.0)
+    ph = np.arctan2(x[..., 1], x[..., 0])
+    am = abs(m)
+    norm = np.sqrt((2 * l + 1) / (4 * np.pi) * factorial(l - am) / factorial(l + am))
+    p = (-1) ** am * lpmv(am, l, ct)
+    if m > 0:
+        return np.sqrt(2.0) * norm * p * np.cos(am * ph)
+    if m < 0:
+        return np.sqrt(2.0) * norm * p * np.sin(am * ph)
+    return norm * p
+
+
+class PerturbedSphere(Sphere6):
+    """Radially perturbed sphere r(x) = 1 + amp * sum_{1<=l<=4} a_lm Y_lm(x) on the cube-face
+    patches of Sphere6: gamma = r(x_hat) x_hat with x_hat the Sphere6 point.  Coefficients are
+    ordered (l, m = -l..l), 24 of them."""
+
+    def __init__(self, coeffs, amp: float = 0.1):
+        self.coeffs = np.asarray(coeffs, dtype=float)
+        if self.coeffs.size != 24:
+            raise ValueError("24 coefficients (l = 1..4) expected")
+        self.amp = amp
+
+    def radius(self, xhat: np.ndarray) -> np.ndarray:
+        r = np.ones(xhat.shape[:-1])
+        k = 0
+        for l in range(1, 5):
+            for m in range(-l, l + 1):
+                r = r + self.amp * self.coeffs[k] * real_harmonic(l, m, xhat)
+                k += 1
+        return r
+
+    def eval(self, patch: int, st: np.ndarray) -> np.ndarray:
+        xh = super().eval(patch, st)
+        return xh * self.radius(xh)[..., None]
+
+    def jacobian(self, patch: int, st: np.ndarray, h: float = 1e-6) -> np.ndarray:
+        """Central differences (used only for mass matrices in tests)."""
+        st = np.asarray(st, dtype=float)
+        cols = []
+        for a in range(2):
+            d = np.zeros(2)
+            d[a] = h
+            cols.append((self.eval(patch, st + d) - self.eval(patch, st - d)) / (2 * h))
+        return np.stack(cols, axis=-1)

@@ -27,7 +27,7 @@ EXPORTED = [
     "bembel_opts_default", "bembel_solve_opts_default", "bembel_last_error", "bembel_geom_create",
     "bembel_geom_destroy", "bembel_assemble", "bembel_op_destroy", "bembel_ndofs", "bembel_op_info_get",
     "bembel_matvec", "bembel_rhs", "bembel_solve", "bembel_eval", "bembel_kernel_launches",
-    "bembel_matvec_noalloc",
+    "bembel_matvec_noalloc", "bembel_autotune",
 ]
 
 
@@ -44,6 +44,7 @@ class GeomDesc(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("eta", C.c_double), ("leaf_level", C.c_int), ("g_regular", C.c_int), ("g_singular", C.c_int),
+                ("g_identical", C.c_int), ("g_edge", C.c_int), ("g_vertex", C.c_int), ("bsr_chunk", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p)]
 
 
@@ -53,6 +54,13 @@ class OpInfo(C.Structure):
         "n_pairs_identical", "n_pairs_edge", "n_pairs_vertex", "near_bytes", "far_bytes")] + [
         ("leaf_level", C.c_int), ("q", C.c_int), ("degree", C.c_int), ("level", C.c_int),
         ("assemble_ms", C.c_double), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 8)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("g_regular", C.c_int), ("g_identical", C.c_int), ("g_edge", C.c_int), ("g_vertex", C.c_int),
+                ("q", C.c_int), ("bsr_chunk", C.c_int), ("err_regular", C.c_double), ("err_identical", C.c_double),
+                ("err_edge", C.c_double), ("err_vertex", C.c_double), ("err_far", C.c_double),
+                ("chunk_ms", C.c_double * 5), ("tune_ms", C.c_double)]
 
 
 class SolveOpts(C.Structure):
@@ -93,6 +101,7 @@ def lib():
     L.bembel_op_info_get.argtypes = [vp, C.POINTER(OpInfo)]
     L.bembel_matvec.argtypes = [vp, vp, vp, ci, ci]
     L.bembel_matvec_noalloc.argtypes = [vp, vp, vp, ci, ci]
+    L.bembel_autotune.argtypes = [vp, ci, dbl, dbl, ci, ci, dbl, dbl, ci, C.POINTER(Opts), C.POINTER(TuneReport)]
     L.bembel_rhs.argtypes = [vp, ci, C.POINTER(dbl), ci, ci, vp]
     L.bembel_solve.argtypes = [vp, vp, vp, ci, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]
     L.bembel_eval.argtypes = [vp, vp, i64, vp, ci, ci, vp]
@@ -183,6 +192,21 @@ def bembel_assemble(geom: Geometry, op: int, k: complex, level: int, p: int, q: 
     k = complex(k)
     _check(lib().bembel_assemble(geom.handle, op, k.real, k.imag, level, p, q, C.byref(o), C.byref(h)))
     return Operator(h, geom, op)
+
+
+def bembel_autotune(geom: Geometry, op: int, k: complex, level: int, p: int, quad_tol: float = 1e-8,
+                    far_tol: float = 1e-5, q_max: int = 8, opts: Opts | None = None, **overrides):
+    """Returns (options with the chosen orders, report dict incl. the chosen q)."""
+    o = opts if opts is not None else bembel_opts_default()
+    for key, v in overrides.items():
+        setattr(o, key, v)
+    rep = TuneReport()
+    k = complex(k)
+    _check(lib().bembel_autotune(geom.handle, op, k.real, k.imag, level, p, quad_tol, far_tol, q_max, C.byref(o),
+                                 C.byref(rep)))
+    out = {f: getattr(rep, f) for f, _ in TuneReport._fields_}
+    out["chunk_ms"] = list(rep.chunk_ms)
+    return o, out
 
 
 def bembel_ndofs(op: Operator) -> int:

@@ -1,0 +1,260 @@
+// autotune.cu - choice of quadrature orders, interpolation order and block-
+// sparse chunk size for a target accuracy (the paper states none of them).
+//
+// * Quadrature: for each pair kind (separated near, identical, common edge,
+//   common vertex) a sample of that kind's element pairs is integrated on the
+//   device at increasing Gauss orders and at a reference order; the smallest
+//   order whose worst relative block difference is <= quad_tol is chosen.
+// * Interpolation: leaf-level far blocks are sampled; the H^2 block V K V^T
+//   (Sec. 2, kernel interpolated at q x q Chebyshev points per cluster) is
+//   compared on the host with a converged tensor-Gauss integration of the same
+//   element pairs; the smallest q with relative error <= far_tol is chosen.
+// * Chunk size of the block-sparse products: the fastest of a few by timing.
+#include <chrono>
+#include <complex>
+#include <vector>
+
+#include "op.h"
+
+namespace bembel {
+
+namespace {
+
+using cplx = std::complex<double>;
+
+cplx green_h(const Op& o, const double* x, const double* y) {
+  const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  const double r = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  if (!o.cplx) return cplx(kInv4Pi / r, 0.0);
+  const cplx kap(o.kre, o.kim);
+  return std::exp(cplx(0.0, -1.0) * kap * r) * (kInv4Pi / r);
+}
+
+// element e -> patch parameters of its local point u
+void elem_point(const Op& o, int64_t e, double u1, double u2, double x[3]) {
+  const int64_t per = int64_t(1) << (2 * o.L);
+  uint32_t i1, i2;
+  morton_decode(uint32_t(e % per), i1, i2);
+  gamma_eval(o.geom, int(e / per), (i1 + u1) * o.h, (i2 + u2) * o.h, x);
+}
+
+// Relative Frobenius error of V K V^T against Gauss integration for sampled
+// leaf-level far blocks, interpolation order q.
+double far_error(const Op& o, int q, const std::vector<std::pair<int, int>>& blocks) {
+  const int d = o.d, D1 = d + 1, nloc = o.nloc, m = o.m, m2 = m * m, nld = m2 * nloc, q2 = q * q;
+  // leaf moments V (nld x q2), as in the operator set-up
+  std::vector<double> gx, gw;
+  gauss01(d + q, gx, gw);
+  std::vector<double> M1((size_t)m * D1 * q);
+  for (int me = 0; me < m; ++me)
+    for (int k = 0; k <= d; ++k)
+      for (int a = 0; a < q; ++a) {
+        double acc = 0.0;
+        for (size_t p = 0; p < gx.size(); ++p)
+          acc += gw[p] * bernstein_h(d, k, gx[p]) * lagrange01(q, a, (me + gx[p]) / m);
+        M1[((size_t)me * D1 + k) * q + a] = acc;
+      }
+  std::vector<double> V((size_t)nld * q2);
+  for (int pe = 0; pe < m2; ++pe) {
+    uint32_t e1, e2;
+    morton_decode(pe, e1, e2);
+    for (int k2 = 0; k2 <= d; ++k2)
+      for (int k1 = 0; k1 <= d; ++k1)
+        for (int a2 = 0; a2 < q; ++a2)
+          for (int a1 = 0; a1 < q; ++a1)
+            V[(size_t)(pe * nloc + k1 + D1 * k2) * q2 + a1 + q * a2] =
+                o.h * o.h * M1[((size_t)e1 * D1 + k1) * q + a1] * M1[((size_t)e2 * D1 + k2) * q + a2];
+  }
+  // converged reference: tensor Gauss with 8 points per direction per element
+  const int G = 8;
+  std::vector<double> rx, rw;
+  gauss01(G, rx, rw);
+  const int64_t leaf_off = o.lvl_off[o.leaf];
+  const int64_t nper = int64_t(1) << (2 * o.leaf);
+  const double H = std::ldexp(1.0, -o.leaf);
+  double worst = 0.0;
+  for (const auto& bl : blocks) {
+    const int64_t t = bl.first - leaf_off, sc = bl.second - leaf_off;
+    // coupling K at the cluster Chebyshev points
+    std::vector<double> xt((size_t)q2 * 3), xs((size_t)q2 * 3);
+    for (int side = 0; side < 2; ++side) {
+      const int64_t c = side == 0 ? t : sc;
+      uint32_t j1, j2;
+      morton_decode(uint32_t(c % nper), j1, j2);
+      for (int a2 = 0; a2 < q; ++a2)
+        for (int a1 = 0; a1 < q; ++a1)
+          gamma_eval(o.geom, int(c / nper), (j1 + chebyshev01(q, a1)) * H, (j2 + chebyshev01(q, a2)) * H,
+                     &(side == 0 ? xt : xs)[(size_t)(a1 + q * a2) * 3]);
+    }
+    std::vector<cplx> K((size_t)q2 * q2);
+    for (int a = 0; a < q2; ++a)
+      for (int b = 0; b < q2; ++b) K[(size_t)a * q2 + b] = green_h(o, &xt[a * 3], &xs[b * 3]);
+    // approx = V K V^T
+    std::vector<cplx> VK((size_t)nld * q2, cplx(0.0));
+    for (int i = 0; i < nld; ++i)
+      for (int a = 0; a < q2; ++a)
+        for (int b = 0; b < q2; ++b) VK[(size_t)i * q2 + b] += V[(size_t)i * q2 + a] * K[(size_t)a * q2 + b];
+    double num = 0.0, den = 0.0;
+    for (int pe = 0; pe < m2; ++pe)
+      for (int pf = 0; pf < m2; ++pf) {
+        const int64_t e = t * m2 + pe, f = sc * m2 + pf;
+        std::vector<double> X((size_t)G * G * 3), Y((size_t)G * G * 3), B((size_t)G * G * nloc);
+        for (int p2 = 0; p2 < G; ++p2)
+          for (int p1 = 0; p1 < G; ++p1) {
+            elem_point(o, e, rx[p1], rx[p2], &X[(size_t)(p1 + G * p2) * 3]);
+            elem_point(o, f, rx[p1], rx[p2], &Y[(size_t)(p1 + G * p2) * 3]);
+            for (int k2 = 0; k2 <= d; ++k2)
+              for (int k1 = 0; k1 <= d; ++k1)
+                B[(size_t)(p1 + G * p2) * nloc + k1 + D1 * k2] = rw[p1] * rw[p2] * o.h * o.h *
+                                                                  bernstein_h(d, k1, rx[p1]) *
+                                                                  bernstein_h(d, k2, rx[p2]);
+          }
+        std::vector<cplx> ex((size_t)nloc * nloc, cplx(0.0));
+        for (int pp = 0; pp < G * G; ++pp)
+          for (int qq = 0; qq < G * G; ++qq) {
+            const cplx gv = green_h(o, &X[(size_t)pp * 3], &Y[(size_t)qq * 3]);
+            for (int i = 0; i < nloc; ++i)
+              for (int j = 0; j < nloc; ++j)
+                ex[(size_t)i * nloc + j] += gv * B[(size_t)pp * nloc + i] * B[(size_t)qq * nloc + j];
+          }
+        for (int i = 0; i < nloc; ++i)
+          for (int j = 0; j < nloc; ++j) {
+            cplx ap(0.0);
+            const int ri = pe * nloc + i, cj = pf * nloc + j;
+            for (int b = 0; b < q2; ++b) ap += VK[(size_t)ri * q2 + b] * V[(size_t)cj * q2 + b];
+            num += std::norm(ap - ex[(size_t)i * nloc + j]);
+            den += std::norm(ex[(size_t)i * nloc + j]);
+          }
+      }
+    if (den > 0) worst = std::max(worst, std::sqrt(num / den));
+  }
+  return worst;
+}
+
+}  // namespace
+
+}  // namespace bembel
+
+namespace bembel {
+
+int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
+                               double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!g || !inout || !(quad_tol > 0) || !(far_tol > 0) || q_max < 2 || q_max > kMaxQ)
+    fail(BEMBEL_EINVAL, "autotune: NULL argument, non-positive tolerance or q_max outside [2, 8]");
+  bembel_opts o = *inout;
+  o.precision = BEMBEL_PREC_FP64;
+  bembel_op* handle = nullptr;
+  // sampling operator: interpolation order 2 keeps the coupling store small;
+  // the block partition does not depend on q
+  const int rc = bembel_assemble(g, op, k_re, k_im, level, p, 2, &o, &handle);
+  if (rc != BEMBEL_OK) fail(rc, std::string("autotune: ") + bembel_last_error());
+  Op& opr = *reinterpret_cast<Op*>(handle);
+  bembel_tune_report r{};
+  try {
+    // quadrature orders per kind
+    const int kinds[4] = {kRegular, kIdentical, kEdge, kVertex};
+    int chosen[4] = {o.g_regular, o.g_singular, o.g_singular, o.g_singular};
+    double errs[4] = {0, 0, 0, 0};
+    for (int ki = 0; ki < 4; ++ki) {
+      const int kind = kinds[ki];
+      if (opr.npairs[kind] == 0) continue;
+      const int g_ref = kMaxG;
+      int best = kMaxG - 1;
+      double err_best = 0.0;
+      for (int gg = 2; gg < g_ref; ++gg) {
+        const double e = sample_pair_error(opr, kind, gg, g_ref, kind == kRegular ? 4096 : 512);
+        best = gg;
+        err_best = e;
+        if (e <= quad_tol) break;
+      }
+      chosen[ki] = best;
+      errs[ki] = err_best;
+    }
+    // interpolation order from sampled leaf-level far blocks
+    int q_best = q_max;
+    double far_err = 0.0;
+    {
+      std::vector<long long> ptr(opr.nclusters + 1);
+      cuda_check(cudaMemcpy(ptr.data(), opr.d_far_ptr, sizeof(long long) * ptr.size(), cudaMemcpyDeviceToHost),
+                 "far ptr");
+      std::vector<int> src(opr.nfar);
+      if (opr.nfar > 0)
+        cuda_check(cudaMemcpy(src.data(), opr.d_far_src, sizeof(int) * opr.nfar, cudaMemcpyDeviceToHost), "far src");
+      std::vector<std::pair<int, int>> blocks;
+      const int64_t leaf_off = opr.lvl_off[opr.leaf];
+      const int64_t nleaf = opr.nleaf;
+      for (int64_t k = 0; k < 32; ++k) {
+        const int64_t t = leaf_off + (k * 7919) % nleaf;
+        const long long n = ptr[t + 1] - ptr[t];
+        if (n == 0) continue;
+        blocks.push_back({int(t), src[ptr[t] + (k * 31) % n]});
+      }
+      if (!blocks.empty()) {
+        for (int qq = 2; qq <= q_max; ++qq) {
+          far_err = far_error(opr, qq, blocks);
+          q_best = qq;
+          if (far_err <= far_tol) break;
+        }
+      }
+    }
+    // chunk size of the block-sparse products, by timing FP64 matvecs
+    int best_chunk = 32;
+    {
+      const int C = opr.cplx ? 2 : 1;
+      double* x = static_cast<double*>(dev_alloc(sizeof(double) * opr.ndofs * C));
+      double* y = static_cast<double*>(dev_alloc(sizeof(double) * opr.ndofs * C));
+      cuda_check(cudaMemset(x, 0, sizeof(double) * opr.ndofs * C), "x");
+      cudaEvent_t e0, e1;
+      cuda_check(cudaEventCreate(&e0), "event");
+      cuda_check(cudaEventCreate(&e1), "event");
+      float best_ms = 1e30f;
+      const int cands[5] = {8, 16, 32, 64, 128};
+      for (int ci = 0; ci < 5; ++ci) {
+        opr.bsr_chunk = cands[ci];
+        matvec_device(opr, x, y, 1, false, opr.stream);
+        cuda_check(cudaEventRecord(e0, opr.stream), "event");
+        for (int it = 0; it < 5; ++it) matvec_device(opr, x, y, 1, false, opr.stream);
+        cuda_check(cudaEventRecord(e1, opr.stream), "event");
+        cuda_check(cudaEventSynchronize(e1), "event");
+        float ms = 0.f;
+        cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+        r.chunk_ms[ci] = ms / 5;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_chunk = cands[ci];
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      dev_free(x);
+      dev_free(y);
+    }
+    inout->g_regular = chosen[0];
+    inout->g_identical = chosen[1];
+    inout->g_edge = chosen[2];
+    inout->g_vertex = chosen[3];
+    inout->g_singular = std::max(chosen[1], std::max(chosen[2], chosen[3]));
+    inout->bsr_chunk = best_chunk;
+    r.g_regular = chosen[0];
+    r.g_identical = chosen[1];
+    r.g_edge = chosen[2];
+    r.g_vertex = chosen[3];
+    r.q = q_best;
+    r.bsr_chunk = best_chunk;
+    r.err_regular = errs[0];
+    r.err_identical = errs[1];
+    r.err_edge = errs[2];
+    r.err_vertex = errs[3];
+    r.err_far = far_err;
+  } catch (...) {
+    bembel_op_destroy(handle);  // release the sampling operator, then report the error
+    throw;
+  }
+  bembel_op_destroy(handle);
+  r.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (rep) *rep = r;
+  return BEMBEL_OK;
+}
+
+}  // namespace bembel

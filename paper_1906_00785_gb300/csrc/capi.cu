@@ -141,6 +141,10 @@ void bembel_opts_default(bembel_opts* o) {
   o->leaf_level = -1;
   o->g_regular = 4;
   o->g_singular = 5;
+  o->g_identical = 0;
+  o->g_edge = 0;
+  o->g_vertex = 0;
+  o->bsr_chunk = 0;
   o->precision = BEMBEL_PREC_FP64;
   o->stream = nullptr;
 }
@@ -208,6 +212,8 @@ int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level,
     if (o) opts = *o;
     if (opts.g_regular < 1 || opts.g_regular > kMaxG || opts.g_singular < 1 || opts.g_singular > kMaxG)
       fail(BEMBEL_EINVAL, "assemble: Gauss orders must be in [1, 10]");
+    for (int gk : {opts.g_identical, opts.g_edge, opts.g_vertex})
+      if (gk < 0 || gk > kMaxG) fail(BEMBEL_EINVAL, "assemble: per-class Gauss orders must be in [0, 10]");
     if (opts.precision != BEMBEL_PREC_FP64 && opts.precision != BEMBEL_PREC_MIXED)
       fail(BEMBEL_EINVAL, "assemble: unknown precision");
     if (q > 0 && !(opts.eta > 0)) fail(BEMBEL_EINVAL, "assemble: eta must be positive");
@@ -225,7 +231,12 @@ int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level,
     res->opts = opts;
     res->g_reg = opts.g_regular;
     res->g_sing = opts.g_singular;
+    res->g_kind[kIdentical] = opts.g_identical > 0 ? opts.g_identical : opts.g_singular;
+    res->g_kind[kEdge] = opts.g_edge > 0 ? opts.g_edge : opts.g_singular;
+    res->g_kind[kVertex] = opts.g_vertex > 0 ? opts.g_vertex : opts.g_singular;
     res->stream = static_cast<cudaStream_t>(opts.stream);
+    if (opts.bsr_chunk < 0 || opts.bsr_chunk > 4096) fail(BEMBEL_EINVAL, "assemble: bsr_chunk must be in [0, 4096]");
+    res->bsr_chunk = opts.bsr_chunk > 0 ? opts.bsr_chunk : 32;
     int dev = 0;
     debug_mark("assemble: cudaGetDevice");
     cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -301,6 +312,11 @@ int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, i
     matvec_noalloc(*o, x_dev, y_dev, nrhs, fp32 != 0, o->stream);
     return BEMBEL_OK;
   });
+}
+
+int bembel_autotune(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
+                    double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep) {
+  return guarded([&] { return autotune_impl(g, op, k_re, k_im, level, p, quad_tol, far_tol, q_max, inout, rep); });
 }
 
 int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, int g, void* b_dev) {

@@ -480,9 +480,8 @@ __global__ void k_down_subtree(const T* __restrict__ yh, T* __restrict__ yl, con
 
 template <typename T, bool CPLX, bool ONFLY>
 void launch_bsr(const int* tgt, const int* src, int64_t nblk, const T* M, const float* pts, float kre, float kim,
-                const T* x, T* y, int bs, int nrhs, cudaStream_t s) {
+                const T* x, T* y, int bs, int nrhs, cudaStream_t s, int chunk) {
   if (nblk == 0) return;
-  const int chunk = 32;
   const int64_t warps = (nblk + chunk - 1) / chunk;
   const int threads = 256;
   const int grid = int((warps * 32 + threads - 1) / threads);
@@ -551,15 +550,15 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     if (o.cplx) {
       if (fp32)
         launch_bsr<T, true, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, float(o.kre),
-                                  float(o.kim), xh, yh, q2, nrhs, s);
+                                  float(o.kim), xh, yh, q2, nrhs, s, o.bsr_chunk);
       else
-        launch_bsr<T, true, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s);
+        launch_bsr<T, true, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s, o.bsr_chunk);
     } else {
       if (fp32)
         launch_bsr<T, false, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, 0.f, 0.f, xh, yh, q2,
-                                   nrhs, s);
+                                   nrhs, s, o.bsr_chunk);
       else
-        launch_bsr<T, false, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s);
+        launch_bsr<T, false, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s, o.bsr_chunk);
     }
     if (fused) {
       for (int l = 1; l <= ls; ++l) {
@@ -588,9 +587,9 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     cuda_check(cudaMemsetAsync(yl, 0, sizeof(T) * o.nlocal * ncol, s), "yl clear");
   }
   if (o.cplx)
-    launch_bsr<T, true, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
+    launch_bsr<T, true, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   else
-    launch_bsr<T, false, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
+    launch_bsr<T, false, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   k_scatter<T><<<blocks_for(o.ndofs * ncol, tb), tb, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
   launched("k_scatter");
 }
@@ -690,9 +689,9 @@ void precond_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const
   launched("k_gather");
   cuda_check(cudaMemsetAsync(yl, 0, sizeof(T) * o.nlocal * ncol, s), "yl clear");
   if (o.cplx)
-    launch_bsr<T, true, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
+    launch_bsr<T, true, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   else
-    launch_bsr<T, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s);
+    launch_bsr<T, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   k_scatter<T><<<blocks_for(o.ndofs * ncol, tb), tb, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
   launched("k_scatter");
 }

@@ -74,13 +74,16 @@ struct Op {
 
   // quadrature tabulation (A1)
   int g_reg = 4, g_sing = 5;
+  int g_kind[4] = {4, 5, 5, 5};  // Gauss points per variable per pair kind (regular unused)
   double* d_Xq = nullptr;  // nelem * g_reg^2 * 3
   double* d_BW = nullptr;  // g_reg^2 * nloc: w_p h^2 B_k(u_p)
-  double* d_gauss = nullptr;  // singular rule: g_sing nodes then weights
+  double* d_gauss = nullptr;  // [g_reg nodes] then per singular kind [nodes, weights]
+  int gauss_off[4] = {0, 0, 0, 0};  // offset of each singular kind's table in d_gauss
   double* d_nodes = nullptr;  // nclusters * q2 * 3 cluster interpolation points
   float* d_nodes32 = nullptr; // FP32 copy (x, y, z, 0) per point for the on-the-fly FP32 coupling
 
   // matvec scratch (grown on demand), FP64 and FP32 views share the bytes
+  int bsr_chunk = 32;        // blocks per warp in the block-sparse products
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
 
@@ -99,6 +102,15 @@ struct GeomHandle {
 
 // setup.cu
 void build_structure(Op& o);            // topology, trees, pairs, moments (host) + uploads
+void gauss01(int n, std::vector<double>& x, std::vector<double>& w);  // Gauss-Legendre on [0,1]
+double chebyshev01(int q, int a);
+double lagrange01(int q, int a, double x);
+double bernstein_h(int d, int k, double u);
+// quad.cu: max over a sample of pairs of |B_g - B_ref|_F / |B_ref|_F for one pair kind
+double sample_pair_error(Op& o, int kind, int g, int g_ref, int max_pairs);
+// autotune.cu
+int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
+                  double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep);
 // quad.cu
 void run_assembly_kernels(Op& o);       // tabulation, near field, coupling
 // h2mv.cu

@@ -13,6 +13,8 @@
 //   in duffy_point().
 // * k_coupling: far-field coupling K_ab = G(gamma(x_a^tau), gamma(x_b^sigma))
 //   at the cluster Chebyshev points (Sec. 2, interpolation on the unit square).
+#include <vector>
+
 #include "op.h"
 
 namespace bembel {
@@ -346,23 +348,26 @@ void launch_pairs(Op& o, cudaEvent_t* ev) {
     launched("k_near_regular");
   }
   cuda_check(cudaEventRecord(ev[2], s), "event");
-  const double* gs = o.d_gauss + o.g_reg;
+
   auto grid_of = [](int64_t n) { return int(std::min<int64_t>((n + kWarps - 1) / kWarps, 152 * 64)); };
   if (o.npairs[kIdentical] > 0) {
     k_near_singular<D, CPLX, kIdentical><<<grid_of(o.npairs[kIdentical]), threads, 0, s>>>(
-        o.d_pairs[kIdentical], o.npairs[kIdentical], o.geom, o.L, o.g_sing, gs, o.kre, o.kim, o.d_N, o.nld);
+        o.d_pairs[kIdentical], o.npairs[kIdentical], o.geom, o.L, o.g_kind[kIdentical], o.d_gauss + o.gauss_off[kIdentical], o.kre,
+        o.kim, o.d_N, o.nld);
     launched("k_near_singular identical");
   }
   cuda_check(cudaEventRecord(ev[3], s), "event");
   if (o.npairs[kEdge] > 0) {
     k_near_singular<D, CPLX, kEdge><<<grid_of(o.npairs[kEdge]), threads, 0, s>>>(
-        o.d_pairs[kEdge], o.npairs[kEdge], o.geom, o.L, o.g_sing, gs, o.kre, o.kim, o.d_N, o.nld);
+        o.d_pairs[kEdge], o.npairs[kEdge], o.geom, o.L, o.g_kind[kEdge], o.d_gauss + o.gauss_off[kEdge], o.kre,
+        o.kim, o.d_N, o.nld);
     launched("k_near_singular edge");
   }
   cuda_check(cudaEventRecord(ev[4], s), "event");
   if (o.npairs[kVertex] > 0) {
     k_near_singular<D, CPLX, kVertex><<<grid_of(o.npairs[kVertex]), threads, 0, s>>>(
-        o.d_pairs[kVertex], o.npairs[kVertex], o.geom, o.L, o.g_sing, gs, o.kre, o.kim, o.d_N, o.nld);
+        o.d_pairs[kVertex], o.npairs[kVertex], o.geom, o.L, o.g_kind[kVertex], o.d_gauss + o.gauss_off[kVertex], o.kre,
+        o.kim, o.d_N, o.nld);
     launched("k_near_singular vertex");
   }
   cuda_check(cudaEventRecord(ev[5], s), "event");
@@ -428,6 +433,117 @@ void run_assembly_kernels(Op& o) {
   }
   o.info.phase_ms[7] = 0.0;
   for (auto& e : ev) cudaEventDestroy(e);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner support: integrate a sample of pairs of one kind at order g and at a
+// reference order g_ref into compact blocks and return the largest relative
+// Frobenius difference over the sample.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int D, bool CPLX>
+void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, int g, double* out) {
+  const cudaStream_t s = o.stream;
+  const int nloc = (D + 1) * (D + 1);
+  std::vector<double> gx, gw;
+  gauss01(g, gx, gw);
+  std::vector<double> tab(gx);
+  tab.insert(tab.end(), gw.begin(), gw.end());
+  double* d_tab = static_cast<double*>(dev_alloc(sizeof(double) * tab.size()));
+  cuda_check(cudaMemcpy(d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice), "tab");
+  const int threads = 32 * kWarps;
+  const int grid = int(std::min<int64_t>((ns + kWarps - 1) / kWarps, 152 * 64));
+  if (kind == kRegular) {
+    const int G2 = g * g;
+    double* Xq = static_cast<double*>(dev_alloc(sizeof(double) * o.nelem * G2 * 3));
+    std::vector<double> BW((size_t)G2 * nloc);
+    for (int p2 = 0; p2 < g; ++p2)
+      for (int p1 = 0; p1 < g; ++p1)
+        for (int k2 = 0; k2 <= D; ++k2)
+          for (int k1 = 0; k1 <= D; ++k1)
+            BW[(size_t)(p1 + g * p2) * nloc + k1 + (D + 1) * k2] =
+                gw[p1] * gw[p2] * o.h * o.h * bernstein_h(D, k1, gx[p1]) * bernstein_h(D, k2, gx[p2]);
+    double* d_BW = static_cast<double*>(dev_alloc(sizeof(double) * BW.size()));
+    cuda_check(cudaMemcpy(d_BW, BW.data(), sizeof(double) * BW.size(), cudaMemcpyHostToDevice), "BW");
+    k_tabulate<<<grid_for(o.nelem * G2, 256), 256, 0, s>>>(o.geom, o.L, o.nelem, g, d_tab, o.h, Xq);
+    launched("k_tabulate");
+    const size_t shm = sizeof(double) * (G2 * nloc + kWarps * G2 * nloc * (CPLX ? 2 : 1));
+    if (shm > 48 * 1024)
+      cuda_check(cudaFuncSetAttribute(k_near_regular<D, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm)),
+                 "smem attr");
+    k_near_regular<D, CPLX><<<grid, threads, shm, s>>>(d_sample, ns, Xq, d_BW, G2, o.kre, o.kim, out, nloc);
+    launched("k_near_regular");
+    cuda_check(cudaStreamSynchronize(s), "sample sync");
+    dev_free(Xq);
+    dev_free(d_BW);
+  } else if (kind == kIdentical) {
+    k_near_singular<D, CPLX, kIdentical><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g, d_tab, o.kre, o.kim,
+                                                                  out, nloc);
+    launched("k_near_singular");
+  } else if (kind == kEdge) {
+    k_near_singular<D, CPLX, kEdge><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g, d_tab, o.kre, o.kim, out,
+                                                             nloc);
+    launched("k_near_singular");
+  } else {
+    k_near_singular<D, CPLX, kVertex><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g, d_tab, o.kre, o.kim,
+                                                               out, nloc);
+    launched("k_near_singular");
+  }
+  cuda_check(cudaStreamSynchronize(s), "sample sync");
+  dev_free(d_tab);
+}
+
+}  // namespace
+
+double sample_pair_error(Op& o, int kind, int g, int g_ref, int max_pairs) {
+  const int64_t ns = std::min<int64_t>(o.npairs[kind], max_pairs);
+  if (ns == 0) return 0.0;
+  const int C = o.cplx ? 2 : 1;
+  const int nloc = o.nloc;
+  // the first ns pairs of the list (built in parallel, so not ordered by
+  // position), each given a compact output block
+  std::vector<PairRec> all(ns);
+  cuda_check(cudaMemcpy(all.data(), o.d_pairs[kind], sizeof(PairRec) * ns, cudaMemcpyDeviceToHost), "sample");
+  for (int64_t i = 0; i < ns; ++i) {
+    all[i].off1 = i * (long long)nloc * nloc;
+    all[i].off2 = -1;
+  }
+  PairRec* d_sample = static_cast<PairRec*>(dev_alloc(sizeof(PairRec) * ns));
+  cuda_check(cudaMemcpy(d_sample, all.data(), sizeof(PairRec) * ns, cudaMemcpyHostToDevice), "sample up");
+  const size_t nb = (size_t)ns * nloc * nloc * C;
+  double* d_a = static_cast<double*>(dev_alloc(sizeof(double) * nb));
+  double* d_b = static_cast<double*>(dev_alloc(sizeof(double) * nb));
+  auto run = [&](int gg, double* out) {
+    switch (o.d * 2 + (o.cplx ? 1 : 0)) {
+      case 0: run_sample<0, false>(o, kind, d_sample, ns, gg, out); break;
+      case 1: run_sample<0, true>(o, kind, d_sample, ns, gg, out); break;
+      case 2: run_sample<1, false>(o, kind, d_sample, ns, gg, out); break;
+      case 3: run_sample<1, true>(o, kind, d_sample, ns, gg, out); break;
+      case 4: run_sample<2, false>(o, kind, d_sample, ns, gg, out); break;
+      default: run_sample<2, true>(o, kind, d_sample, ns, gg, out); break;
+    }
+  };
+  run(g, d_a);
+  run(g_ref, d_b);
+  std::vector<double> a(nb), b(nb);
+  cuda_check(cudaMemcpy(a.data(), d_a, sizeof(double) * nb, cudaMemcpyDeviceToHost), "sample down");
+  cuda_check(cudaMemcpy(b.data(), d_b, sizeof(double) * nb, cudaMemcpyDeviceToHost), "sample down");
+  dev_free(d_sample);
+  dev_free(d_a);
+  dev_free(d_b);
+  double worst = 0.0;
+  const size_t per = (size_t)nloc * nloc * C;
+  for (int64_t i = 0; i < ns; ++i) {
+    double num = 0.0, den = 0.0;
+    for (size_t k = 0; k < per; ++k) {
+      const double dd = a[i * per + k] - b[i * per + k];
+      num += dd * dd;
+      den += b[i * per + k] * b[i * per + k];
+    }
+    if (den > 0) worst = std::max(worst, std::sqrt(num / den));
+  }
+  return worst;
 }
 
 }  // namespace bembel

@@ -22,8 +22,6 @@
 
 namespace bembel {
 
-namespace {
-
 // Gauss-Legendre rule on [0,1] by Newton iteration on P_n.
 void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
@@ -78,6 +76,8 @@ double bernstein_h(int d, int k, double u) {
   for (int i = 0; i < k; ++i) c = c * (d - i) / (i + 1);
   return c * std::pow(u, k) * std::pow(1.0 - u, d - k);
 }
+
+namespace {
 
 // Cox-de Boor on the open knot vector of degree d with n_el uniform elements;
 // value of B-spline j at x in [0,1] (x = 1 belongs to the last interval).
@@ -556,10 +556,13 @@ void build_structure(Op& o) {
     std::vector<double> rg;
     gauss01(G, gx, gw);
     rg.insert(rg.end(), gx.begin(), gx.end());
-    gauss01(o.g_sing, gx, gw);
-    rg.insert(rg.end(), gx.begin(), gx.end());
-    rg.insert(rg.end(), gw.begin(), gw.end());
-    o.d_gauss = upload(rg);  // [g_reg nodes][g_sing nodes][g_sing weights]
+    for (int k = kIdentical; k <= kVertex; ++k) {
+      o.gauss_off[k] = int(rg.size());
+      gauss01(o.g_kind[k], gx, gw);
+      rg.insert(rg.end(), gx.begin(), gx.end());
+      rg.insert(rg.end(), gw.begin(), gw.end());
+    }
+    o.d_gauss = upload(rg);  // [g_reg nodes] then per singular kind [nodes][weights]
   }
 
   debug_mark("setup: report");

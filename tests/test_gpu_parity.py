@@ -229,3 +229,53 @@ def test_batched_solve_matches_single(geom):
     Y = torch.empty_like(B)
     bem.bembel_matvec(gop, X, Y, 4)
     assert (torch.linalg.norm(Y - B) / torch.linalg.norm(B)).item() < 1e-9
+
+
+def test_perturbed_sphere_parity():
+    """Perturbed sphere (dense Helmholtz, and H^2 Laplace): the device harmonics vs the oracle's."""
+    from inputs import perturbed_sphere_coeffs
+    from oracle.geometry import PerturbedSphere
+
+    a = perturbed_sphere_coeffs(1000)
+    g = bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=a, amplitude=0.1)
+    geo = PerturbedSphere(a, 0.1)
+    gop = bem.bembel_assemble(g, HEL, 3.0, 2, 1, 0, g_regular=4, g_singular=5)
+    sp = S2Space(geo, 2, 1)
+    A_ref = Assembler(sp, "helmholtz", 3.0, 4, 5).dense()
+    assert rel_err(gpu_matrix(gop, sp.ndofs), A_ref) < 1e-12
+    gop2 = bem.bembel_assemble(g, LAP, 0.0, 3, 0, 3, g_regular=3, g_singular=4, leaf_level=2)
+    sp2 = S2Space(geo, 3, 0)
+    h2 = H2Oracle(sp2, "laplace", q=3, eta=1.6, leaf_level=2, g_reg=3, g_sing=4)
+    info = bem.bembel_op_info_get(gop2)
+    assert info["n_far_blocks"] == len(h2.far) > 0
+    assert rel_err(gpu_matrix(gop2, sp2.ndofs), h2.dense()) < 1e-12
+
+
+def test_per_class_orders_parity(geom):
+    gop = bem.bembel_assemble(geom, LAP, 0.0, 2, 1, 0, g_regular=3, g_singular=4, g_identical=6, g_edge=5,
+                              g_vertex=3)
+    sp = S2Space(Sphere6(), 2, 1)
+    A_ref = Assembler(sp, "laplace", 0.0, 3, (6, 5, 3)).dense()
+    assert rel_err(gpu_matrix(gop, sp.ndofs), A_ref) < 1e-12
+
+
+@pytest.mark.parametrize("op,k,d", [("laplace", 0.0, 1), ("helmholtz", 4.0, 2)])
+def test_autotune_meets_target(geom, op, k, d):
+    """Tuned orders meet the accuracy target: the operator assembled with them
+    differs from a high-order assembly by about the target, and q meets far_tol."""
+    kind = LAP if op == "laplace" else HEL
+    quad_tol, far_tol = 1e-6, 1e-4
+    opts, rep = bem.bembel_autotune(geom, kind, k, 4, d, quad_tol=quad_tol, far_tol=far_tol, q_max=6)
+    for key in ("err_regular", "err_identical", "err_edge", "err_vertex"):
+        assert rep[key] <= quad_tol, rep
+    assert rep["err_far"] <= far_tol and 2 <= rep["q"] <= 6, rep
+    assert all(2 <= opts.__getattribute__(f) <= 9 for f in ("g_regular", "g_identical", "g_edge", "g_vertex"))
+    tuned = bem.bembel_assemble(geom, kind, k, 4, d, 0, opts=opts)
+    ref = bem.bembel_assemble(geom, kind, k, 4, d, 0, g_regular=8, g_singular=8)
+    n = bem.bembel_ndofs(tuned)
+    dt = torch.complex128 if op == "helmholtz" else torch.float64
+    x = torch.from_numpy(random_vector(n, 5, complex_=(op == "helmholtz"))).to(dt).cuda()
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    bem.bembel_matvec(tuned, x, y1, 1)
+    bem.bembel_matvec(ref, x, y2, 1)
+    assert (torch.linalg.norm(y1 - y2) / torch.linalg.norm(y2)).item() < 10 * quad_tol
