@@ -70,11 +70,14 @@ enum bembel_rhs_kind {
 };
 enum bembel_precond_kind {
   BEMBEL_PRECOND_NONE = 0,
-  BEMBEL_PRECOND_BLOCK_JACOBI = 1 /* inverse of the near-field diagonal leaf blocks */
+  BEMBEL_PRECOND_BLOCK_JACOBI = 1, /* M^-1 = E^T D^-1 E, D = near-field diagonal leaf blocks */
+  BEMBEL_PRECOND_LEARNED = 2       /* M^-1 = E^T W D^-1 W E, W from bembel_learned_attach   */
 };
+#define BEMBEL_LEARNED_NPARAM 433  /* parameters of the learned preconditioner's network */
 
 typedef struct bembel_geom bembel_geom;
 typedef struct bembel_op bembel_op;
+typedef struct bembel_learned_set bembel_learned_set;
 
 /* Geometry description (App. D boundary representation; Sec. 4.1 allows
  * arbitrary smooth parametric patch maps).  Host memory; copied by
@@ -251,6 +254,35 @@ int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs,
  * Errors: EINVAL (NULL, nrhs < 1, aliasing, scratch too small, fp32 on an FP64
  * operator), ECUDA. */
 int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
+
+/* ---- learned preconditioner (not in the paper: the solver's own extension) ----
+ * M_W^-1 = E^T W D^-1 W E with W = diag(exp(MLP(f_i))) over element-local dofs,
+ * f_i 8 local features (basis position in the element, element position in its
+ * leaf, patch/leaf boundary flags, log element distortion, |kappa| * element
+ * size); MLP 8 -> 16 -> 16 -> 1 with tanh, parameters packed [W1 (16x8, row-
+ * major), b1, W2 (16x16), b2, w3 (16), b3] (BEMBEL_LEARNED_NPARAM floats).
+ * Zero w3, b3 gives W = I, i.e. block-Jacobi.  Trained with the unsupervised
+ * loss sum_s |M_W^-1 A z_s - z_s|^2 / |z_s|^2 on systems the solver generates. */
+
+/* Training data of one operator: builds the block-Jacobi inverses, the dof
+ * features and nsamples pairs (z ~ N(0,1) seeded, A z by the FP64 product), and
+ * keeps only those (the operator may be destroyed afterwards).  1 <= nsamples <= 64. */
+int bembel_learned_collect(bembel_op* op, int nsamples, uint64_t seed, bembel_learned_set** out);
+int bembel_learned_set_destroy(bembel_learned_set* s);
+/* Adam on the loss over all sets, one step per epoch (full batch); params (host,
+ * BEMBEL_LEARNED_NPARAM floats) in/out; loss_history (host, epochs doubles, may
+ * be NULL) receives the mean loss before each step.  Forward and backward run
+ * in this library's kernels. */
+int bembel_learned_train(bembel_learned_set* const* sets, int nsets, int epochs, double lr, float* params,
+                         double* loss_history);
+/* Evaluate the network on the operator's dofs and keep the weights for
+ * bembel_solve with precond = BEMBEL_PRECOND_LEARNED. */
+int bembel_learned_attach(bembel_op* op, const float* params);
+/* Network evaluation on n feature rows (device, n x 8 FP32): weights to w_dev
+ * (device, n); when gw_dev (device, n) is given, grad_host (host, NPARAM) gets
+ * d/dparams of sum_i gw_i w_i.  For checking the kernels. */
+int bembel_mlp_eval(const float* params, const float* feat_dev, int64_t n, const float* gw_dev, float* w_dev,
+                    float* grad_host);
 
 /* Load vectors b_i = int_Gamma g phi_i (Sec. 4.4) for nrhs data functions of
  * the given kind (enum bembel_rhs_kind), with params (host, 3 doubles per rhs).

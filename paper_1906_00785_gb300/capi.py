@@ -21,13 +21,15 @@ BEMBEL_GEOM_SPHERE6, BEMBEL_GEOM_PERTURBED_SPHERE = 0, 1
 BEMBEL_LAPLACE_SL, BEMBEL_HELMHOLTZ_SL, BEMBEL_MAXWELL_SL = 0, 1, 2
 BEMBEL_PREC_FP64, BEMBEL_PREC_MIXED = 0, 1
 BEMBEL_RHS_POINT_SOURCE, BEMBEL_RHS_PLANE_WAVE = 0, 1
-BEMBEL_PRECOND_NONE, BEMBEL_PRECOND_BLOCK_JACOBI = 0, 1
+BEMBEL_PRECOND_NONE, BEMBEL_PRECOND_BLOCK_JACOBI, BEMBEL_PRECOND_LEARNED = 0, 1, 2
+BEMBEL_LEARNED_NPARAM = 433
 
 EXPORTED = [
     "bembel_opts_default", "bembel_solve_opts_default", "bembel_last_error", "bembel_geom_create",
     "bembel_geom_destroy", "bembel_assemble", "bembel_op_destroy", "bembel_ndofs", "bembel_op_info_get",
     "bembel_matvec", "bembel_rhs", "bembel_solve", "bembel_eval", "bembel_kernel_launches",
-    "bembel_matvec_noalloc", "bembel_autotune",
+    "bembel_matvec_noalloc", "bembel_autotune", "bembel_learned_collect", "bembel_learned_set_destroy",
+    "bembel_learned_train", "bembel_learned_attach", "bembel_mlp_eval",
 ]
 
 
@@ -101,6 +103,12 @@ def lib():
     L.bembel_op_info_get.argtypes = [vp, C.POINTER(OpInfo)]
     L.bembel_matvec.argtypes = [vp, vp, vp, ci, ci]
     L.bembel_matvec_noalloc.argtypes = [vp, vp, vp, ci, ci]
+    fp = C.POINTER(C.c_float)
+    L.bembel_learned_collect.argtypes = [vp, ci, C.c_uint64, C.POINTER(vp)]
+    L.bembel_learned_set_destroy.argtypes = [vp]
+    L.bembel_learned_train.argtypes = [C.POINTER(vp), ci, ci, dbl, fp, C.POINTER(dbl)]
+    L.bembel_learned_attach.argtypes = [vp, fp]
+    L.bembel_mlp_eval.argtypes = [fp, vp, i64, vp, vp, fp]
     L.bembel_autotune.argtypes = [vp, ci, dbl, dbl, ci, ci, dbl, dbl, ci, C.POINTER(Opts), C.POINTER(TuneReport)]
     L.bembel_rhs.argtypes = [vp, ci, C.POINTER(dbl), ci, ci, vp]
     L.bembel_solve.argtypes = [vp, vp, vp, ci, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]
@@ -207,6 +215,53 @@ def bembel_autotune(geom: Geometry, op: int, k: complex, level: int, p: int, qua
     out = {f: getattr(rep, f) for f, _ in TuneReport._fields_}
     out["chunk_ms"] = list(rep.chunk_ms)
     return o, out
+
+
+class LearnedSet:
+    """Owning wrapper of a bembel_learned_set handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bembel_learned_set_destroy(self.handle)
+            self.handle = None
+
+
+def bembel_learned_collect(op: Operator, nsamples: int = 4, seed: int = 0) -> LearnedSet:
+    h = C.c_void_p()
+    _check(lib().bembel_learned_collect(op.handle, nsamples, seed, C.byref(h)))
+    return LearnedSet(h)
+
+
+def bembel_learned_train(sets, epochs: int, lr: float, params) -> tuple[np.ndarray, np.ndarray]:
+    """Returns (trained parameters, loss history)."""
+    arr = (C.c_void_p * len(sets))(*[s.handle for s in sets])
+    prm = np.ascontiguousarray(params, dtype=np.float32).copy()
+    hist = np.zeros(epochs)
+    _check(lib().bembel_learned_train(arr, len(sets), epochs, lr, prm.ctypes.data_as(C.POINTER(C.c_float)),
+                                      hist.ctypes.data_as(C.POINTER(C.c_double))))
+    return prm, hist
+
+
+def bembel_learned_attach(op: Operator, params) -> None:
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().bembel_learned_attach(op.handle, prm.ctypes.data_as(C.POINTER(C.c_float))))
+
+
+def bembel_mlp_eval(params, feats, gw=None):
+    """Weights (device tensor) and, with gw, d/dparams of sum gw * weights (numpy)."""
+    import torch
+
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    n = feats.shape[0]
+    w = torch.empty(n, dtype=torch.float32, device=feats.device)
+    grad = np.zeros(BEMBEL_LEARNED_NPARAM, dtype=np.float32)
+    _check(lib().bembel_mlp_eval(prm.ctypes.data_as(C.POINTER(C.c_float)), _ptr(feats), n,
+                                 _ptr(gw) if gw is not None else None, _ptr(w),
+                                 grad.ctypes.data_as(C.POINTER(C.c_float))))
+    return w, grad
 
 
 def bembel_ndofs(op: Operator) -> int:

@@ -46,7 +46,7 @@ void free_op(Op* o) {
   void* ptrs[] = {o->d_far_ptr, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
                   o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_nodes, o->d_scratch, o->d_bj,
-                  o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids};
+                  o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* p : o->d_pairs)
@@ -319,6 +319,47 @@ int bembel_autotune(bembel_geom* g, int op, double k_re, double k_im, int level,
   return guarded([&] { return autotune_impl(g, op, k_re, k_im, level, p, quad_tol, far_tol, q_max, inout, rep); });
 }
 
+int bembel_learned_collect(bembel_op* op, int nsamples, uint64_t seed, bembel_learned_set** out) {
+  return guarded([&] {
+    if (!op || !out || nsamples < 1 || nsamples > 64) fail(BEMBEL_EINVAL, "learned_collect: bad argument");
+    *out = reinterpret_cast<bembel_learned_set*>(learned_collect(*reinterpret_cast<Op*>(op), nsamples, seed));
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_learned_set_destroy(bembel_learned_set* s) {
+  learned_set_free(reinterpret_cast<LearnedSet*>(s));
+  return BEMBEL_OK;
+}
+
+int bembel_learned_train(bembel_learned_set* const* sets, int nsets, int epochs, double lr, float* params,
+                         double* loss_history) {
+  return guarded([&] {
+    if (!sets || nsets < 1 || epochs < 1 || !params || !(lr > 0)) fail(BEMBEL_EINVAL, "learned_train: bad argument");
+    for (int i = 0; i < nsets; ++i)
+      if (!sets[i]) fail(BEMBEL_EINVAL, "learned_train: NULL set");
+    learned_train(reinterpret_cast<LearnedSet* const*>(sets), nsets, epochs, lr, params, loss_history);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_learned_attach(bembel_op* op, const float* params) {
+  return guarded([&] {
+    if (!op || !params) fail(BEMBEL_EINVAL, "learned_attach: NULL argument");
+    learned_attach(*reinterpret_cast<Op*>(op), params);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_mlp_eval(const float* params, const float* feat_dev, int64_t n, const float* gw_dev, float* w_dev,
+                    float* grad_host) {
+  return guarded([&] {
+    if (!params || !feat_dev || !w_dev || n < 1) fail(BEMBEL_EINVAL, "mlp_eval: bad argument");
+    mlp_eval_dev(params, feat_dev, n, gw_dev, w_dev, grad_host);
+    return BEMBEL_OK;
+  });
+}
+
 int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, int g, void* b_dev) {
   return guarded([&] {
     if (!op || !params || !b_dev) fail(BEMBEL_EINVAL, "rhs: NULL argument");
@@ -340,7 +381,8 @@ int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, 
     if (so) o = *so;
     if (o.restart < 1 || o.restart > 200 || o.max_iter < 1 || !(o.tol > 0))
       fail(BEMBEL_EINVAL, "solve: restart in [1, 200], max_iter >= 1, tol > 0 required");
-    if (o.precond != BEMBEL_PRECOND_NONE && o.precond != BEMBEL_PRECOND_BLOCK_JACOBI)
+    if (o.precond != BEMBEL_PRECOND_NONE && o.precond != BEMBEL_PRECOND_BLOCK_JACOBI &&
+        o.precond != BEMBEL_PRECOND_LEARNED)
       fail(BEMBEL_EINVAL, "solve: unknown preconditioner");
     const int rc = solve_gmres(*reinterpret_cast<const Op*>(op), b_dev, x_dev, nrhs, o, info);
     if (rc == BEMBEL_ENOTCONV) g_last_error = "solve: GMRES reached max_iter before the tolerance";

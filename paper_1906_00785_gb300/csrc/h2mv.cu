@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(256) k_bsr_mv1(const int* __restrict__ tgt, co
             if (CPLX) {
               const float rr = r2 * rinv;
               float sn, cs;
-              __sincosf(kre * rr, &sn, &cs);
-              const float am = (kim != 0.f ? __expf(kim * rr) : 1.f) * rinv;
+              sincosf(kre * rr, &sn, &cs);  // full range reduction: kappa r reaches tens
+              const float am = (kim != 0.f ? expf(kim * rr) : 1.f) * rinv;
               const float mr = am * cs, mi = -am * sn;
               ar = fma(T(mr), xx[u], fma(T(-mi), xx[u + 1], ar));
               ai = fma(T(mr), xx[u + 1], fma(T(mi), xx[u], ai));
@@ -687,15 +687,71 @@ void precond_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const
   const int tb = 256;
   k_gather<T><<<blocks_for(o.nlocal * ncol, tb), tb, 0, s>>>(x, xl, o.d_ex, o.L, o.d, o.n1, o.ndofs, o.nlocal, ncol, C);
   launched("k_gather");
+  const bool learned = o.active_precond == BEMBEL_PRECOND_LEARNED && o.d_lw;
+  if (learned) learned_scale_local(o, xl, nrhs, sizeof(T) == 4, s);
   cuda_check(cudaMemsetAsync(yl, 0, sizeof(T) * o.nlocal * ncol, s), "yl clear");
   if (o.cplx)
     launch_bsr<T, true, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   else
     launch_bsr<T, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
+  if (learned) learned_scale_local(o, yl, nrhs, sizeof(T) == 4, s);
   k_scatter<T><<<blocks_for(o.ndofs * ncol, tb), tb, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
   launched("k_scatter");
 }
 }  // namespace
+
+void local_gather(const Op& o, const void* x, void* xl, int nrhs, bool fp32, cudaStream_t s) {
+  const int C = o.cplx ? 2 : 1;
+  const int ncol = nrhs * C;
+  if (fp32)
+    k_gather<float><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(static_cast<const float*>(x),
+                                                                     static_cast<float*>(xl), o.d_ex, o.L, o.d, o.n1,
+                                                                     o.ndofs, o.nlocal, ncol, C);
+  else
+    k_gather<double><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(static_cast<const double*>(x),
+                                                                      static_cast<double*>(xl), o.d_ex, o.L, o.d,
+                                                                      o.n1, o.ndofs, o.nlocal, ncol, C);
+  launched("k_gather");
+}
+
+void local_scatter(const Op& o, const void* yl, void* y, int nrhs, bool fp32, cudaStream_t s) {
+  const int C = o.cplx ? 2 : 1;
+  const int ncol = nrhs * C;
+  if (fp32)
+    k_scatter<float><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(static_cast<const float*>(yl),
+                                                                     static_cast<float*>(y), o.d_ex, o.L, o.d, o.n1,
+                                                                     o.ndofs, ncol, C);
+  else
+    k_scatter<double><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(static_cast<const double*>(yl),
+                                                                      static_cast<double*>(y), o.d_ex, o.L, o.d,
+                                                                      o.n1, o.ndofs, ncol, C);
+  launched("k_scatter");
+}
+
+void blockdiag_apply(const Op& o, const void* Dinv, const void* xl, void* yl, int nrhs, bool fp32, cudaStream_t s) {
+  const int C = o.cplx ? 2 : 1;
+  const size_t el = fp32 ? sizeof(float) : sizeof(double);
+  cuda_check(cudaMemsetAsync(yl, 0, el * o.nlocal * nrhs * C, s), "yl clear");
+  if (fp32) {
+    if (o.cplx)
+      launch_bsr<float, true, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, static_cast<const float*>(Dinv), nullptr,
+                                     0.f, 0.f, static_cast<const float*>(xl), static_cast<float*>(yl), o.nld, nrhs, s,
+                                     o.bsr_chunk);
+    else
+      launch_bsr<float, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, static_cast<const float*>(Dinv), nullptr,
+                                      0.f, 0.f, static_cast<const float*>(xl), static_cast<float*>(yl), o.nld, nrhs,
+                                      s, o.bsr_chunk);
+  } else {
+    if (o.cplx)
+      launch_bsr<double, true, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, static_cast<const double*>(Dinv),
+                                      nullptr, 0.f, 0.f, static_cast<const double*>(xl), static_cast<double*>(yl),
+                                      o.nld, nrhs, s, o.bsr_chunk);
+    else
+      launch_bsr<double, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, static_cast<const double*>(Dinv),
+                                       nullptr, 0.f, 0.f, static_cast<const double*>(xl), static_cast<double*>(yl),
+                                       o.nld, nrhs, s, o.bsr_chunk);
+  }
+}
 
 void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s) {
   if (!o.d_bj) fail(BEMBEL_EINVAL, "block-Jacobi preconditioner not set up");

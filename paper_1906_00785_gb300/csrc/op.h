@@ -92,6 +92,8 @@ struct Op {
   float* d_bj32 = nullptr;
   int* d_diag_blk = nullptr;      // near-field block index of the diagonal block of each leaf
   int* d_leaf_ids = nullptr;      // 0 .. nleaf-1 (target = source list of the block diagonal)
+  float* d_lw = nullptr;          // learned weights per element-local dof (learned.cu)
+  int active_precond = 0;         // preconditioner of the running solve (enum bembel_precond_kind)
 
   bembel_op_info info{};
 };
@@ -122,8 +124,20 @@ void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cu
 size_t matvec_noalloc_limit();
 // y = E^T D^-1 E x (block-Jacobi), uses the matvec scratch
 void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
+// element-local helpers (h2mv.cu): gather E x, scatter E^T y, block-diagonal D^-1 x_loc
+void local_gather(const Op& o, const void* x, void* xl, int nrhs, bool fp32, cudaStream_t s);
+void local_scatter(const Op& o, const void* yl, void* y, int nrhs, bool fp32, cudaStream_t s);
+void blockdiag_apply(const Op& o, const void* Dinv, const void* xl, void* yl, int nrhs, bool fp32, cudaStream_t s);
 // precond.cu
 void precond_setup(Op& o);
+// learned.cu
+struct LearnedSet;
+LearnedSet* learned_collect(Op& src, int ns, unsigned long long seed);
+void learned_train(LearnedSet* const* sets, int nsets, int epochs, double lr, float* params, double* hist);
+void learned_attach(Op& o, const float* params);
+void learned_scale_local(const Op& o, void* yl, int nrhs, bool fp32, cudaStream_t s);
+void mlp_eval_dev(const float* params_host, const float* F, int64_t n, const float* gw, float* W, float* grad_host);
+void learned_set_free(LearnedSet* s);
 // element-local layout: dof-major, nrhs (x2 complex) real columns contiguous
 void gather_to_local(const Op& o, const double* x, double* xl, int nrhs, cudaStream_t s);
 void scatter_to_global(const Op& o, const double* yl, double* y, int nrhs, cudaStream_t s);

@@ -571,8 +571,11 @@ int solve_gmres(const Op& o, const void* bv, void* xv, int nrhs, const bembel_so
     cuda_check(cudaStreamWaitEvent(s, e, 0), "wait");
     cudaEventDestroy(e);
   }
-  const bool prec = so.precond == BEMBEL_PRECOND_BLOCK_JACOBI;
+  const bool prec = so.precond == BEMBEL_PRECOND_BLOCK_JACOBI || so.precond == BEMBEL_PRECOND_LEARNED;
   if (prec) precond_setup(const_cast<Op&>(o));
+  if (so.precond == BEMBEL_PRECOND_LEARNED && !o.d_lw)
+    fail(BEMBEL_EINVAL, "solve: the learned preconditioner needs bembel_learned_attach first");
+  const_cast<Op&>(o).active_precond = so.precond;
   const double* b = static_cast<const double*>(bv);
   double* x = static_cast<double*>(xv);
   const int C = o.cplx ? 2 : 1;
@@ -615,8 +618,10 @@ int solve_gmres(const Op& o, const void* bv, void* xv, int nrhs, const bembel_so
       if (worst <= so.tol) break;
       ++refinements;
       // inner tolerance relative to the current residual: what is still
-      // missing to reach tol, but not below what FP32 Krylov vectors resolve
-      const double inner = std::min(0.5, std::max(2e-6, 0.3 * so.tol / worst));
+      // missing to reach tol, but not below what FP32 Krylov vectors and FP32
+      // operator products resolve on ill-conditioned systems (each refinement
+      // step then gains up to four digits)
+      const double inner = std::min(0.5, std::max(1e-4, 0.3 * so.tol / worst));
       std::vector<double> rel_inner;
       iters += o.cplx ? gmres_run<float, true>(o, r, dx, nrhs, inner, so.restart, so.max_iter - iters, prec,
                                                rel_inner, s)
