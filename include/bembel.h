@@ -99,6 +99,7 @@ typedef struct {
   int g_edge;        /* common-vertex pairs; 0 = use g_singular (0)                          */
   int g_vertex;
   int bsr_chunk;     /* blocks per warp in the block-sparse products; 0 = 32                 */
+  int tensor_cores;  /* MIXED, q = 4: coupling for 8..128 right-hand sides on tcgen05 (1)    */
   int precision;     /* enum bembel_precision (FP64)                                         */
   void* stream;      /* cudaStream_t used by every call on the operator (NULL: default)      */
 } bembel_opts;
@@ -146,7 +147,7 @@ typedef struct {
 } bembel_solve_info;
 
 /* Defaults: eta 1.6, leaf_level -1, g_regular 4, g_singular 5 (no per-class overrides),
- * FP64, stream NULL. */
+ * bsr_chunk 32, tensor_cores 1, FP64, stream NULL. */
 void bembel_opts_default(bembel_opts* o);
 /* Result of bembel_autotune: chosen orders and the estimated errors at them. */
 typedef struct {
@@ -224,6 +225,11 @@ int bembel_op_info_get(const bembel_op* op, bembel_op_info* info);
  * float) and the FP32 copies of the near and coupling matrices are used.
  * Errors: EINVAL (NULL, nrhs < 1), ENOMEM, ECUDA. */
 int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
+/* Note: for MIXED operators with q = 4 and tensor_cores = 1, the FP32 product
+ * with 8 <= nrhs (x2 complex) <= 256 real columns, a multiple of 16, evaluates the
+ * far-field coupling on the tensor cores in bf16 with FP32 accumulation
+ * (relative error ~1e-3 of the far-field part); other FP32 products use FP32
+ * CUDA-core arithmetic. */
 
 /* y = A x like bembel_matvec, but without allocating anything.  The paper has
  * no counterpart: this entry point exists for callers that cannot call
@@ -254,6 +260,14 @@ int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs,
  * Errors: EINVAL (NULL, nrhs < 1, aliasing, scratch too small, fp32 on an FP64
  * operator), ECUDA. */
 int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
+
+/* Diagnostic: one tcgen05.mma (M = 128, N = n, K = 16, bf16 operands in the
+ * canonical K-major shared-memory layout used by the tensor-core coupling, FP32
+ * accumulation in TMEM) on exactly representable data, compared with a host
+ * product; *max_abs_err receives the largest difference (0 when the layout and
+ * descriptors are right).  n: multiple of 16 in [16, 256].  The paper has no
+ * counterpart.  Errors: EINVAL, ETIMEOUT (bounded wait expired), ECUDA. */
+int bembel_tc_selftest(int n, double* max_abs_err);
 
 /* ---- learned preconditioner (not in the paper: the solver's own extension) ----
  * M_W^-1 = E^T W D^-1 W E with W = diag(exp(MLP(f_i))) over element-local dofs,

@@ -29,7 +29,7 @@ EXPORTED = [
     "bembel_geom_destroy", "bembel_assemble", "bembel_op_destroy", "bembel_ndofs", "bembel_op_info_get",
     "bembel_matvec", "bembel_rhs", "bembel_solve", "bembel_eval", "bembel_kernel_launches",
     "bembel_matvec_noalloc", "bembel_autotune", "bembel_learned_collect", "bembel_learned_set_destroy",
-    "bembel_learned_train", "bembel_learned_attach", "bembel_mlp_eval",
+    "bembel_learned_train", "bembel_learned_attach", "bembel_mlp_eval", "bembel_tc_selftest",
 ]
 
 
@@ -47,6 +47,7 @@ class GeomDesc(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("eta", C.c_double), ("leaf_level", C.c_int), ("g_regular", C.c_int), ("g_singular", C.c_int),
                 ("g_identical", C.c_int), ("g_edge", C.c_int), ("g_vertex", C.c_int), ("bsr_chunk", C.c_int),
+                ("tensor_cores", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p)]
 
 
@@ -109,6 +110,7 @@ def lib():
     L.bembel_learned_train.argtypes = [C.POINTER(vp), ci, ci, dbl, fp, C.POINTER(dbl)]
     L.bembel_learned_attach.argtypes = [vp, fp]
     L.bembel_mlp_eval.argtypes = [fp, vp, i64, vp, vp, fp]
+    L.bembel_tc_selftest.argtypes = [ci, C.POINTER(dbl)]
     L.bembel_autotune.argtypes = [vp, ci, dbl, dbl, ci, ci, dbl, dbl, ci, C.POINTER(Opts), C.POINTER(TuneReport)]
     L.bembel_rhs.argtypes = [vp, ci, C.POINTER(dbl), ci, ci, vp]
     L.bembel_solve.argtypes = [vp, vp, vp, ci, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]
@@ -262,6 +264,12 @@ def bembel_mlp_eval(params, feats, gw=None):
                                  _ptr(gw) if gw is not None else None, _ptr(w),
                                  grad.ctypes.data_as(C.POINTER(C.c_float))))
     return w, grad
+
+
+def bembel_tc_selftest(n: int) -> float:
+    err = C.c_double()
+    _check(lib().bembel_tc_selftest(n, C.byref(err)))
+    return err.value
 
 
 def bembel_ndofs(op: Operator) -> int:

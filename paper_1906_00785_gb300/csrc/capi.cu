@@ -46,7 +46,8 @@ void free_op(Op* o) {
   void* ptrs[] = {o->d_far_ptr, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
                   o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_nodes, o->d_scratch, o->d_bj,
-                  o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw};
+                  o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
+                  o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt, o->d_tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* p : o->d_pairs)
@@ -145,6 +146,7 @@ void bembel_opts_default(bembel_opts* o) {
   o->g_edge = 0;
   o->g_vertex = 0;
   o->bsr_chunk = 0;
+  o->tensor_cores = 1;
   o->precision = BEMBEL_PREC_FP64;
   o->stream = nullptr;
 }
@@ -356,6 +358,14 @@ int bembel_mlp_eval(const float* params, const float* feat_dev, int64_t n, const
   return guarded([&] {
     if (!params || !feat_dev || !w_dev || n < 1) fail(BEMBEL_EINVAL, "mlp_eval: bad argument");
     mlp_eval_dev(params, feat_dev, n, gw_dev, w_dev, grad_host);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_tc_selftest(int n, double* max_abs_err) {
+  return guarded([&] {
+    if (!max_abs_err) fail(BEMBEL_EINVAL, "tc_selftest: NULL argument");
+    *max_abs_err = tc_selftest(n);
     return BEMBEL_OK;
   });
 }

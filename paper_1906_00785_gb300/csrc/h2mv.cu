@@ -547,7 +547,10 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     }
     cuda_check(cudaMemsetAsync(yh, 0, sizeof(T) * o.nclusters * q2 * ncol, s), "yh clear");
     // FP32: coupling evaluated on the fly from the cluster points; FP64: stored coupling
-    if (o.cplx) {
+    if (fp32 && tc_coupling_usable(o, nrhs)) {
+      // many right-hand sides: sibling-grouped coupling on the tensor cores
+      tc_coupling(o, reinterpret_cast<const float*>(xh), reinterpret_cast<float*>(yh), nrhs, s);
+    } else if (o.cplx) {
       if (fp32)
         launch_bsr<T, true, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, float(o.kre),
                                   float(o.kim), xh, yh, q2, nrhs, s, o.bsr_chunk);

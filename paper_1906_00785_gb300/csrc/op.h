@@ -84,6 +84,14 @@ struct Op {
 
   // matvec scratch (grown on demand), FP64 and FP32 views share the bytes
   int bsr_chunk = 32;        // blocks per warp in the block-sparse products
+  // tensor-core coupling for many right-hand sides (tc_coupling.cu)
+  int* d_tc_gptr = nullptr;        // CSR over sibling-target groups
+  int* d_tc_gsrc = nullptr;        // union of far sources per group
+  unsigned* d_tc_gmask = nullptr;  // which group targets interact with the source
+  int* d_tc_gfirst = nullptr;      // first target of the group
+  int* d_tc_gcnt = nullptr;        // targets in the group
+  int* d_tc_err = nullptr;         // set when a bounded wait timed out
+  int64_t tc_ngroups = 0, tc_nentries = 0;
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
 
@@ -128,6 +136,11 @@ void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cud
 void local_gather(const Op& o, const void* x, void* xl, int nrhs, bool fp32, cudaStream_t s);
 void local_scatter(const Op& o, const void* yl, void* y, int nrhs, bool fp32, cudaStream_t s);
 void blockdiag_apply(const Op& o, const void* Dinv, const void* xl, void* yl, int nrhs, bool fp32, cudaStream_t s);
+// tc_coupling.cu
+bool tc_coupling_usable(const Op& o, int nrhs);
+void tc_coupling(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s);
+void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vector<int>& fsrc);
+double tc_selftest(int N);
 // precond.cu
 void precond_setup(Op& o);
 // learned.cu

@@ -1,0 +1,485 @@
+// tc_coupling.cu - far-field coupling of the H^2 matvec for many right-hand
+// sides on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// For a block of nrhs columns the coupling yh_t = sum_s K_ts xh_s (Sec. 2,
+// kernel interpolated at the cluster Chebyshev points) is a sum of small
+// products (q^2 x q^2) x (q^2 x ncol).  One CTA takes a group of sibling target
+// clusters (8 for real kernels, 4 for complex ones) and walks the sorted union
+// of their far sources.  Per source sigma it builds in shared memory
+//   A (128 x 16, bf16): rows = (target, a) [x (Re, Im) for complex kernels], the
+//       coupling K_t,sigma[a][b] evaluated on the fly in FP32 from the cluster
+//       points, zero rows for group targets that do not interact with sigma;
+//   B (ncol x 16, bf16): the source moments xh_sigma[b][col];
+// and one thread issues tcgen05.mma.kind::f16 (M = 128, N = ncol, K = 16) that
+// accumulates D = A B^T in TMEM (FP32).  The epilogue reads D with tcgen05.ld
+// and writes yh for the group (complex: D_re-row / D_im-row recombined).
+// Operands are double-buffered; a tcgen05.commit per MMA arrives on an
+// mbarrier that guards the buffer's reuse.  Every wait is bounded: on time-out
+// the kernel records an error, drains, frees its TMEM and returns.
+//
+// Shared-memory operands use the canonical K-major layout without swizzling:
+// 8 x 16-byte core matrices, element (row r, k) at byte
+// (r/8)*256 + (k/8)*128 + (r%8)*16 + (k%8)*2 of the tile.
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "op.h"
+
+namespace bembel {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcSmem = 100 * 1024;  // also caps residency at two CTAs per SM (TMEM 2 x 256 columns)
+constexpr long long kSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle, LBO = K-direction core
+// stride, SBO = row-direction core stride (bytes), version 1
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor kind::f16: D f32, A/B bf16, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(m, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* m) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(m))
+               : "memory");
+}
+
+// 32 lanes x 8 consecutive 32-bit columns per thread
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const uint32_t a = __float_as_uint(lo), b = __float_as_uint(hi);
+  // round to nearest even on the upper 16 bits
+  const uint32_t ra = (a + 0x7FFFu + ((a >> 16) & 1u)) >> 16;
+  const uint32_t rb = (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+  return (ra & 0xFFFFu) | (rb << 16);
+}
+
+// write 16 bf16 values (one K = 16 row) of a K-major no-swizzle tile
+__device__ __forceinline__ void store_row16(unsigned char* tile, int row, const float (&v)[16]) {
+  uint4 lo, hi;
+  lo.x = pack_bf16(v[0], v[1]);
+  lo.y = pack_bf16(v[2], v[3]);
+  lo.z = pack_bf16(v[4], v[5]);
+  lo.w = pack_bf16(v[6], v[7]);
+  hi.x = pack_bf16(v[8], v[9]);
+  hi.y = pack_bf16(v[10], v[11]);
+  hi.z = pack_bf16(v[12], v[13]);
+  hi.w = pack_bf16(v[14], v[15]);
+  unsigned char* base = tile + (row >> 3) * 256 + (row & 7) * 16;
+  *reinterpret_cast<uint4*>(base) = lo;
+  *reinterpret_cast<uint4*>(base + 128) = hi;
+}
+
+__device__ __forceinline__ uint32_t tmem_cols_for(int ncol) {
+  uint32_t c = 32;
+  while ((int)c < ncol) c <<= 1;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test: D (128 x N) = A (128 x 16) B^T (B: N x 16), one MMA, one CTA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads) k_tc_selftest(const float* __restrict__ A, const float* __restrict__ B,
+                                                            int N, float* __restrict__ D, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* tA = sm;
+  unsigned char* tB = sm + 4096;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t ncols = tmem_cols_for(N);
+  if (warp == 0) tmem_alloc(&tbase, ncols);
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    float v[16];
+    for (int k = 0; k < 16; ++k) v[k] = A[tid * 16 + k];
+    store_row16(tA, tid, v);
+    for (int n = tid; n < N; n += kTcThreads) {
+      for (int k = 0; k < 16; ++k) v[k] = B[n * 16 + k];
+      store_row16(tB, n, v);
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t d = tbase;
+  if (tid == 0) {
+    mma_bf16(d, make_desc(smem_addr(tA), 128, 256), make_desc(smem_addr(tB), 128, 256), make_idesc(128, N), 0);
+    mma_commit(&mbar);
+  }
+  const bool ok = mbar_wait(&mbar, 0);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  tc_fence_after();
+  __syncthreads();
+  if (ok) {
+    const int row = tid;
+    for (int c0 = 0; c0 < N; c0 += 8) {
+      float v[8];
+      tmem_ld8(d + ((uint32_t)(warp * 32) << 16) + c0, v);
+      for (int i = 0; i < 8; ++i) D[row * N + c0 + i] = v[i];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(d, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Production kernel.
+// ---------------------------------------------------------------------------
+template <bool CPLX>
+__global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restrict__ gptr, const int* __restrict__ gsrc,
+                                                            const unsigned* __restrict__ gmask,
+                                                            const int* __restrict__ gfirst, const int* __restrict__ gcnt,
+                                                            int ngroups, const float4* __restrict__ pts, float kre,
+                                                            float kim, const float* __restrict__ xh,
+                                                            float* __restrict__ yh, int ncol, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* tA[2] = {sm, sm + 4096};
+  unsigned char* tB[2] = {sm + 8192, sm + 8192 + 8192};
+  __shared__ float4 tpt[128];  // target points of the group (rows / (1 + CPLX))
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  constexpr int TG = CPLX ? 4 : 8;  // targets per group
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tmem_cols_for(ncol);
+  if (warp == 0) tmem_alloc(&tbase, ncols);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t d = tbase;
+  const uint32_t idesc = make_idesc(128, ncol);
+  uint32_t phase[2] = {0, 0};
+  int issued[2] = {0, 0};
+  const int row = tid;  // A row owned by this thread
+  const int tslot = CPLX ? (row >> 1) / 16 : row / 16;
+  const int arow = CPLX ? (row >> 1) % 16 : row % 16;
+  const int part = CPLX ? (row & 1) : 0;
+  for (int gi = blockIdx.x; gi < ngroups && !abort_flag; gi += gridDim.x) {
+    const int t0 = gfirst[gi], nt = gcnt[gi];
+    if (tid < TG * 16) tpt[tid] = (tid / 16 < nt) ? pts[(int64_t)(t0 + tid / 16) * 16 + tid % 16] : make_float4(0, 0, 0, 0);
+    __syncthreads();
+    const int e0 = gptr[gi], e1 = gptr[gi + 1];
+    int stage = 0;
+    for (int e = e0; e < e1; ++e, stage ^= 1) {
+      if (issued[stage]) {  // buffer still read by the MMA issued two steps ago
+        if (!mbar_wait(&mbar[stage], phase[stage])) {
+          if (tid == 0) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+          }
+        }
+        phase[stage] ^= 1;
+        issued[stage] = 0;
+      }
+      __syncthreads();
+      if (abort_flag) break;
+      const int sc = gsrc[e];
+      const unsigned mask = gmask[e];
+      // A row: coupling of (target tslot, row a) with the 16 source points
+      {
+        float v[16];
+        const bool on = tslot < nt && ((mask >> tslot) & 1u);
+        const float4 pa = tpt[tslot * 16 + arow];
+        const float4* pb = pts + (int64_t)sc * 16;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          float val = 0.f;
+          if (on) {
+            const float4 p = pb[b];
+            const float d0 = pa.x - p.x, d1 = pa.y - p.y, d2 = pa.z - p.z;
+            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+            const float rinv = rsqrtf(r2) * float(kInv4Pi);
+            if (CPLX) {
+              const float rr = r2 * rsqrtf(r2);
+              float sn, cs;
+              sincosf(kre * rr, &sn, &cs);
+              const float am = (kim != 0.f ? expf(kim * rr) : 1.f) * rinv;
+              val = part == 0 ? am * cs : -am * sn;
+            } else {
+              val = rinv;
+            }
+          }
+          v[b] = val;
+        }
+        store_row16(tA[stage], row, v);
+      }
+      // B rows: source moments, column n, k = b
+      for (int n = tid; n < ncol; n += kTcThreads) {
+        float v[16];
+        const float* xs = xh + (int64_t)sc * 16 * ncol + n;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) v[b] = xs[(int64_t)b * ncol];
+        store_row16(tB[stage], n, v);
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        mma_bf16(d, make_desc(smem_addr(tA[stage]), 128, 256), make_desc(smem_addr(tB[stage]), 128, 256), idesc,
+                 e > e0 ? 1 : 0);
+        mma_commit(&mbar[stage]);
+      }
+      issued[stage] = 1;
+    }
+    // drain both buffers before reading the accumulator
+    for (int st = 0; st < 2; ++st)
+      if (issued[st]) {
+        if (!mbar_wait(&mbar[st], phase[st]) && tid == 0) {
+          atomicExch(err, 1);
+          abort_flag = 1;
+        }
+        phase[st] ^= 1;
+        issued[st] = 0;
+      }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (abort_flag) break;
+    // epilogue: row -> (target, a[, part]); D row = sum over sources
+    const bool have = e1 > e0;
+    for (int c0 = 0; c0 < ncol; c0 += 8) {
+      float v[8];
+      if (have) {
+        tmem_ld8(d + ((uint32_t)(warp * 32) << 16) + c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      }
+      if (!CPLX) {
+        if (tslot < nt) {
+          float* y = yh + ((int64_t)(t0 + tslot) * 16 + arow) * ncol + c0;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) y[i] = v[i];
+        }
+      } else {
+        // partner lane holds the other part of the same (target, a)
+        float w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
+        // columns interleave (re, im) per right-hand side: D_re-row = Kr X', D_im-row = Ki X'
+        // Y_re = Kr x_re - Ki x_im (even columns), Y_im = Kr x_im + Ki x_re (odd columns)
+        if (tslot < nt && part == 0) {
+          float* y = yh + ((int64_t)(t0 + tslot) * 16 + arow) * ncol + c0;
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            y[i] = v[i] - w[i + 1];
+            y[i + 1] = v[i + 1] + w[i];
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  (void)lane;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(d, ncols);
+}
+
+}  // namespace
+
+bool tc_coupling_usable(const Op& o, int nrhs) {
+  const int ncol = nrhs * (o.cplx ? 2 : 1);
+  return o.d_tc_gptr != nullptr && o.q2 == 16 && ncol >= 16 && ncol <= 256 && ncol % 16 == 0;
+}
+
+void tc_coupling(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s) {
+  const int ncol = nrhs * (o.cplx ? 2 : 1);
+  static bool attr_set[2] = {false, false};
+  const int grid = int(std::min<int64_t>(o.tc_ngroups, 152 * 2));
+  if (o.cplx) {
+    if (!attr_set[1]) {
+      cuda_check(cudaFuncSetAttribute(k_coupling_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
+                 "tc smem");
+      attr_set[1] = true;
+    }
+    k_coupling_tc<true><<<grid, kTcThreads, kTcSmem, s>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
+                                                          o.d_tc_gcnt, int(o.tc_ngroups),
+                                                          reinterpret_cast<const float4*>(o.d_nodes32),
+                                                          float(o.kre), float(o.kim), xh, yh, ncol, o.d_tc_err);
+  } else {
+    if (!attr_set[0]) {
+      cuda_check(cudaFuncSetAttribute(k_coupling_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
+                 "tc smem");
+      attr_set[0] = true;
+    }
+    k_coupling_tc<false><<<grid, kTcThreads, kTcSmem, s>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
+                                                           o.d_tc_gcnt, int(o.tc_ngroups),
+                                                           reinterpret_cast<const float4*>(o.d_nodes32), 0.f, 0.f, xh,
+                                                           yh, ncol, o.d_tc_err);
+  }
+  launched("k_coupling_tc");
+}
+
+// Groups of sibling targets and the union of their far sources (host set-up).
+void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vector<int>& fsrc) {
+  const int TG = o.cplx ? 4 : 8;
+  std::vector<int> gptr = {0}, gsrc, gfirst, gcnt;
+  std::vector<unsigned> gmask;
+  for (int l = 0; l <= o.leaf; ++l) {
+    const int64_t t0 = o.lvl_off[l], t1 = o.lvl_off[l + 1];
+    for (int64_t g = t0; g < t1; g += TG) {
+      const int nt = int(std::min<int64_t>(TG, t1 - g));
+      // merge the sorted source lists of the group's targets
+      std::vector<std::pair<int, unsigned>> u;
+      for (int i = 0; i < nt; ++i)
+        for (long long k = fptr[g + i]; k < fptr[g + i + 1]; ++k) u.push_back({fsrc[k], 1u << i});
+      std::sort(u.begin(), u.end());
+      for (size_t k = 0; k < u.size();) {
+        unsigned m = 0;
+        const int sc = u[k].first;
+        while (k < u.size() && u[k].first == sc) m |= u[k++].second;
+        gsrc.push_back(sc);
+        gmask.push_back(m);
+      }
+      gptr.push_back(int(gsrc.size()));
+      gfirst.push_back(int(g));
+      gcnt.push_back(nt);
+    }
+  }
+  o.tc_ngroups = (int64_t)gfirst.size();
+  o.tc_nentries = (int64_t)gsrc.size();
+  auto up = [](const auto& v) {
+    using T = typename std::decay<decltype(v)>::type::value_type;
+    T* p = static_cast<T*>(dev_alloc(sizeof(T) * std::max<size_t>(1, v.size())));
+    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "tc upload");
+    return p;
+  };
+  o.d_tc_gptr = up(gptr);
+  o.d_tc_gsrc = up(gsrc);
+  o.d_tc_gmask = up(gmask);
+  o.d_tc_gfirst = up(gfirst);
+  o.d_tc_gcnt = up(gcnt);
+  o.d_tc_err = static_cast<int*>(dev_alloc(sizeof(int)));
+  cuda_check(cudaMemset(o.d_tc_err, 0, sizeof(int)), "tc err");
+}
+
+double tc_selftest(int N) {
+  if (N < 16 || N > 256 || N % 16) fail(BEMBEL_EINVAL, "tc_selftest: N must be a multiple of 16 in [16, 256]");
+  std::vector<float> A(128 * 16), B((size_t)N * 16);
+  uint32_t st = 12345u;
+  auto rnd = [&]() {
+    st = st * 1664525u + 1013904223u;
+    // values exactly representable in bf16: small integers / 8
+    return float(int((st >> 16) % 17) - 8) / 8.0f;
+  };
+  for (auto& v : A) v = rnd();
+  for (auto& v : B) v = rnd();
+  float *dA, *dB, *dD;
+  int* derr;
+  dA = static_cast<float*>(dev_alloc(sizeof(float) * A.size()));
+  dB = static_cast<float*>(dev_alloc(sizeof(float) * B.size()));
+  dD = static_cast<float*>(dev_alloc(sizeof(float) * 128 * N));
+  derr = static_cast<int*>(dev_alloc(sizeof(int)));
+  cuda_check(cudaMemcpy(dA, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice), "A");
+  cuda_check(cudaMemcpy(dB, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice), "B");
+  cuda_check(cudaMemset(dD, 0, sizeof(float) * 128 * N), "D");
+  cuda_check(cudaMemset(derr, 0, sizeof(int)), "err");
+  cuda_check(cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem), "smem");
+  k_tc_selftest<<<1, kTcThreads, kTcSmem>>>(dA, dB, N, dD, derr);
+  launched("k_tc_selftest");
+  cuda_check(cudaDeviceSynchronize(), "selftest sync");
+  std::vector<float> D((size_t)128 * N);
+  int herr = 0;
+  cuda_check(cudaMemcpy(D.data(), dD, sizeof(float) * D.size(), cudaMemcpyDeviceToHost), "D");
+  cuda_check(cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost), "err");
+  dev_free(dA);
+  dev_free(dB);
+  dev_free(dD);
+  dev_free(derr);
+  if (herr) fail(BEMBEL_ETIMEOUT, "tc_selftest: MMA completion wait timed out");
+  double worst = 0.0;
+  for (int m = 0; m < 128; ++m)
+    for (int n = 0; n < N; ++n) {
+      double ref = 0.0;
+      for (int k = 0; k < 16; ++k) ref += double(A[m * 16 + k]) * B[(size_t)n * 16 + k];
+      worst = std::max(worst, std::fabs(ref - D[(size_t)m * N + n]));
+    }
+  return worst;
+}
+
+}  // namespace bembel

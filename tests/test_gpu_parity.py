@@ -279,3 +279,36 @@ def test_autotune_meets_target(geom, op, k, d):
     bem.bembel_matvec(tuned, x, y1, 1)
     bem.bembel_matvec(ref, x, y2, 1)
     assert (torch.linalg.norm(y1 - y2) / torch.linalg.norm(y2)).item() < 10 * quad_tol
+
+
+def test_sound_soft_scattering_batch(geom):
+    """Sound-soft unit sphere, 6 plane waves solved as one batch (degree 2, q = 4,
+    mixed precision): the scattered field at |x| = 3 against the partial-wave
+    series for the exp(-i k r) convention,
+    u_s = -sum_l (2l+1) (-i)^l j_l(k)/h2_l(k) h2_l(k|x|) P_l(cos angle(x, d))."""
+    import scipy.special as ss
+
+    from inputs import sphere_points, unit_directions
+
+    k = 2.0
+    gop = bem.bembel_assemble(geom, HEL, k, 4, 2, 4, precision=bem.BEMBEL_PREC_MIXED)
+    n = bem.bembel_ndofs(gop)
+    dirs = unit_directions(6, 3)
+    B = torch.empty((6, n), dtype=torch.complex128, device="cuda")
+    bem.bembel_rhs(gop, bem.BEMBEL_RHS_PLANE_WAVE, dirs, B, g=6)
+    B = -B  # Dirichlet data of the scattered field: u_s = -u_inc on the sphere
+    X = torch.empty_like(B)
+    info = bem.bembel_solve(gop, B, X, 6, tol=1e-10, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)
+    assert info["converged"]
+    pts = sphere_points(10, 3.0, 11)
+    U = torch.empty((6, 10), dtype=torch.complex128, device="cuda")
+    bem.bembel_eval(gop, torch.from_numpy(pts).cuda(), X, U, 6, g=6)
+    U = U.cpu().numpy()
+    rr = np.linalg.norm(pts, axis=1)
+    h2 = lambda l, z: ss.spherical_jn(l, z) - 1j * ss.spherical_yn(l, z)  # noqa: E731
+    for r in range(6):
+        c = pts @ dirs[r] / rr
+        ref = np.zeros(10, dtype=complex)
+        for l in range(25):
+            ref += -(2 * l + 1) * (-1j) ** l * ss.spherical_jn(l, k) / h2(l, k) * h2(l, k * rr) * ss.eval_legendre(l, c)
+        assert np.max(np.abs(U[r] - ref)) / np.max(np.abs(ref)) < 1e-4, r
