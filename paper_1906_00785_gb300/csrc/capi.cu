@@ -97,6 +97,8 @@ long long capture_end(cudaStream_t s, cudaGraph_t* g) {
   return t_captured;
 }
 
+bool capturing() { return t_capturing; }
+
 void note_graph_kernels(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void launched(const char* what) {

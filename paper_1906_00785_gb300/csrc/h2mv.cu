@@ -767,6 +767,9 @@ void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cud
 
 void ensure_scratch(Op& o, size_t bytes) {
   if (bytes <= o.scratch_bytes) return;
+  // a captured graph keeps the scratch address: growing it under capture
+  // would leave earlier graphs pointing at freed memory
+  if (capturing()) fail(BEMBEL_ECUDA, "matvec scratch must be reserved before graph capture");
   if (o.d_scratch) {
     cuda_check(cudaStreamSynchronize(o.stream), "scratch sync");
     dev_free(o.d_scratch);

@@ -175,6 +175,8 @@ void debug_mark(const char* what);
 void capture_begin(cudaStream_t s);
 long long capture_end(cudaStream_t s, cudaGraph_t* g);
 void note_graph_kernels(long long n);
+// true between capture_begin and capture_end on this thread
+bool capturing();
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
 

@@ -14,6 +14,7 @@
 // Preconditioning (block-Jacobi) is applied from the right: A M^-1 u = b,
 // x = M^-1 u.
 #include <chrono>
+#include <cmath>
 #include <vector>
 
 #include "op.h"
@@ -21,6 +22,9 @@
 namespace bembel {
 
 namespace {
+
+// max that treats a NaN residual as the worst possible (std::max would drop it)
+inline double worse(double a, double b) { return std::isnan(b) ? HUGE_VAL : (b > a ? b : a); }
 
 inline int nblk(int64_t n, int t) { return int(std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535 * 16))); }
 
@@ -297,17 +301,20 @@ __global__ void k_backsolve(Gm st) {
   }
 }
 
-// z[n, r] = sum_{i < nv} V_i[n, r] y[i][r]   (FP64 output)
+// z[n, r] = sum_{i < jend[r]} V_i[n, r] y[i][r]   (FP64 output).  Only the
+// basis vectors built in this cycle enter: later columns hold stale memory
+// (y is zero there, but 0 * NaN is not).
 template <typename T, bool CPLX>
 __global__ void k_combine(const T* __restrict__ V, int64_t vstride, int nv, double* __restrict__ z, int64_t n,
-                          int nrhs, const cd_t* __restrict__ y) {
+                          int nrhs, const cd_t* __restrict__ y, const int* __restrict__ jend) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= n * nrhs) return;
   const int r = int(id / n);
   const int64_t k = id % n;
   const int C = CPLX ? 2 : 1;
   double ar = 0.0, ai = 0.0;
-  for (int i = 0; i < nv; ++i) {
+  const int nvr = min(nv, jend[r]);
+  for (int i = 0; i < nvr; ++i) {
     const T* v = V + (int64_t)i * vstride + ((int64_t)r * n + k) * C;
     const cd_t c = y[i * nrhs + r];
     if (CPLX) {
@@ -377,7 +384,8 @@ void col_norms(const double* x, int64_t n, int nrhs, cd_t* d_h, std::vector<doub
   cuda_check(cudaMemcpyAsync(h.data(), d_h, sizeof(cd_t) * nrhs, cudaMemcpyDeviceToHost, s), "norm copy");
   cuda_check(cudaStreamSynchronize(s), "norm sync");
   out.resize(nrhs);
-  for (int r = 0; r < nrhs; ++r) out[r] = std::sqrt(std::max(0.0, h[r].r));
+  // a NaN stays NaN (std::max(0, NaN) would return 0 and hide it)
+  for (int r = 0; r < nrhs; ++r) out[r] = std::isnan(h[r].r) ? h[r].r : std::sqrt(std::max(0.0, h[r].r));
 }
 
 // One GMRES(m) solve of A x = b from x0 = 0 on stream s.  b, x: FP64 blocks
@@ -392,6 +400,7 @@ int gmres_run(const Op& o, const double* b, double* x, int nrhs, double tol, int
   const int64_t vstride = n * nrhs * C;
   const int m = restart;
   const int tb = 256;
+  // FP64 bytes cover the FP32 products too; reserved before the graphs capture the address
   ensure_scratch(const_cast<Op&>(o), matvec_scratch_bytes(o, nrhs, false));
   DevBuf Vbuf(sizeof(T) * vstride * (m + 1)), wbuf(sizeof(T) * vstride), zbuf(sizeof(T) * vstride),
       rbuf(sizeof(double) * vstride), ubuf(sizeof(double) * vstride);
@@ -542,7 +551,7 @@ int gmres_run(const Op& o, const double* b, double* x, int nrhs, double tol, int
     // x += M^-1 V y
     k_backsolve<<<1, std::max(32, ((nrhs + 31) / 32) * 32), 0, s>>>(st);
     launched("k_backsolve");
-    k_combine<T, CPLX><<<nblk(n * nrhs, tb), tb, 0, s>>>(V, vstride, m + 1, u, n, nrhs, st.y);
+    k_combine<T, CPLX><<<nblk(n * nrhs, tb), tb, 0, s>>>(V, vstride, m + 1, u, n, nrhs, st.y, st.jend);
     launched("k_combine");
     if (prec) {
       precond_apply(o, u, r, nrhs, false, s);
@@ -613,7 +622,7 @@ int solve_gmres(const Op& o, const void* bv, void* xv, int nrhs, const bembel_so
       double worst = 0.0;
       for (int rr = 0; rr < nrhs; ++rr) {
         relres[rr] = bn[rr] > 0 ? rn[rr] / bn[rr] : 0.0;
-        worst = std::max(worst, relres[rr]);
+        worst = worse(worst, relres[rr]);
       }
       if (worst <= so.tol) break;
       ++refinements;
@@ -633,7 +642,7 @@ int solve_gmres(const Op& o, const void* bv, void* xv, int nrhs, const bembel_so
   }
   cuda_check(cudaStreamSynchronize(s), "solve sync");
   double worst = 0.0;
-  for (double v : relres) worst = std::max(worst, v);
+  for (double v : relres) worst = worse(worst, v);
   if (info) {
     info->iterations = iters;
     info->refinements = refinements;

@@ -174,6 +174,27 @@ def test_mixed_precision_solution(geom):
     assert (torch.linalg.norm(xmx - x64) / torch.linalg.norm(x64)).item() < 1e-6
 
 
+def test_mixed_precision_restarts(geom):
+    """Short restart cycles with FP64 residuals between graph-replayed FP32
+    Arnoldi steps, on device memory that held NaN before."""
+    gop64 = bem.bembel_assemble(geom, LAP, 0.0, 4, 1, 4)
+    gopmx = bem.bembel_assemble(geom, LAP, 0.0, 4, 1, 4, precision=bem.BEMBEL_PREC_MIXED)
+    n = bem.bembel_ndofs(gop64)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    bem.bembel_rhs(gop64, bem.BEMBEL_RHS_POINT_SOURCE, np.array([[0.0, 0.0, 2.0]]), b)
+    x64, xmx = torch.empty_like(b), torch.empty_like(b)
+    bem.bembel_solve(gop64, b, x64, 1, tol=1e-10)
+    # leave NaN in freed device memory: the solver's fresh buffers may reuse it,
+    # and Krylov columns a cycle did not build must never be read
+    poison = torch.full((64 << 20,), float("nan"), dtype=torch.float32, device="cuda")
+    del poison
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    imx = bem.bembel_solve(gopmx, b, xmx, 1, tol=1e-10, restart=4)
+    assert imx["converged"] and torch.isfinite(xmx).all().item()
+    assert (torch.linalg.norm(xmx - x64) / torch.linalg.norm(x64)).item() < 1e-6
+
+
 def test_invalid_arguments(geom):
     gop = bem.bembel_assemble(geom, LAP, 0.0, 1, 0, 0)
     x = torch.zeros(24, dtype=torch.float64, device="cuda")
