@@ -77,8 +77,12 @@ static const bool g_sync_debug = std::getenv("BEMBEL_SYNC_DEBUG") != nullptr;
 
 void debug_mark(const char* what) {
   if (g_sync_debug) {
-    std::fprintf(stderr, "[bembel] %s\n", what);
+    // host time since the previous marker (launches are synchronised in this mode)
+    static thread_local auto last = std::chrono::steady_clock::now();
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[bembel] +%.3f ms  %s\n", std::chrono::duration<double, std::milli>(now - last).count(), what);
     std::fflush(stderr);
+    last = now;
   }
 }
 

@@ -398,6 +398,7 @@ void build_structure(Op& o) {
   }
   o.d_near_ptr = upload(nptr);
   o.d_near_col = upload(ncol);
+  debug_mark("setup: tensor-core groups");
   if (o.opts.precision == BEMBEL_PREC_MIXED && o.q == 4 && o.opts.tensor_cores) tc_build_groups(o, fptr, fsrc);
   {
     std::vector<int> diag(o.nleaf, -1), ids(o.nleaf), ntgt(o.nnear);

@@ -31,7 +31,9 @@ namespace bembel {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr int kTcSmem = 100 * 1024;  // also caps residency at two CTAs per SM (TMEM 2 x 256 columns)
+constexpr int kTcSmem = 100 * 1024;  // self-test launch (one CTA)
+constexpr int kSmPerSm = 233472;     // shared memory per SM (228 KB)
+constexpr int kSmReserved = 1024;    // per-CTA reservation
 constexpr long long kSpinLimit = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -364,33 +366,50 @@ __global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restric
 
 bool tc_coupling_usable(const Op& o, int nrhs) {
   const int ncol = nrhs * (o.cplx ? 2 : 1);
-  return o.d_tc_gptr != nullptr && o.q2 == 16 && ncol >= 16 && ncol <= 256 && ncol % 16 == 0;
+  // below these widths the CUDA-core product is as fast (measured on the
+  // level-6 sphere: real 32 columns 1.4x, complex 64 columns 1.15x faster here)
+  const int min_cols = o.cplx ? 64 : 32;
+  return o.d_tc_gptr != nullptr && o.q2 == 16 && ncol >= min_cols && ncol <= 256 && ncol % 16 == 0;
+}
+
+// CTAs per SM that the TMEM accumulators allow (512 columns per SM), and the
+// dynamic shared memory that keeps residency at that count: the operand
+// buffers need 2 x (4 KB + ncol x 32 B); the rest is padding.
+static int tc_smem_bytes(int ncol, int static_bytes, int* ctas_per_sm) {
+  int cols = 32;
+  while (cols < ncol) cols <<= 1;
+  const int ctas = std::min(8, 512 / cols);
+  const int need = 2 * 4096 + 2 * ncol * 32;
+  // (ctas + 1) CTAs must not fit: per-CTA footprint above kSmPerSm / (ctas + 1)
+  const int cap = kSmPerSm / (ctas + 1) - kSmReserved - static_bytes + 128;
+  *ctas_per_sm = ctas;
+  return std::max(need, cap);
 }
 
 void tc_coupling(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s) {
   const int ncol = nrhs * (o.cplx ? 2 : 1);
-  static bool attr_set[2] = {false, false};
-  const int grid = int(std::min<int64_t>(o.tc_ngroups, 152 * 2));
+  cudaFuncAttributes fa{};
+  int ctas = 1;
   if (o.cplx) {
-    if (!attr_set[1]) {
-      cuda_check(cudaFuncSetAttribute(k_coupling_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
-                 "tc smem");
-      attr_set[1] = true;
-    }
-    k_coupling_tc<true><<<grid, kTcThreads, kTcSmem, s>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
-                                                          o.d_tc_gcnt, int(o.tc_ngroups),
-                                                          reinterpret_cast<const float4*>(o.d_nodes32),
-                                                          float(o.kre), float(o.kim), xh, yh, ncol, o.d_tc_err);
+    cuda_check(cudaFuncGetAttributes(&fa, k_coupling_tc<true>), "tc attributes");
+    const int smem = tc_smem_bytes(ncol, int(fa.sharedSizeBytes), &ctas);
+    cuda_check(cudaFuncSetAttribute(k_coupling_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+               "tc smem");
+    const int grid = int(std::min<int64_t>(o.tc_ngroups, int64_t(152) * ctas));
+    k_coupling_tc<true><<<grid, kTcThreads, smem, s>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
+                                                       o.d_tc_gcnt, int(o.tc_ngroups),
+                                                       reinterpret_cast<const float4*>(o.d_nodes32), float(o.kre),
+                                                       float(o.kim), xh, yh, ncol, o.d_tc_err);
   } else {
-    if (!attr_set[0]) {
-      cuda_check(cudaFuncSetAttribute(k_coupling_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
-                 "tc smem");
-      attr_set[0] = true;
-    }
-    k_coupling_tc<false><<<grid, kTcThreads, kTcSmem, s>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
-                                                           o.d_tc_gcnt, int(o.tc_ngroups),
-                                                           reinterpret_cast<const float4*>(o.d_nodes32), 0.f, 0.f, xh,
-                                                           yh, ncol, o.d_tc_err);
+    cuda_check(cudaFuncGetAttributes(&fa, k_coupling_tc<false>), "tc attributes");
+    const int smem = tc_smem_bytes(ncol, int(fa.sharedSizeBytes), &ctas);
+    cuda_check(cudaFuncSetAttribute(k_coupling_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+               "tc smem");
+    const int grid = int(std::min<int64_t>(o.tc_ngroups, int64_t(152) * ctas));
+    k_coupling_tc<false><<<grid, kTcThreads, smem, s>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
+                                                        o.d_tc_gcnt, int(o.tc_ngroups),
+                                                        reinterpret_cast<const float4*>(o.d_nodes32), 0.f, 0.f, xh,
+                                                        yh, ncol, o.d_tc_err);
   }
   launched("k_coupling_tc");
 }
@@ -400,21 +419,28 @@ void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vecto
   const int TG = o.cplx ? 4 : 8;
   std::vector<int> gptr = {0}, gsrc, gfirst, gcnt;
   std::vector<unsigned> gmask;
+  gsrc.reserve(fsrc.size());
+  gmask.reserve(fsrc.size());
+  // union of the group targets' far sources: mark[src] collects the target
+  // bits, touched lists each source once (linear in the far-list length)
+  std::vector<unsigned> mark(o.nclusters, 0u);
+  std::vector<int> touched;
   for (int l = 0; l <= o.leaf; ++l) {
     const int64_t t0 = o.lvl_off[l], t1 = o.lvl_off[l + 1];
     for (int64_t g = t0; g < t1; g += TG) {
       const int nt = int(std::min<int64_t>(TG, t1 - g));
-      // merge the sorted source lists of the group's targets
-      std::vector<std::pair<int, unsigned>> u;
+      touched.clear();
       for (int i = 0; i < nt; ++i)
-        for (long long k = fptr[g + i]; k < fptr[g + i + 1]; ++k) u.push_back({fsrc[k], 1u << i});
-      std::sort(u.begin(), u.end());
-      for (size_t k = 0; k < u.size();) {
-        unsigned m = 0;
-        const int sc = u[k].first;
-        while (k < u.size() && u[k].first == sc) m |= u[k++].second;
+        for (long long k = fptr[g + i]; k < fptr[g + i + 1]; ++k) {
+          const int sc = fsrc[k];
+          if (!mark[sc]) touched.push_back(sc);
+          mark[sc] |= 1u << i;
+        }
+      std::sort(touched.begin(), touched.end());  // ascending sources: neighbouring loads
+      for (int sc : touched) {
         gsrc.push_back(sc);
-        gmask.push_back(m);
+        gmask.push_back(mark[sc]);
+        mark[sc] = 0u;
       }
       gptr.push_back(int(gsrc.size()));
       gfirst.push_back(int(g));

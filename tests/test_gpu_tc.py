@@ -21,9 +21,10 @@ def test_tc_selftest_exact(n):
     assert bem.bembel_tc_selftest(n) == 0.0
 
 
-@pytest.mark.parametrize("op,k,nrhs", [("laplace", 0.0, 16), ("laplace", 0.0, 64), ("helmholtz", 3.0, 32),
-                                       ("helmholtz", 3.0, 64)])
-def test_tc_coupling_matches_cuda_cores(op, k, nrhs):
+@pytest.mark.parametrize("op,k,nrhs,tc_used", [("laplace", 0.0, 16, False), ("laplace", 0.0, 32, True),
+                                               ("laplace", 0.0, 128, True), ("helmholtz", 3.0, 16, False),
+                                               ("helmholtz", 3.0, 32, True), ("helmholtz", 3.0, 64, True)])
+def test_tc_coupling_matches_cuda_cores(op, k, nrhs, tc_used):
     g = bem.bembel_geom_create()
     kind = bem.BEMBEL_LAPLACE_SL if op == "laplace" else bem.BEMBEL_HELMHOLTZ_SL
     tc = bem.bembel_assemble(g, kind, k, 4, 1, 4, precision=bem.BEMBEL_PREC_MIXED, tensor_cores=1)
@@ -37,8 +38,12 @@ def test_tc_coupling_matches_cuda_cores(op, k, nrhs):
     bem.bembel_matvec(cc, Xt, Y2, nrhs, fp32=True)
     torch.cuda.synchronize()
     rel = (torch.linalg.norm(Y1 - Y2) / torch.linalg.norm(Y2)).item()
-    assert rel < 5e-3, rel
-    assert rel > 0.0  # the bf16 path actually ran
+    # the CUDA-core product accumulates with atomics: two runs differ by FP32
+    # rounding order only; bf16 operands differ by ~1e-4..1e-3
+    if tc_used:
+        assert 1e-5 < rel < 5e-3, rel
+    else:
+        assert rel < 1e-6, rel  # narrow blocks stay on the CUDA-core product
 
 
 def test_tc_batched_helmholtz_solve():
