@@ -47,7 +47,8 @@ extern "C" {
 #define BEMBEL_ENOMEM 2        /* device or host allocation failed             */
 #define BEMBEL_ECUDA 3         /* a CUDA call failed (message has the reason)  */
 #define BEMBEL_ENOTCONV 4      /* GMRES reached max_iter; x holds its iterate  */
-#define BEMBEL_ETIMEOUT 5      /* reserved: a bounded device wait expired      */
+#define BEMBEL_ETIMEOUT 5      /* a bounded device wait (tensor-core MMA completion) expired;
+                                  reported after a solve or by the next call on the operator */
 #define BEMBEL_EUNSUPPORTED 6  /* valid request the library does not implement */
 
 /* ---- enumerations ---------------------------------------------------------- */

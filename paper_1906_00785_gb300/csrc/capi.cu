@@ -47,11 +47,12 @@ void free_op(Op* o) {
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
                   o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_nodes, o->d_scratch, o->d_bj,
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
-                  o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt, o->d_tc_err};
+                  o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* p : o->d_pairs)
     if (p) cudaFree(p);
+  if (o->h_tc_err) cudaFreeHost(o->h_tc_err);
   delete o;
 }
 
@@ -306,6 +307,7 @@ int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs,
     if (nrhs < 1) fail(BEMBEL_EINVAL, "matvec: nrhs must be >= 1");
     if (x_dev == y_dev) fail(BEMBEL_EINVAL, "matvec: x and y must not overlap");
     const Op* o = reinterpret_cast<const Op*>(op);
+    tc_check(*o);
     matvec_device(*o, x_dev, y_dev, nrhs, fp32 != 0, o->stream);
     return BEMBEL_OK;
   });
@@ -317,6 +319,7 @@ int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, i
     if (nrhs < 1) fail(BEMBEL_EINVAL, "matvec_noalloc: nrhs must be >= 1");
     if (x_dev == y_dev) fail(BEMBEL_EINVAL, "matvec_noalloc: x and y must not overlap");
     const Op* o = reinterpret_cast<const Op*>(op);
+    tc_check(*o);
     matvec_noalloc(*o, x_dev, y_dev, nrhs, fp32 != 0, o->stream);
     return BEMBEL_OK;
   });
@@ -400,7 +403,9 @@ int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, 
     if (o.precond != BEMBEL_PRECOND_NONE && o.precond != BEMBEL_PRECOND_BLOCK_JACOBI &&
         o.precond != BEMBEL_PRECOND_LEARNED)
       fail(BEMBEL_EINVAL, "solve: unknown preconditioner");
+    tc_check(*reinterpret_cast<const Op*>(op));
     const int rc = solve_gmres(*reinterpret_cast<const Op*>(op), b_dev, x_dev, nrhs, o, info);
+    tc_check(*reinterpret_cast<const Op*>(op));  // solve_gmres synchronised its stream
     if (rc == BEMBEL_ENOTCONV) g_last_error = "solve: GMRES reached max_iter before the tolerance";
     return rc;
   });

@@ -90,7 +90,8 @@ struct Op {
   unsigned* d_tc_gmask = nullptr;  // which group targets interact with the source
   int* d_tc_gfirst = nullptr;      // first target of the group
   int* d_tc_gcnt = nullptr;        // targets in the group
-  int* d_tc_err = nullptr;         // set when a bounded wait timed out
+  int* d_tc_err = nullptr;         // device alias of h_tc_err
+  int* h_tc_err = nullptr;         // host-mapped flag: set when a bounded MMA wait timed out
   int64_t tc_ngroups = 0, tc_nentries = 0;
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -141,6 +142,8 @@ bool tc_coupling_usable(const Op& o, int nrhs);
 void tc_coupling(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s);
 void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vector<int>& fsrc);
 double tc_selftest(int N);
+// fails with BEMBEL_ETIMEOUT if an earlier tensor-core product on o timed out
+void tc_check(const Op& o);
 // precond.cu
 void precond_setup(Op& o);
 // learned.cu

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restric
       if (issued[stage]) {  // buffer still read by the MMA issued two steps ago
         if (!mbar_wait(&mbar[stage], phase[stage])) {
           if (tid == 0) {
-            atomicExch(err, 1);
+            *reinterpret_cast<volatile int*>(err) = 1;
             abort_flag = 1;
           }
         }
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restric
     for (int st = 0; st < 2; ++st)
       if (issued[st]) {
         if (!mbar_wait(&mbar[st], phase[st]) && tid == 0) {
-          atomicExch(err, 1);
+          *reinterpret_cast<volatile int*>(err) = 1;
           abort_flag = 1;
         }
         phase[st] ^= 1;
@@ -460,8 +460,20 @@ void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vecto
   o.d_tc_gmask = up(gmask);
   o.d_tc_gfirst = up(gfirst);
   o.d_tc_gcnt = up(gcnt);
-  o.d_tc_err = static_cast<int*>(dev_alloc(sizeof(int)));
-  cuda_check(cudaMemset(o.d_tc_err, 0, sizeof(int)), "tc err");
+  // the time-out flag lives in mapped host memory: the host reads it without
+  // synchronising (the next call on the operator reports it)
+  void* h = nullptr;
+  cuda_check(cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped), "tc err flag");
+  o.h_tc_err = static_cast<int*>(h);
+  *o.h_tc_err = 0;
+  void* dptr = nullptr;
+  cuda_check(cudaHostGetDevicePointer(&dptr, h, 0), "tc err flag alias");
+  o.d_tc_err = static_cast<int*>(dptr);
+}
+
+void tc_check(const Op& o) {
+  if (o.h_tc_err && *static_cast<volatile int*>(o.h_tc_err))
+    fail(BEMBEL_ETIMEOUT, "a tensor-core MMA completion wait timed out in an earlier product on this operator");
 }
 
 double tc_selftest(int N) {
