@@ -127,7 +127,9 @@ typedef struct {
   double setup_ms;          /* host time of topology, trees and pair lists      */
   /* device time per assembly phase (CUDA events on the operator's stream):
    * 0 tabulation, 1 regular near field, 2 identical, 3 common edge,
-   * 4 common vertex, 5 coupling, 6 FP32 copies, 7 unused */
+   * 4 common vertex, 5 coupling, 6 FP32 copies, 7 the persistent multi-mesh
+   * kernel (operators from bembel_assemble_batch: phases 0, 6 and 7 are the
+   * whole batch's, 1-5 are zero) */
   double phase_ms[8];
 } bembel_op_info;
 
@@ -193,6 +195,30 @@ int bembel_geom_destroy(bembel_geom* g);
  * (Maxwell), ENOMEM, ECUDA. */
 int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q,
                     const bembel_opts* o, bembel_op** out);
+
+/* One mesh of a batched assembly. */
+typedef struct {
+  bembel_geom* geom;  /* geometry of this mesh (must outlive the operator)   */
+  double k_re, k_im;  /* wavenumber (Helmholtz; ignored for Laplace)          */
+  int level;          /* refinement level L of this mesh                      */
+} bembel_batch_item;
+
+/* Assemble n operators that share op, p, q and the options (same quadrature
+ * orders, eta, leaf rule, precision) but may differ in geometry, level and
+ * wavenumber -- e.g. a family of meshes or a frequency sweep.  No counterpart
+ * in the paper, which assembles one operator at a time: every operator is the
+ * one bembel_assemble builds from the same arguments (bit-identical blocks).
+ * The host set-up runs per mesh; then one tabulation launch, ONE persistent
+ * launch that walks a global work list of (mesh, phase, pair or block range)
+ * items over the near field and coupling of all meshes, and one FP32-copy
+ * launch (MIXED).  out[0..n-1] receive independent handles (destroy each);
+ * info.assemble_ms is the batch's device time and phase_ms 0 / 7 / 6 the
+ * tabulation, persistent and copy launches.  items and out: host arrays of n.
+ * On failure every out[i] is NULL and nothing is left allocated.
+ * Errors: EINVAL (NULL, n outside [1, 64], bad item), EUNSUPPORTED (Maxwell),
+ * ENOMEM, ECUDA. */
+int bembel_assemble_batch(int op, int p, int q, const bembel_batch_item* items, int n, const bembel_opts* o,
+                          bembel_op** out);
 int bembel_op_destroy(bembel_op* op);
 
 /* Choose quadrature orders, the interpolation order q and the block-product
@@ -227,10 +253,10 @@ int bembel_op_info_get(const bembel_op* op, bembel_op_info* info);
  * Errors: EINVAL (NULL, nrhs < 1), ENOMEM, ECUDA. */
 int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
 /* Note: for MIXED operators with q = 4 and tensor_cores = 1, the FP32 product
- * with 8 <= nrhs (x2 complex) <= 256 real columns, a multiple of 16, evaluates the
- * far-field coupling on the tensor cores in bf16 with FP32 accumulation
- * (relative error ~1e-3 of the far-field part); other FP32 products use FP32
- * CUDA-core arithmetic. */
+ * with nrhs (x2 complex) real columns a multiple of 16 in [32, 256] (Laplace)
+ * or [64, 256] (Helmholtz) evaluates the far-field coupling on the tensor cores
+ * in bf16 with FP32 accumulation (relative error ~1e-3 of the far-field part);
+ * other FP32 products use FP32 CUDA-core arithmetic. */
 
 /* y = A x like bembel_matvec, but without allocating anything.  The paper has
  * no counterpart: this entry point exists for callers that cannot call

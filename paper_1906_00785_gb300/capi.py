@@ -30,6 +30,7 @@ EXPORTED = [
     "bembel_matvec", "bembel_rhs", "bembel_solve", "bembel_eval", "bembel_kernel_launches",
     "bembel_matvec_noalloc", "bembel_autotune", "bembel_learned_collect", "bembel_learned_set_destroy",
     "bembel_learned_train", "bembel_learned_attach", "bembel_mlp_eval", "bembel_tc_selftest",
+    "bembel_assemble_batch",
 ]
 
 
@@ -66,6 +67,10 @@ class TuneReport(C.Structure):
                 ("chunk_ms", C.c_double * 5), ("tune_ms", C.c_double)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("geom", C.c_void_p), ("k_re", C.c_double), ("k_im", C.c_double), ("level", C.c_int)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int), ("precond", C.c_int),
                 ("refine", C.c_int)]
@@ -99,6 +104,7 @@ def lib():
     L.bembel_geom_create.argtypes = [C.POINTER(GeomDesc), C.POINTER(vp)]
     L.bembel_geom_destroy.argtypes = [vp]
     L.bembel_assemble.argtypes = [vp, ci, dbl, dbl, ci, ci, ci, C.POINTER(Opts), C.POINTER(vp)]
+    L.bembel_assemble_batch.argtypes = [ci, ci, ci, C.POINTER(BatchItem), ci, C.POINTER(Opts), C.POINTER(vp)]
     L.bembel_op_destroy.argtypes = [vp]
     L.bembel_ndofs.argtypes = [vp, C.POINTER(i64)]
     L.bembel_op_info_get.argtypes = [vp, C.POINTER(OpInfo)]
@@ -202,6 +208,24 @@ def bembel_assemble(geom: Geometry, op: int, k: complex, level: int, p: int, q: 
     k = complex(k)
     _check(lib().bembel_assemble(geom.handle, op, k.real, k.imag, level, p, q, C.byref(o), C.byref(h)))
     return Operator(h, geom, op)
+
+
+def bembel_assemble_batch(items, op: int, p: int, q: int, opts: Opts | None = None, **overrides) -> list:
+    """items: sequence of (geometry, k, level).  Returns one Operator per item."""
+    o = opts if opts is not None else bembel_opts_default()
+    for key, v in overrides.items():
+        setattr(o, key, v)
+    n = len(items)
+    arr = (BatchItem * max(1, n))()
+    for i, (geom, k, level) in enumerate(items):
+        k = complex(k)
+        arr[i].geom = geom.handle.value if isinstance(geom.handle, C.c_void_p) else geom.handle
+        arr[i].k_re = k.real
+        arr[i].k_im = k.imag
+        arr[i].level = level
+    outs = (C.c_void_p * max(1, n))()
+    _check(lib().bembel_assemble_batch(op, p, q, arr, n, C.byref(o), outs))
+    return [Operator(C.c_void_p(outs[i]), items[i][0], op) for i in range(n)]
 
 
 def bembel_autotune(geom: Geometry, op: int, k: complex, level: int, p: int, quad_tol: float = 1e-8,

@@ -206,58 +206,70 @@ int bembel_geom_destroy(bembel_geom* g) {
   return BEMBEL_OK;
 }
 
+namespace {
+// Validated operator description (no device work yet).
+Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q, const bembel_opts* o) {
+  if (!g) fail(BEMBEL_EINVAL, "assemble: NULL geometry");
+  if (op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE operator is not implemented");
+  if (op != BEMBEL_LAPLACE_SL && op != BEMBEL_HELMHOLTZ_SL) fail(BEMBEL_EINVAL, "assemble: unknown operator");
+  if (level < 0 || level > 10) fail(BEMBEL_EINVAL, "assemble: level must be in [0, 10]");
+  if (p < 0 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: degree p must be in [0, 2]");
+  if (q < 0 || q > kMaxQ) fail(BEMBEL_EINVAL, "assemble: q must be in [0, 8]");
+  bembel_opts opts;
+  bembel_opts_default(&opts);
+  if (o) opts = *o;
+  if (opts.g_regular < 1 || opts.g_regular > kMaxG || opts.g_singular < 1 || opts.g_singular > kMaxG)
+    fail(BEMBEL_EINVAL, "assemble: Gauss orders must be in [1, 10]");
+  for (int gk : {opts.g_identical, opts.g_edge, opts.g_vertex})
+    if (gk < 0 || gk > kMaxG) fail(BEMBEL_EINVAL, "assemble: per-class Gauss orders must be in [0, 10]");
+  if (opts.precision != BEMBEL_PREC_FP64 && opts.precision != BEMBEL_PREC_MIXED)
+    fail(BEMBEL_EINVAL, "assemble: unknown precision");
+  if (q > 0 && !(opts.eta > 0)) fail(BEMBEL_EINVAL, "assemble: eta must be positive");
+  if (opts.bsr_chunk < 0 || opts.bsr_chunk > 4096) fail(BEMBEL_EINVAL, "assemble: bsr_chunk must be in [0, 4096]");
+  const int leaf = opts.leaf_level < 0 ? (level > 0 ? level - 1 : 0) : opts.leaf_level;
+  if (leaf > level) fail(BEMBEL_EINVAL, "assemble: leaf_level above level");
+  Op* res = new Op();
+  res->geom = reinterpret_cast<GeomHandle*>(g)->g;
+  res->op = op;
+  res->cplx = op == BEMBEL_HELMHOLTZ_SL;
+  res->kre = res->cplx ? k_re : 0.0;
+  res->kim = res->cplx ? k_im : 0.0;
+  res->L = level;
+  res->d = p;
+  res->q = q;
+  res->leaf = leaf;
+  res->opts = opts;
+  res->g_reg = opts.g_regular;
+  res->g_sing = opts.g_singular;
+  res->g_kind[kIdentical] = opts.g_identical > 0 ? opts.g_identical : opts.g_singular;
+  res->g_kind[kEdge] = opts.g_edge > 0 ? opts.g_edge : opts.g_singular;
+  res->g_kind[kVertex] = opts.g_vertex > 0 ? opts.g_vertex : opts.g_singular;
+  res->stream = static_cast<cudaStream_t>(opts.stream);
+  res->bsr_chunk = opts.bsr_chunk > 0 ? opts.bsr_chunk : 32;
+  return res;
+}
+
+// host set-up of one operator, timed into info.setup_ms
+void setup_op(Op& o) {
+  debug_mark("assemble: build_structure");
+  const auto th0 = std::chrono::steady_clock::now();
+  build_structure(o);
+  o.info.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+}
+}  // namespace
+
 int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q, const bembel_opts* o,
                     bembel_op** out) {
   Op* res = nullptr;
   const int rc = guarded([&] {
     if (!g || !out) fail(BEMBEL_EINVAL, "assemble: NULL argument");
-    if (op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE operator is not implemented");
-    if (op != BEMBEL_LAPLACE_SL && op != BEMBEL_HELMHOLTZ_SL) fail(BEMBEL_EINVAL, "assemble: unknown operator");
-    if (level < 0 || level > 10) fail(BEMBEL_EINVAL, "assemble: level must be in [0, 10]");
-    if (p < 0 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: degree p must be in [0, 2]");
-    if (q < 0 || q > kMaxQ) fail(BEMBEL_EINVAL, "assemble: q must be in [0, 8]");
-    bembel_opts opts;
-    bembel_opts_default(&opts);
-    if (o) opts = *o;
-    if (opts.g_regular < 1 || opts.g_regular > kMaxG || opts.g_singular < 1 || opts.g_singular > kMaxG)
-      fail(BEMBEL_EINVAL, "assemble: Gauss orders must be in [1, 10]");
-    for (int gk : {opts.g_identical, opts.g_edge, opts.g_vertex})
-      if (gk < 0 || gk > kMaxG) fail(BEMBEL_EINVAL, "assemble: per-class Gauss orders must be in [0, 10]");
-    if (opts.precision != BEMBEL_PREC_FP64 && opts.precision != BEMBEL_PREC_MIXED)
-      fail(BEMBEL_EINVAL, "assemble: unknown precision");
-    if (q > 0 && !(opts.eta > 0)) fail(BEMBEL_EINVAL, "assemble: eta must be positive");
-    res = new Op();
-    res->geom = reinterpret_cast<GeomHandle*>(g)->g;
-    res->op = op;
-    res->cplx = op == BEMBEL_HELMHOLTZ_SL;
-    res->kre = res->cplx ? k_re : 0.0;
-    res->kim = res->cplx ? k_im : 0.0;
-    res->L = level;
-    res->d = p;
-    res->q = q;
-    res->leaf = opts.leaf_level < 0 ? (level > 0 ? level - 1 : 0) : opts.leaf_level;
-    if (res->leaf > level) fail(BEMBEL_EINVAL, "assemble: leaf_level above level");
-    res->opts = opts;
-    res->g_reg = opts.g_regular;
-    res->g_sing = opts.g_singular;
-    res->g_kind[kIdentical] = opts.g_identical > 0 ? opts.g_identical : opts.g_singular;
-    res->g_kind[kEdge] = opts.g_edge > 0 ? opts.g_edge : opts.g_singular;
-    res->g_kind[kVertex] = opts.g_vertex > 0 ? opts.g_vertex : opts.g_singular;
-    res->stream = static_cast<cudaStream_t>(opts.stream);
-    if (opts.bsr_chunk < 0 || opts.bsr_chunk > 4096) fail(BEMBEL_EINVAL, "assemble: bsr_chunk must be in [0, 4096]");
-    res->bsr_chunk = opts.bsr_chunk > 0 ? opts.bsr_chunk : 32;
+    res = make_op(g, op, k_re, k_im, level, p, q, o);
     int dev = 0;
-    debug_mark("assemble: cudaGetDevice");
     cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     cudaEvent_t e0, e1;
-    debug_mark("assemble: events");
     cuda_check(cudaEventCreate(&e0), "event");
     cuda_check(cudaEventCreate(&e1), "event");
-    debug_mark("assemble: build_structure");
-    const auto th0 = std::chrono::steady_clock::now();
-    build_structure(*res);
-    res->info.setup_ms =
-        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+    setup_op(*res);
     debug_mark("assemble: kernels");
     cuda_check(cudaEventRecord(e0, res->stream), "event record");
     run_assembly_kernels(*res);
@@ -274,6 +286,44 @@ int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level,
   if (rc != BEMBEL_OK && res) {
     free_op(res);
     if (out) *out = nullptr;
+  }
+  return rc;
+}
+
+int bembel_assemble_batch(int op, int p, int q, const bembel_batch_item* items, int n, const bembel_opts* o,
+                          bembel_op** out) {
+  std::vector<Op*> ops;
+  const int rc = guarded([&] {
+    if (!items || !out) fail(BEMBEL_EINVAL, "assemble_batch: NULL argument");
+    if (n < 1 || n > kMaxBatch) fail(BEMBEL_EINVAL, "assemble_batch: n must be in [1, 64]");
+    for (int i = 0; i < n; ++i) out[i] = nullptr;
+    for (int i = 0; i < n; ++i) {
+      if (!items[i].geom) fail(BEMBEL_EINVAL, "assemble_batch: NULL geometry in an item");
+      ops.push_back(make_op(items[i].geom, op, items[i].k_re, items[i].k_im, items[i].level, p, q, o));
+    }
+    for (Op* r : ops) setup_op(*r);
+    debug_mark("assemble_batch: kernels");
+    cudaEvent_t e0, e1;
+    cuda_check(cudaEventCreate(&e0), "event");
+    cuda_check(cudaEventCreate(&e1), "event");
+    cuda_check(cudaEventRecord(e0, ops[0]->stream), "event record");
+    run_assembly_batch(ops);
+    cuda_check(cudaEventRecord(e1, ops[0]->stream), "event record");
+    cuda_check(cudaEventSynchronize(e1), "assembly sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < n; ++i) {
+      ops[i]->info.assemble_ms = ms;  // the whole batch's device time
+      out[i] = reinterpret_cast<bembel_op*>(ops[i]);
+    }
+    return BEMBEL_OK;
+  });
+  if (rc != BEMBEL_OK) {
+    for (Op* r : ops) free_op(r);
+    if (out && items && n >= 1 && n <= kMaxBatch)
+      for (int i = 0; i < n; ++i) out[i] = nullptr;
   }
   return rc;
 }

@@ -124,6 +124,10 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
                   double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep);
 // quad.cu
 void run_assembly_kernels(Op& o);       // tabulation, near field, coupling
+void alloc_assembly_outputs(Op& o);     // Xq, near field, coupling, FP32 near copy
+// several operators sharing (op, degree, q, options): tabulation, one
+// persistent launch for all near-field pairs and coupling blocks, FP32 copies
+void run_assembly_batch(const std::vector<Op*>& ops);
 // h2mv.cu
 void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
 void ensure_scratch(Op& o, size_t bytes);
@@ -182,5 +186,13 @@ void note_graph_kernels(long long n);
 bool capturing();
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
+// scoped device allocation
+struct DevBuf {
+  void* p = nullptr;
+  explicit DevBuf(size_t bytes) { p = dev_alloc(bytes); }
+  ~DevBuf() { dev_free(p); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
 
 }  // namespace bembel

@@ -351,14 +351,6 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
   if (id < n) c[id] = a[id] - b[id];
 }
 
-struct DevBuf {
-  void* p = nullptr;
-  explicit DevBuf(size_t bytes) { p = dev_alloc(bytes); }
-  ~DevBuf() { dev_free(p); }
-  DevBuf(const DevBuf&) = delete;
-  DevBuf& operator=(const DevBuf&) = delete;
-};
-
 struct HostBuf {
   void* p = nullptr;
   explicit HostBuf(size_t bytes) { cuda_check(cudaMallocHost(&p, bytes), "cudaMallocHost"); }
