@@ -59,7 +59,8 @@ enum bembel_geom_kind {
 enum bembel_op_kind {
   BEMBEL_LAPLACE_SL = 0,   /* App. B (LS): G = 1/(4 pi r)                 */
   BEMBEL_HELMHOLTZ_SL = 1, /* App. B (HS): G = exp(-i kappa r)/(4 pi r)    */
-  BEMBEL_MAXWELL_SL = 2    /* App. B (MS): not implemented (EUNSUPPORTED) */
+  BEMBEL_MAXWELL_SL = 2    /* App. B (MS): electric field integral equation on the S^1
+                              space of App. E (see "EFIE" below)                 */
 };
 enum bembel_precision {
   BEMBEL_PREC_FP64 = 0,  /* everything in FP64                                       */
@@ -67,7 +68,10 @@ enum bembel_precision {
 };
 enum bembel_rhs_kind {
   BEMBEL_RHS_POINT_SOURCE = 0, /* g(x) = exp(-i kappa |x-x0|)/|x-x0| (kappa = 0: 1/|x-x0|); params: 3 per rhs */
-  BEMBEL_RHS_PLANE_WAVE = 1    /* g(x) = exp(-i kappa d.x); params: direction d, 3 per rhs */
+  BEMBEL_RHS_PLANE_WAVE = 1,   /* g(x) = exp(-i kappa d.x); params: direction d, 3 per rhs */
+  BEMBEL_RHS_EFIE_PLANE_WAVE = 2 /* EFIE only: E_inc(x) = pol exp(-i kappa d.x); params:
+                                    direction d then polarisation pol, 6 per rhs;
+                                    b_i = -int_Gamma E_inc . mu_i */
 };
 enum bembel_precond_kind {
   BEMBEL_PRECOND_NONE = 0,
@@ -180,6 +184,25 @@ int64_t bembel_kernel_launches(void);
 int bembel_geom_create(const bembel_geom_desc* desc, bembel_geom** out);
 int bembel_geom_destroy(bembel_geom* g);
 
+/* EFIE (op = BEMBEL_MAXWELL_SL).  App. B (MS) with the kernel of (HS); the
+ * Galerkin form moves the kappa^-2 gradient onto the test function:
+ *   a(j, mu) = int int G(x,y) [ j(y) . mu(x) - kappa^-2 div j(y) div mu(x) ],
+ * and the perfect-conductor condition n x (E_inc + E) = 0 of (MP) reads
+ * a(j, mu) = -int E_inc . mu (BEMBEL_RHS_EFIE_PLANE_WAVE builds that right-hand
+ * side).  Space: S^1 of App. E, p in [1, 2] (degree p across, p-1 along each
+ * component), lifted by the div-conforming Piola transform, with the normal
+ * component glued across patch edges.  Dofs per patch 2 (2^L+p)(2^L+p-1), minus
+ * one per glued edge function: ndofs = 12 (2^L+p)(2^L+p-1) - 12 (2^L+p-1).
+ * Global numbering: patches in order; inside a patch the first component
+ * i1 + np j2 (i1 < np = 2^L+p, j2 < np-1), then the second component
+ * np (np-1) + j1 + (np-1) i2; a function glued to one numbered earlier shares
+ * its number, with sign -s_own s_partner (s = +1 on the sides s = 1, t = 1,
+ * -1 on s = 0, t = 0).  This release assembles the EFIE densely (q = 0) on the
+ * cube-face sphere; bembel_eval returns the scattered field (MS) at the points,
+ * 3 complex values per point (out: [rhs][point][3] interleaved complex).
+ * bembel_autotune, bembel_assemble_batch and the learned preconditioner are
+ * for the scalar operators only (EUNSUPPORTED). */
+
 /* Assemble the compressed single-layer Galerkin matrix (Sec. 2, Sec. 4.5).
  *   op     enum bembel_op_kind; Laplace (LS) or Helmholtz (HS)
  *   k_re, k_im  complex wavenumber kappa (Sec. 4.2); ignored for Laplace
@@ -191,8 +214,8 @@ int bembel_geom_destroy(bembel_geom* g);
  * Builds the element topology, cluster tree and block tree on the host, then
  * runs the tabulation, near-field (regular + singular) quadrature and
  * coupling kernels.  The geometry must outlive the operator.
- * Errors: EINVAL (bad sizes, 0 <= level <= 10 required), EUNSUPPORTED
- * (Maxwell), ENOMEM, ECUDA. */
+ * Errors: EINVAL (bad sizes, 0 <= level <= 10 required, EFIE with k = 0 or
+ * p = 0), EUNSUPPORTED (EFIE with q > 0 or on another geometry), ENOMEM, ECUDA. */
 int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q,
                     const bembel_opts* o, bembel_op** out);
 
@@ -345,6 +368,8 @@ int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, 
  * rho_dev: device ndofs x nrhs; out_dev: device npts x nrhs column-major
  * (complex for Helmholtz).  Tensor Gauss with g points per direction per
  * element (g <= 10); points should keep a distance of a few elements from Gamma.
+ * EFIE operators: the scattered field E(x) of (MS) instead, out_dev holding
+ * 3 complex values per point and column ([rhs][point][x, y, z] interleaved).
  * Errors: EINVAL, ECUDA. */
 int bembel_eval(const bembel_op* op, const double* pts_dev, int64_t npts, const void* rho_dev, int nrhs, int g,
                 void* out_dev);

@@ -47,3 +47,27 @@ def bspline_basis(knots: np.ndarray, degree: int, x: np.ndarray) -> np.ndarray:
             nb[:, j] = t1 + t2
         b = nb
     return b
+
+
+def bspline_deriv(knots: np.ndarray, degree: int, x: np.ndarray) -> np.ndarray:
+    """Derivatives d/dx b_j^degree(x) for all j, shape (len(x), len(knots)-degree-1).
+
+    Differentiating the App. C recursion gives the standard two-term formula
+    b'_{j,p} = p b_{j,p-1} / (xi_{j+p} - xi_j) - p b_{j+1,p-1} / (xi_{j+p+1} - xi_{j+1})
+    on the same knot vector, with 0/0 := 0.
+    """
+    x = np.atleast_1d(np.asarray(x, dtype=float))
+    knots = np.asarray(knots, dtype=float)
+    n = len(knots) - degree - 1
+    if degree == 0:
+        return np.zeros((x.size, n))
+    low = bspline_basis(knots, degree - 1, x)  # (len(x), n + 1)
+    out = np.zeros((x.size, n))
+    for j in range(n):
+        d1 = knots[j + degree] - knots[j]
+        d2 = knots[j + degree + 1] - knots[j + 1]
+        if d1 > 0:
+            out[:, j] += degree * low[:, j] / d1
+        if d2 > 0:
+            out[:, j] -= degree * low[:, j + 1] / d2
+    return out

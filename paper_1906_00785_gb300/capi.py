@@ -20,7 +20,7 @@ BEMBEL_OK, BEMBEL_EINVAL, BEMBEL_ENOMEM, BEMBEL_ECUDA, BEMBEL_ENOTCONV, BEMBEL_E
 BEMBEL_GEOM_SPHERE6, BEMBEL_GEOM_PERTURBED_SPHERE = 0, 1
 BEMBEL_LAPLACE_SL, BEMBEL_HELMHOLTZ_SL, BEMBEL_MAXWELL_SL = 0, 1, 2
 BEMBEL_PREC_FP64, BEMBEL_PREC_MIXED = 0, 1
-BEMBEL_RHS_POINT_SOURCE, BEMBEL_RHS_PLANE_WAVE = 0, 1
+BEMBEL_RHS_POINT_SOURCE, BEMBEL_RHS_PLANE_WAVE, BEMBEL_RHS_EFIE_PLANE_WAVE = 0, 1, 2
 BEMBEL_PRECOND_NONE, BEMBEL_PRECOND_BLOCK_JACOBI, BEMBEL_PRECOND_LEARNED = 0, 1, 2
 BEMBEL_LEARNED_NPARAM = 433
 

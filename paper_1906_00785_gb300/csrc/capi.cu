@@ -47,7 +47,8 @@ void free_op(Op* o) {
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
                   o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_nodes, o->d_scratch, o->d_bj,
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
-                  o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt};
+                  o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
+                  o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* p : o->d_pairs)
@@ -210,8 +211,15 @@ namespace {
 // Validated operator description (no device work yet).
 Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q, const bembel_opts* o) {
   if (!g) fail(BEMBEL_EINVAL, "assemble: NULL geometry");
-  if (op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE operator is not implemented");
-  if (op != BEMBEL_LAPLACE_SL && op != BEMBEL_HELMHOLTZ_SL) fail(BEMBEL_EINVAL, "assemble: unknown operator");
+  if (op != BEMBEL_LAPLACE_SL && op != BEMBEL_HELMHOLTZ_SL && op != BEMBEL_MAXWELL_SL)
+    fail(BEMBEL_EINVAL, "assemble: unknown operator");
+  if (op == BEMBEL_MAXWELL_SL) {
+    if (p < 1 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: the EFIE needs the S^1 degree p in [1, 2]");
+    if (q != 0) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE is assembled densely (q = 0)");
+    if (reinterpret_cast<GeomHandle*>(g)->g.kind != BEMBEL_GEOM_SPHERE6)
+      fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE is available on the cube-face sphere");
+    if (k_re == 0.0 && k_im == 0.0) fail(BEMBEL_EINVAL, "assemble: the EFIE needs a nonzero wavenumber");
+  }
   if (level < 0 || level > 10) fail(BEMBEL_EINVAL, "assemble: level must be in [0, 10]");
   if (p < 0 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: degree p must be in [0, 2]");
   if (q < 0 || q > kMaxQ) fail(BEMBEL_EINVAL, "assemble: q must be in [0, 8]");
@@ -231,7 +239,8 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
   Op* res = new Op();
   res->geom = reinterpret_cast<GeomHandle*>(g)->g;
   res->op = op;
-  res->cplx = op == BEMBEL_HELMHOLTZ_SL;
+  res->efie = op == BEMBEL_MAXWELL_SL;
+  res->cplx = op == BEMBEL_HELMHOLTZ_SL || res->efie;
   res->kre = res->cplx ? k_re : 0.0;
   res->kim = res->cplx ? k_im : 0.0;
   res->L = level;
@@ -297,6 +306,7 @@ int bembel_assemble_batch(int op, int p, int q, const bembel_batch_item* items, 
     if (!items || !out) fail(BEMBEL_EINVAL, "assemble_batch: NULL argument");
     if (n < 1 || n > kMaxBatch) fail(BEMBEL_EINVAL, "assemble_batch: n must be in [1, 64]");
     for (int i = 0; i < n; ++i) out[i] = nullptr;
+    if (op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble_batch: single-layer scalar operators only");
     for (int i = 0; i < n; ++i) {
       if (!items[i].geom) fail(BEMBEL_EINVAL, "assemble_batch: NULL geometry in an item");
       ops.push_back(make_op(items[i].geom, op, items[i].k_re, items[i].k_im, items[i].level, p, q, o));
@@ -377,12 +387,16 @@ int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, i
 
 int bembel_autotune(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
                     double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep) {
-  return guarded([&] { return autotune_impl(g, op, k_re, k_im, level, p, quad_tol, far_tol, q_max, inout, rep); });
+  return guarded([&] {
+    if (op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "autotune: scalar operators only");
+    return autotune_impl(g, op, k_re, k_im, level, p, quad_tol, far_tol, q_max, inout, rep);
+  });
 }
 
 int bembel_learned_collect(bembel_op* op, int nsamples, uint64_t seed, bembel_learned_set** out) {
   return guarded([&] {
     if (!op || !out || nsamples < 1 || nsamples > 64) fail(BEMBEL_EINVAL, "learned_collect: bad argument");
+    if (reinterpret_cast<Op*>(op)->efie) fail(BEMBEL_EUNSUPPORTED, "learned_collect: scalar operators only");
     *out = reinterpret_cast<bembel_learned_set*>(learned_collect(*reinterpret_cast<Op*>(op), nsamples, seed));
     return BEMBEL_OK;
   });
@@ -433,9 +447,12 @@ int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, in
   return guarded([&] {
     if (!op || !params || !b_dev) fail(BEMBEL_EINVAL, "rhs: NULL argument");
     if (nrhs < 1) fail(BEMBEL_EINVAL, "rhs: nrhs must be >= 1");
-    if (kind != BEMBEL_RHS_POINT_SOURCE && kind != BEMBEL_RHS_PLANE_WAVE) fail(BEMBEL_EINVAL, "rhs: unknown kind");
+    const Op* o = reinterpret_cast<const Op*>(op);
+    if (o->efie ? kind != BEMBEL_RHS_EFIE_PLANE_WAVE
+                : (kind != BEMBEL_RHS_POINT_SOURCE && kind != BEMBEL_RHS_PLANE_WAVE))
+      fail(BEMBEL_EINVAL, "rhs: unknown kind for this operator");
     if (g < 1 || g > kMaxG) fail(BEMBEL_EINVAL, "rhs: g must be in [1, 10]");
-    rhs_device(*reinterpret_cast<const Op*>(op), kind, params, nrhs, g, b_dev);
+    rhs_device(*o, kind, params, nrhs, g, b_dev);
     return BEMBEL_OK;
   });
 }

@@ -1,0 +1,477 @@
+// efie.cu - electric field integral equation on the S^1 space (App. B (MS),
+// App. E).
+//
+// Galerkin form (the kappa^-2 gradient term of (MS) moved onto the test
+// function by surface integration by parts):
+//   a(j, mu) = int int G(x,y) [ j(y) . mu(x) - kappa^-2 div j(y) div mu(x) ],
+//   G = exp(-i kappa r) / (4 pi r),
+// with the perfectly conducting boundary condition of (MP) as
+//   a(j, mu) = -int E_inc . mu.
+// The div-conforming Piola lift j = D gamma phi_hat / |d1 gamma x d2 gamma|,
+// div j = div phi_hat / |...| cancels every surface measure, so an element pair
+// contributes
+//   h^4 sum_k W_k G(x_k, y_k) [ (d_alpha gamma(s_k) . d_beta gamma(t_k)) b_i(s_k) b_j(t_k)
+//                               - kappa^-2 d_i(s_k) d_j(t_k) ]
+// for element-local functions i of component alpha and j of component beta,
+// b = the Bernstein product of the function, d = its parameter divergence.
+// Quadrature: the same element-pair rules as the scalar operators (tensor
+// Gauss on separated pairs, the Duffy-type rules on touching ones; identical
+// pairs use all 8 sub-domains).  One warp per pair, lanes over rule points; the
+// 2 x 2 component quadrants of the block are accumulated one after the other so
+// the accumulators stay in registers.
+//
+// Geometry: the cube-face sphere (analytic Jacobian).
+#include <vector>
+
+#include "op.h"
+#include "pairrules.cuh"
+
+namespace bembel {
+
+namespace {
+
+constexpr int kEfieWarps = 4;
+
+// gamma and its parameter derivatives on the cube-face sphere: gamma = c / |c|,
+// d gamma = (dc - gamma (gamma . dc)) / |c| with dc/ds, dc/dt constant per patch.
+__device__ __forceinline__ void sphere6_jac(int patch, double s, double t, double x[3], double ds[3],
+                                            double dt[3]) {
+  double c[3], c00[3], c10[3], c01[3];
+  cube_point(patch, s, t, c);
+  cube_point(patch, 0.0, 0.0, c00);
+  cube_point(patch, 1.0, 0.0, c10);
+  cube_point(patch, 0.0, 1.0, c01);
+  const double inv = rsqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  double gs = 0.0, gt = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    x[k] = c[k] * inv;
+    gs += x[k] * (c10[k] - c00[k]);
+    gt += x[k] * (c01[k] - c00[k]);
+  }
+  for (int k = 0; k < 3; ++k) {
+    ds[k] = ((c10[k] - c00[k]) - x[k] * gs) * inv;
+    dt[k] = ((c01[k] - c00[k]) - x[k] * gt) * inv;
+  }
+}
+
+// Bernstein values and derivatives d/du of degree D at u
+template <int D>
+__device__ __forceinline__ void bern_d(double u, double b[D + 1], double db[D + 1]) {
+  const double v = 1.0 - u;
+  if (D == 0) {
+    b[0] = 1.0;
+    db[0] = 0.0;
+  } else if (D == 1) {
+    b[0] = v;
+    b[1] = u;
+    db[0] = -1.0;
+    db[1] = 1.0;
+  } else {
+    b[0] = v * v;
+    b[1] = 2.0 * u * v;
+    b[2] = u * u;
+    db[0] = -2.0 * v;
+    db[1] = 2.0 * (v - u);
+    db[2] = 2.0 * u;
+  }
+}
+
+// 1-D factors of component comp (0: degree P in the first parameter, P-1 in
+// the second; 1: the reverse) at local (u, v):
+//   values fa (first parameter) x fb (second), divergence factor dfa x fb or fa x dfb.
+template <int P>
+struct Comp1D {
+  double a[P + 1], da[P + 1], b[P + 1], db[P + 1];
+};
+
+template <int P>
+__device__ __forceinline__ void comp_factors(int comp, double u, double v, Comp1D<P>& f) {
+  // component 0: a = degree P in u, b = degree P-1 in v; component 1: a = degree P-1 in u, b = degree P in v
+  double hb[P + 1], hd[P + 1], lb[P], ld[P];
+  if (comp == 0) {
+    bern_d<P>(u, hb, hd);
+    bern_d<P - 1>(v, lb, ld);
+    for (int k = 0; k <= P; ++k) {
+      f.a[k] = hb[k];
+      f.da[k] = hd[k];
+    }
+    for (int k = 0; k < P; ++k) {
+      f.b[k] = lb[k];
+      f.db[k] = 0.0;
+    }
+  } else {
+    bern_d<P - 1>(u, lb, ld);
+    bern_d<P>(v, hb, hd);
+    for (int k = 0; k < P; ++k) {
+      f.a[k] = lb[k];
+      f.da[k] = 0.0;
+    }
+    for (int k = 0; k <= P; ++k) {
+      f.b[k] = hb[k];
+      f.db[k] = hd[k];
+    }
+  }
+}
+
+// value b and divergence factor d (d/du or d/dv on the local square) of local
+// function n (0 <= n < P (P+1)) of component comp
+template <int P>
+__device__ __forceinline__ void comp_fun(int comp, int n, const Comp1D<P>& f, double& b, double& d) {
+  if (comp == 0) {  // k1 <= P (first), k2 < P (second)
+    const int k1 = n % (P + 1), k2 = n / (P + 1);
+    b = f.a[k1] * f.b[k2];
+    d = f.da[k1] * f.b[k2];
+  } else {  // k1 < P, k2 <= P
+    const int k1 = n % P, k2 = n / P;
+    b = f.a[k1] * f.b[k2];
+    d = f.a[k1] * f.db[k2];
+  }
+}
+
+template <int P, int KIND>
+__global__ void __launch_bounds__(32 * kEfieWarps) k_efie_pairs(const PairRec* __restrict__ pairs, int64_t npairs,
+                                                                int L, int G, const double* __restrict__ gauss,
+                                                                double kre, double kim, double* __restrict__ N,
+                                                                int nld) {
+  constexpr int NH = P * (P + 1);  // local functions per component
+  constexpr int NSUB = KIND == kIdentical ? 8 : (KIND == kEdge ? 6 : (KIND == kVertex ? 4 : 1));
+  __shared__ double gx[kMaxG], gw[kMaxG];
+  if (threadIdx.x < G) {
+    gx[threadIdx.x] = gauss[threadIdx.x];
+    gw[threadIdx.x] = gauss[G + threadIdx.x];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int G2 = G * G, G4 = G2 * G2;
+  const int npts = NSUB * G4;
+  const int64_t per = int64_t(1) << (2 * L);
+  const double h = ldexp(1.0, -L);
+  const double hinv = 1.0 / h;
+  // -kappa^-2
+  const double kk_r = kre * kre - kim * kim, kk_i = 2.0 * kre * kim;
+  const double kk_n = kk_r * kk_r + kk_i * kk_i;
+  const double cr = -kk_r / kk_n, ci = kk_i / kk_n;
+  for (int64_t w = blockIdx.x * (int64_t)kEfieWarps + (threadIdx.x >> 5); w < npairs;
+       w += (int64_t)gridDim.x * kEfieWarps) {
+    const PairRec pr = pairs[w];
+    const int pe = int(pr.e / per), pf = int(pr.f / per);
+    uint32_t e1, e2, f1, f2;
+    morton_decode(uint32_t(pr.e % per), e1, e2);
+    morton_decode(uint32_t(pr.f % per), f1, f2);
+    const int ce = (pr.code >> 2) & 7, cf = (pr.code >> 5) & 7;
+    for (int quad = 0; quad < 4; ++quad) {
+      const int al = quad & 1, be = quad >> 1;
+      double ar[NH * NH], ai[NH * NH];
+#pragma unroll
+      for (int k = 0; k < NH * NH; ++k) ar[k] = ai[k] = 0.0;
+      for (int idx = lane; idx < npts; idx += 32) {
+        const int sub = idx / G4;
+        int rem = idx - sub * G4;
+        const int i0 = rem % G;
+        rem /= G;
+        const int i1 = rem % G;
+        rem /= G;
+        const int i2 = rem % G;
+        const int i3 = rem / G;
+        double ls1, ls2, lt1, lt2, wt;
+        if (KIND == kRegular) {
+          ls1 = gx[i0];
+          ls2 = gx[i1];
+          lt1 = gx[i2];
+          lt2 = gx[i3];
+          wt = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+        } else {
+          double s1, s2, t1, t2;
+          const double jac = duffy_point<KIND == kRegular ? kIdentical : KIND>(sub, gx[i0], gx[i1], gx[i2], gx[i3],
+                                                                                s1, s2, t1, t2);
+          wt = jac * gw[i0] * gw[i1] * gw[i2] * gw[i3];
+          apply_cmap(ce, s1, s2, ls1, ls2);
+          apply_cmap(cf, t1, t2, lt1, lt2);
+        }
+        double x[3], xs[3], xt[3], y[3], ys[3], yt[3];
+        sphere6_jac(pe, (e1 + ls1) * h, (e2 + ls2) * h, x, xs, xt);
+        sphere6_jac(pf, (f1 + lt1) * h, (f2 + lt2) * h, y, ys, yt);
+        const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+        double gr, gi;
+        kernel_value(true, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+        gr *= wt;
+        gi *= wt;
+        const double* ja = al == 0 ? xs : xt;
+        const double* jb = be == 0 ? ys : yt;
+        const double g = ja[0] * jb[0] + ja[1] * jb[1] + ja[2] * jb[2];
+        // P = G g (vector part), Q = -kappa^-2 G / h^2 (divergence part; d/du -> d/ds)
+        const double Pr = gr * g, Pi = gi * g;
+        const double Qr = (gr * cr - gi * ci) * hinv * hinv, Qi = (gr * ci + gi * cr) * hinv * hinv;
+        Comp1D<P> fs, ft;
+        comp_factors<P>(al, ls1, ls2, fs);
+        comp_factors<P>(be, lt1, lt2, ft);
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+          double bi, di;
+          comp_fun<P>(al, i, fs, bi, di);
+#pragma unroll
+          for (int j = 0; j < NH; ++j) {
+            double bj, dj;
+            comp_fun<P>(be, j, ft, bj, dj);
+            const double bb = bi * bj, dd = di * dj;
+            ar[i * NH + j] = fma(Pr, bb, fma(Qr, dd, ar[i * NH + j]));
+            ai[i * NH + j] = fma(Pi, bb, fma(Qi, dd, ai[i * NH + j]));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NH * NH; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
+          ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], o);
+        }
+      }
+      const double sc = kInv4Pi * h * h * h * h;
+      const int io = al * NH, jo = be * NH;
+#pragma unroll
+      for (int k = 0; k < NH * NH; ++k) {
+        if ((k & 31) != lane) continue;
+        const int i = io + k / NH, j = jo + k % NH;
+        const long long o1 = pr.off1 + (long long)i * nld + j;
+        N[o1 * 2] = ar[k] * sc;
+        N[o1 * 2 + 1] = ai[k] * sc;
+        if (pr.off2 >= 0) {
+          const long long o2 = pr.off2 + (long long)j * nld + i;
+          N[o2 * 2] = ar[k] * sc;
+          N[o2 * 2 + 1] = ai[k] * sc;
+        }
+      }
+    }
+  }
+}
+
+// Load vectors b_loc[e, i][rhs] = -h^2 sum_q w_q E_inc(x_q) . (d_alpha gamma(q) b_i(q)),
+// E_inc = pol exp(-i kappa dir . x).  One thread per (element, rhs).
+template <int P>
+__global__ void k_efie_rhs_local(int L, int64_t nelem, int G, const double* __restrict__ gx,
+                                 const double* __restrict__ gw, const double* __restrict__ prm, int nrhs, double kre,
+                                 double kim, double* __restrict__ bl) {
+  constexpr int NH = P * (P + 1), NLOC = 2 * NH;
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nelem * nrhs) return;
+  const int64_t e = id / nrhs;
+  const int r = int(id % nrhs);
+  const int64_t per = int64_t(1) << (2 * L);
+  const int patch = int(e / per);
+  uint32_t i1, i2;
+  morton_decode(uint32_t(e % per), i1, i2);
+  const double h = ldexp(1.0, -L);
+  const double* pp = prm + 6 * r;
+  double accr[NLOC], acci[NLOC];
+  for (int k = 0; k < NLOC; ++k) accr[k] = acci[k] = 0.0;
+  for (int b = 0; b < G; ++b)
+    for (int a = 0; a < G; ++a) {
+      const double u = gx[a], v = gx[b];
+      double x[3], xs[3], xt[3];
+      sphere6_jac(patch, (i1 + u) * h, (i2 + v) * h, x, xs, xt);
+      // exp(-i kappa d.x) = exp(kim d.x) (cos(kre d.x) - i sin(kre d.x))
+      const double dx = pp[0] * x[0] + pp[1] * x[1] + pp[2] * x[2];
+      double sn, cs;
+      sincos(kre * dx, &sn, &cs);
+      const double am = exp(kim * dx) * gw[a] * gw[b] * h * h;
+      const double er = am * cs, ei = -am * sn;
+      const double ps = pp[3] * xs[0] + pp[4] * xs[1] + pp[5] * xs[2];  // pol . d_s gamma
+      const double pt = pp[3] * xt[0] + pp[4] * xt[1] + pp[5] * xt[2];
+      for (int comp = 0; comp < 2; ++comp) {
+        Comp1D<P> f;
+        comp_factors<P>(comp, u, v, f);
+        const double pj = comp == 0 ? ps : pt;
+        for (int n = 0; n < NH; ++n) {
+          double bv, dv;
+          comp_fun<P>(comp, n, f, bv, dv);
+          accr[comp * NH + n] -= er * pj * bv;
+          acci[comp * NH + n] -= ei * pj * bv;
+        }
+      }
+    }
+  const int ncol = 2 * nrhs;
+  for (int k = 0; k < NLOC; ++k) {
+    bl[(e * NLOC + k) * ncol + 2 * r] = accr[k];
+    bl[(e * NLOC + k) * ncol + 2 * r + 1] = acci[k];
+  }
+}
+
+// Per element quadrature point: position, the current D gamma phi (3 complex)
+// and the divergence (1 complex), weights included, for every rhs.
+template <int P>
+__global__ void k_efie_density(const double* __restrict__ rl, int L, int64_t nelem, int G,
+                               const double* __restrict__ gx, const double* __restrict__ gw, int nrhs,
+                               double* __restrict__ Y, double* __restrict__ J) {
+  constexpr int NH = P * (P + 1), NLOC = 2 * NH;
+  const int G2 = G * G;
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nelem * G2) return;
+  const int64_t e = id / G2;
+  const int q = int(id % G2);
+  const int64_t per = int64_t(1) << (2 * L);
+  const int patch = int(e / per);
+  uint32_t i1, i2;
+  morton_decode(uint32_t(e % per), i1, i2);
+  const double h = ldexp(1.0, -L);
+  const double u = gx[q % G], v = gx[q / G];
+  double x[3], xs[3], xt[3];
+  sphere6_jac(patch, (i1 + u) * h, (i2 + v) * h, x, xs, xt);
+  Y[id * 3] = x[0];
+  Y[id * 3 + 1] = x[1];
+  Y[id * 3 + 2] = x[2];
+  const double wq = gw[q % G] * gw[q / G] * h * h;
+  const int ncol = 2 * nrhs;
+  Comp1D<P> f0, f1;
+  comp_factors<P>(0, u, v, f0);
+  comp_factors<P>(1, u, v, f1);
+  for (int r = 0; r < nrhs; ++r) {
+    double js_r = 0, js_i = 0, jt_r = 0, jt_i = 0, dv_r = 0, dv_i = 0;
+    for (int k = 0; k < NLOC; ++k) {
+      const int comp = k / NH, n = k % NH;
+      double bv, dvv;
+      comp_fun<P>(comp, n, comp == 0 ? f0 : f1, bv, dvv);
+      const double cr = rl[(e * NLOC + k) * ncol + 2 * r], ci = rl[(e * NLOC + k) * ncol + 2 * r + 1];
+      if (comp == 0) {
+        js_r += bv * cr;
+        js_i += bv * ci;
+      } else {
+        jt_r += bv * cr;
+        jt_i += bv * ci;
+      }
+      dv_r += dvv * cr;
+      dv_i += dvv * ci;
+    }
+    double* out = J + (id * nrhs + r) * 8;
+    for (int c = 0; c < 3; ++c) {
+      out[2 * c] = wq * (xs[c] * js_r + xt[c] * jt_r);
+      out[2 * c + 1] = wq * (xs[c] * js_i + xt[c] * jt_i);
+    }
+    out[6] = wq * dv_r / h;  // divergence in patch parameters (d/du = h d/ds)
+    out[7] = wq * dv_i / h;
+  }
+}
+
+// Block per (evaluation point, rhs): E(x) = sum_k G (D gamma phi)_k + kappa^-2 grad_x G (div phi)_k,
+// grad_x G = G (-i kappa - 1/r) (x - y) / r.
+__global__ void k_efie_field(const double* __restrict__ pts, const double* __restrict__ Y,
+                             const double* __restrict__ J, int64_t nsrc, int nrhs, double kre, double kim,
+                             double* __restrict__ out, int64_t npts) {
+  const int64_t ip = blockIdx.x;
+  const int r = blockIdx.y;
+  const double x0 = pts[ip * 3], x1 = pts[ip * 3 + 1], x2 = pts[ip * 3 + 2];
+  // 1 / kappa^2
+  const double kk_r = kre * kre - kim * kim, kk_i = 2.0 * kre * kim;
+  const double kk_n = kk_r * kk_r + kk_i * kk_i;
+  const double ikr = kk_r / kk_n, iki = -kk_i / kk_n;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t k = threadIdx.x; k < nsrc; k += blockDim.x) {
+    const double d[3] = {x0 - Y[k * 3], x1 - Y[k * 3 + 1], x2 - Y[k * 3 + 2]};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double rinv = rsqrt(r2);
+    const double rr = r2 * rinv;
+    double sn, cs;
+    sincos(kre * rr, &sn, &cs);
+    const double am = exp(kim * rr) * rinv * kInv4Pi;
+    const double gr = am * cs, gi = -am * sn;
+    // factor (-i kappa - 1/r) / r
+    const double fr = (kim - rinv) * rinv, fi = -kre * rinv;
+    const double hr = gr * fr - gi * fi, hi = gr * fi + gi * fr;  // G (-i kappa - 1/r) / r
+    const double* jj = J + (k * nrhs + r) * 8;
+    // kappa^-2 * div
+    const double qr = ikr * jj[6] - iki * jj[7], qi = ikr * jj[7] + iki * jj[6];
+    const double tr = hr * qr - hi * qi, ti = hr * qi + hi * qr;
+    for (int c = 0; c < 3; ++c) {
+      acc[2 * c] += gr * jj[2 * c] - gi * jj[2 * c + 1] + tr * d[c];
+      acc[2 * c + 1] += gr * jj[2 * c + 1] + gi * jj[2 * c] + ti * d[c];
+    }
+  }
+  __shared__ double red[6][32];
+  for (int c = 0; c < 6; ++c)
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) red[c][wid] = acc[c];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+    out[((int64_t)r * npts + ip) * 6 + threadIdx.x] = s;
+  }
+}
+
+template <int P>
+void launch_efie_pairs(Op& o, cudaEvent_t* ev) {
+  const cudaStream_t s = o.stream;
+  const int threads = 32 * kEfieWarps;
+  auto grid_of = [](int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + kEfieWarps - 1) / kEfieWarps, 152 * 64))); };
+  if (o.npairs[kRegular] > 0) {
+    k_efie_pairs<P, kRegular><<<grid_of(o.npairs[kRegular]), threads, 0, s>>>(
+        o.d_pairs[kRegular], o.npairs[kRegular], o.L, o.g_reg, o.d_gauss + o.gauss_off[kRegular], o.kre, o.kim, o.d_N, o.nld);
+    launched("k_efie_pairs regular");
+  }
+  cuda_check(cudaEventRecord(ev[2], s), "event");
+  if (o.npairs[kIdentical] > 0) {
+    k_efie_pairs<P, kIdentical><<<grid_of(o.npairs[kIdentical]), threads, 0, s>>>(
+        o.d_pairs[kIdentical], o.npairs[kIdentical], o.L, o.g_kind[kIdentical], o.d_gauss + o.gauss_off[kIdentical],
+        o.kre, o.kim, o.d_N, o.nld);
+    launched("k_efie_pairs identical");
+  }
+  cuda_check(cudaEventRecord(ev[3], s), "event");
+  if (o.npairs[kEdge] > 0) {
+    k_efie_pairs<P, kEdge><<<grid_of(o.npairs[kEdge]), threads, 0, s>>>(
+        o.d_pairs[kEdge], o.npairs[kEdge], o.L, o.g_kind[kEdge], o.d_gauss + o.gauss_off[kEdge], o.kre, o.kim,
+        o.d_N, o.nld);
+    launched("k_efie_pairs edge");
+  }
+  cuda_check(cudaEventRecord(ev[4], s), "event");
+  if (o.npairs[kVertex] > 0) {
+    k_efie_pairs<P, kVertex><<<grid_of(o.npairs[kVertex]), threads, 0, s>>>(
+        o.d_pairs[kVertex], o.npairs[kVertex], o.L, o.g_kind[kVertex], o.d_gauss + o.gauss_off[kVertex], o.kre,
+        o.kim, o.d_N, o.nld);
+    launched("k_efie_pairs vertex");
+  }
+  cuda_check(cudaEventRecord(ev[5], s), "event");
+}
+
+}  // namespace
+
+void efie_pair_kernels(Op& o, cudaEvent_t* ev) {
+  if (o.d == 1)
+    launch_efie_pairs<1>(o, ev);
+  else
+    launch_efie_pairs<2>(o, ev);
+}
+
+void efie_rhs_local(const Op& o, const double* gx, const double* gw, int G, const double* prm_dev, int nrhs,
+                    double* bl, cudaStream_t s) {
+  const int64_t n = o.nelem * nrhs;
+  const int grid = int((n + 127) / 128);
+  if (o.d == 1)
+    k_efie_rhs_local<1><<<grid, 128, 0, s>>>(o.L, o.nelem, G, gx, gw, prm_dev, nrhs, o.kre, o.kim, bl);
+  else
+    k_efie_rhs_local<2><<<grid, 128, 0, s>>>(o.L, o.nelem, G, gx, gw, prm_dev, nrhs, o.kre, o.kim, bl);
+  launched("k_efie_rhs_local");
+}
+
+void efie_field(const Op& o, const double* rl, const double* gx, const double* gw, int G, const double* pts,
+                int64_t npts, int nrhs, double* out, cudaStream_t s) {
+  const int64_t nq = o.nelem * G * G;
+  DevBuf Y(sizeof(double) * nq * 3), J(sizeof(double) * nq * nrhs * 8);
+  const int grid = int((nq + 127) / 128);
+  if (o.d == 1)
+    k_efie_density<1><<<grid, 128, 0, s>>>(rl, o.L, o.nelem, G, gx, gw, nrhs, static_cast<double*>(Y.p),
+                                           static_cast<double*>(J.p));
+  else
+    k_efie_density<2><<<grid, 128, 0, s>>>(rl, o.L, o.nelem, G, gx, gw, nrhs, static_cast<double*>(Y.p),
+                                           static_cast<double*>(J.p));
+  launched("k_efie_density");
+  if (npts > 0) {
+    k_efie_field<<<dim3(unsigned(npts), unsigned(nrhs)), 256, 0, s>>>(
+        pts, static_cast<double*>(Y.p), static_cast<double*>(J.p), nq, nrhs, o.kre, o.kim, out, npts);
+    launched("k_efie_field");
+  }
+  cuda_check(cudaStreamSynchronize(s), "efie field sync");
+}
+
+}  // namespace bembel

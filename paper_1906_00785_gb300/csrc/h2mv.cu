@@ -92,6 +92,60 @@ __global__ void k_scatter(const T* __restrict__ yl, T* __restrict__ y, const dou
   y[((int64_t)r * ndofs + g) * C + comp] = T(acc);
 }
 
+// S^1 (EFIE): extraction as CSR.  Gather: xl[row][col] = sum val * x[col_k][col];
+// scatter with the transposed CSR (rows = global dofs).  API vectors are
+// column-major (ndofs x nrhs, C reals per entry); local vectors dof-major.
+template <typename T>
+__global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict__ cols,
+                             const double* __restrict__ val, const T* __restrict__ x, T* __restrict__ xl,
+                             int64_t ndofs, int64_t nlocal, int ncol, int C) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nlocal * ncol) return;
+  const int64_t row = id / ncol;
+  const int col = int(id % ncol);
+  const int r = col / C, comp = col % C;
+  const T* xr = x + (int64_t)r * ndofs * C + comp;
+  double acc = 0.0;
+  for (int k = ptr[row]; k < ptr[row + 1]; ++k) acc += val[k] * (double)xr[(int64_t)cols[k] * C];
+  xl[id] = T(acc);
+}
+
+template <typename T>
+__global__ void k_csr_scatter(const int* __restrict__ ptr, const int* __restrict__ rows,
+                              const double* __restrict__ val, const T* __restrict__ yl, T* __restrict__ y,
+                              int64_t ndofs, int ncol, int C) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= ndofs * ncol) return;
+  const int64_t g = id / ncol;
+  const int col = int(id % ncol);
+  const int r = col / C, comp = col % C;
+  double acc = 0.0;
+  for (int k = ptr[g]; k < ptr[g + 1]; ++k) acc += val[k] * (double)yl[(int64_t)rows[k] * ncol + col];
+  y[((int64_t)r * ndofs + g) * C + comp] = T(acc);
+}
+
+// element-local <-> global for either space
+template <typename T>
+void gather_l(const Op& o, const T* x, T* xl, int ncol, int C, cudaStream_t s) {
+  if (o.efie)
+    k_csr_gather<T><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(o.d_e_ptr, o.d_e_col, o.d_e_val, x, xl,
+                                                                      o.ndofs, o.nlocal, ncol, C);
+  else
+    k_gather<T><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(x, xl, o.d_ex, o.L, o.d, o.n1, o.ndofs, o.nlocal,
+                                                                  ncol, C);
+  launched("k_gather");
+}
+
+template <typename T>
+void scatter_l(const Op& o, const T* yl, T* y, int ncol, int C, cudaStream_t s) {
+  if (o.efie)
+    k_csr_scatter<T><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(o.d_et_ptr, o.d_et_col, o.d_et_val, yl, y,
+                                                                      o.ndofs, ncol, C);
+  else
+    k_scatter<T><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
+  launched("k_scatter");
+}
+
 // xh[leaf][a][col] = sum_i V[i][a] xl[leaf*nld + i][col]
 template <typename T>
 __global__ void k_leaf_up(const T* __restrict__ xl, T* __restrict__ xh, const T* __restrict__ V, int64_t nleaf,
@@ -510,8 +564,7 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
   T* xh = yl + o.nlocal * ncol;
   T* yh = xh + o.nclusters * q2 * ncol;
   const int tb = 256;
-  k_gather<T><<<blocks_for(o.nlocal * ncol, tb), tb, 0, s>>>(x, xl, o.d_ex, o.L, o.d, o.n1, o.ndofs, o.nlocal, ncol, C);
-  launched("k_gather");
+  gather_l<T>(o, x, xl, ncol, C, s);
   if (q2 > 0) {
     const int64_t leaf_off = o.lvl_off[o.leaf];
     const int ls = std::max(0, o.leaf - 3);
@@ -593,8 +646,7 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     launch_bsr<T, true, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   else
     launch_bsr<T, false, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
-  k_scatter<T><<<blocks_for(o.ndofs * ncol, tb), tb, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
-  launched("k_scatter");
+  scatter_l<T>(o, yl, y, ncol, C, s);
 }
 
 }  // namespace
@@ -602,16 +654,13 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
 void gather_to_local(const Op& o, const double* x, double* xl, int nrhs, cudaStream_t s) {
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
-  k_gather<double><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(x, xl, o.d_ex, o.L, o.d, o.n1, o.ndofs, o.nlocal,
-                                                                    ncol, C);
-  launched("k_gather");
+  gather_l<double>(o, x, xl, ncol, C, s);
 }
 
 void scatter_to_global(const Op& o, const double* yl, double* y, int nrhs, cudaStream_t s) {
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
-  k_scatter<double><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
-  launched("k_scatter");
+  scatter_l<double>(o, yl, y, ncol, C, s);
 }
 
 size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32) {
@@ -687,9 +736,7 @@ void precond_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const
   const int ncol = nrhs * C;
   T* xl = static_cast<T*>(o.d_scratch);
   T* yl = xl + o.nlocal * ncol;
-  const int tb = 256;
-  k_gather<T><<<blocks_for(o.nlocal * ncol, tb), tb, 0, s>>>(x, xl, o.d_ex, o.L, o.d, o.n1, o.ndofs, o.nlocal, ncol, C);
-  launched("k_gather");
+  gather_l<T>(o, x, xl, ncol, C, s);
   const bool learned = o.active_precond == BEMBEL_PRECOND_LEARNED && o.d_lw;
   if (learned) learned_scale_local(o, xl, nrhs, sizeof(T) == 4, s);
   cuda_check(cudaMemsetAsync(yl, 0, sizeof(T) * o.nlocal * ncol, s), "yl clear");
@@ -698,8 +745,7 @@ void precond_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const
   else
     launch_bsr<T, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   if (learned) learned_scale_local(o, yl, nrhs, sizeof(T) == 4, s);
-  k_scatter<T><<<blocks_for(o.ndofs * ncol, tb), tb, 0, s>>>(yl, y, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol, C);
-  launched("k_scatter");
+  scatter_l<T>(o, yl, y, ncol, C, s);
 }
 }  // namespace
 
@@ -707,28 +753,18 @@ void local_gather(const Op& o, const void* x, void* xl, int nrhs, bool fp32, cud
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
   if (fp32)
-    k_gather<float><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(static_cast<const float*>(x),
-                                                                     static_cast<float*>(xl), o.d_ex, o.L, o.d, o.n1,
-                                                                     o.ndofs, o.nlocal, ncol, C);
+    gather_l<float>(o, static_cast<const float*>(x), static_cast<float*>(xl), ncol, C, s);
   else
-    k_gather<double><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(static_cast<const double*>(x),
-                                                                      static_cast<double*>(xl), o.d_ex, o.L, o.d,
-                                                                      o.n1, o.ndofs, o.nlocal, ncol, C);
-  launched("k_gather");
+    gather_l<double>(o, static_cast<const double*>(x), static_cast<double*>(xl), ncol, C, s);
 }
 
 void local_scatter(const Op& o, const void* yl, void* y, int nrhs, bool fp32, cudaStream_t s) {
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
   if (fp32)
-    k_scatter<float><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(static_cast<const float*>(yl),
-                                                                     static_cast<float*>(y), o.d_ex, o.L, o.d, o.n1,
-                                                                     o.ndofs, ncol, C);
+    scatter_l<float>(o, static_cast<const float*>(yl), static_cast<float*>(y), ncol, C, s);
   else
-    k_scatter<double><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(static_cast<const double*>(yl),
-                                                                      static_cast<double*>(y), o.d_ex, o.L, o.d,
-                                                                      o.n1, o.ndofs, ncol, C);
-  launched("k_scatter");
+    scatter_l<double>(o, static_cast<const double*>(yl), static_cast<double*>(y), ncol, C, s);
 }
 
 void blockdiag_apply(const Op& o, const void* Dinv, const void* xl, void* yl, int nrhs, bool fp32, cudaStream_t s) {

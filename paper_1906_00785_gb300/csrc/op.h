@@ -78,9 +78,18 @@ struct Op {
   double* d_Xq = nullptr;  // nelem * g_reg^2 * 3
   double* d_BW = nullptr;  // g_reg^2 * nloc: w_p h^2 B_k(u_p)
   double* d_gauss = nullptr;  // [g_reg nodes] then per singular kind [nodes, weights]
-  int gauss_off[4] = {0, 0, 0, 0};  // offset of each singular kind's table in d_gauss
+  int gauss_off[4] = {0, 0, 0, 0};  // offset of each pair kind's [nodes][weights] table in d_gauss
   double* d_nodes = nullptr;  // nclusters * q2 * 3 cluster interpolation points
   float* d_nodes32 = nullptr; // FP32 copy (x, y, z, 0) per point for the on-the-fly FP32 coupling
+
+  // EFIE on the S^1 space: signed extraction E (element-local <- global) as CSR and its transpose
+  bool efie = false;
+  int* d_e_ptr = nullptr;
+  int* d_e_col = nullptr;
+  double* d_e_val = nullptr;
+  int* d_et_ptr = nullptr;
+  int* d_et_col = nullptr;
+  double* d_et_val = nullptr;
 
   // matvec scratch (grown on demand), FP64 and FP32 views share the bytes
   int bsr_chunk = 32;        // blocks per warp in the block-sparse products
@@ -128,6 +137,13 @@ void alloc_assembly_outputs(Op& o);     // Xq, near field, coupling, FP32 near c
 // several operators sharing (op, degree, q, options): tabulation, one
 // persistent launch for all near-field pairs and coupling blocks, FP32 copies
 void run_assembly_batch(const std::vector<Op*>& ops);
+// efie.cu: S^1 element-pair quadrature (phases 1-4 with events ev[2..5]),
+// local load vectors of plane waves, and the scattered field at points
+void efie_pair_kernels(Op& o, cudaEvent_t* ev);
+void efie_rhs_local(const Op& o, const double* gx, const double* gw, int G, const double* prm_dev, int nrhs,
+                    double* bl, cudaStream_t s);
+void efie_field(const Op& o, const double* rl, const double* gx, const double* gw, int G, const double* pts,
+                int64_t npts, int nrhs, double* out, cudaStream_t s);
 // h2mv.cu
 void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
 void ensure_scratch(Op& o, size_t bytes);

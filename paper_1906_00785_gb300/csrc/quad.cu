@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "op.h"
+#include "pairrules.cuh"
 
 namespace bembel {
 
@@ -23,21 +24,6 @@ namespace {
 
 constexpr int kWarps = 4;  // warps per block in the pair kernels
 
-__device__ __forceinline__ void kernel_value(bool cplx, double r2, double kre, double kim, double& gr, double& gi) {
-  const double rinv = rsqrt(r2);
-  if (!cplx) {
-    gr = rinv;
-    gi = 0.0;
-  } else {
-    // exp(-i kappa r) = exp(kim r) (cos(kre r) - i sin(kre r))
-    const double r = r2 * rinv;
-    double sn, cs;
-    sincos(kre * r, &sn, &cs);
-    const double a = (kim != 0.0 ? exp(kim * r) : 1.0) * rinv;
-    gr = a * cs;
-    gi = -a * sn;
-  }
-}
 
 // gamma at regular point id = e * G^2 + p of element e
 __device__ __forceinline__ void tabulate_point(const Geom& g, int L, int G, const double* __restrict__ gx, double h,
@@ -148,52 +134,6 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_regular(const PairRec* __r
   const int lane = threadIdx.x & 31;
   for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < npairs; w += (int64_t)gridDim.x * kWarps)
     regular_pair<D, CPLX>(pairs[w], Xq, BW, ubuf, G2, kre, kim, N, nld, lane);
-}
-
-// Point of a Duffy rule in canonical position.  x = (x0, x1, x2, x3) are the
-// Gauss variables in [0,1]^4, sub the sub-domain.  Returns (s1, s2, t1, t2) and
-// the Jacobian factor.
-//  KIND 1 (identical): z = t - s in quadrant (sg1, sg2) = (+-1, +-1) from sub & 3,
-//     triangle sub >> 2: (a, b) = (xi, xi eta) or (xi eta, xi); |z| = (a, b);
-//     s_k = max(0, -z_k) + u_k (1 - |z_k|), t = s + z; Jacobian xi (1-a)(1-b).
-//  KIND 2 (common edge {s1 = 0} = {t1 = 0}): sign of z = t2 - s2 from sub / 3,
-//     pyramid c = sub % 3 puts xi on coordinate c of (s1, t1, |z|), the others
-//     xi eta1, xi eta2; s2 = max(0, -z) + u (1 - |z|); Jacobian xi^2 (1 - |z|).
-//  KIND 3 (common vertex s = t = 0): pyramid c = sub puts xi on coordinate c of
-//     (s1, s2, t1, t2), the others xi eta1..3; Jacobian xi^3.
-template <int KIND>
-__device__ __forceinline__ double duffy_point(int sub, double x0, double x1, double x2, double x3, double& s1,
-                                              double& s2, double& t1, double& t2) {
-  const double xi = x0;
-  if (KIND == kIdentical) {
-    const double a = (sub >> 2) == 0 ? xi : xi * x1;
-    const double b = (sub >> 2) == 0 ? xi * x1 : xi;
-    const double z1 = (sub & 1) ? -a : a;
-    const double z2 = (sub & 2) ? -b : b;
-    s1 = fmax(0.0, -z1) + x2 * (1.0 - a);
-    s2 = fmax(0.0, -z2) + x3 * (1.0 - b);
-    t1 = s1 + z1;
-    t2 = s2 + z2;
-    return xi * (1.0 - a) * (1.0 - b);
-  } else if (KIND == kEdge) {
-    // (s1, t1, |z|) = xi at position c, (xi eta1, xi eta2) in order elsewhere
-    const int c = sub % 3;
-    const double e1 = xi * x1, e2 = xi * x2;
-    s1 = c == 0 ? xi : e1;
-    t1 = c == 0 ? e1 : (c == 1 ? xi : e2);
-    const double az = c == 2 ? xi : e2;
-    const double z = (sub < 3) ? az : -az;
-    s2 = fmax(0.0, -z) + x3 * (1.0 - az);
-    t2 = s2 + z;
-    return xi * xi * (1.0 - az);
-  } else {
-    const double e1 = xi * x1, e2 = xi * x2, e3 = xi * x3;
-    s1 = sub == 0 ? xi : e1;
-    s2 = sub == 0 ? e1 : (sub == 1 ? xi : e2);
-    t1 = sub <= 1 ? e2 : (sub == 2 ? xi : e3);
-    t2 = sub <= 2 ? e3 : xi;
-    return xi * xi * xi;
-  }
 }
 
 // One touching pair per warp; lanes stride over the nsub * g^4 rule points and
@@ -433,14 +373,18 @@ void run_assembly_kernels(Op& o) {
     launched("k_tabulate");
   }
   cuda_check(cudaEventRecord(ev[1], s), "event");
-  // A4 + A5: near field
-  switch (o.d * 2 + (o.cplx ? 1 : 0)) {
-    case 0: launch_pairs<0, false>(o, ev); break;
-    case 1: launch_pairs<0, true>(o, ev); break;
-    case 2: launch_pairs<1, false>(o, ev); break;
-    case 3: launch_pairs<1, true>(o, ev); break;
-    case 4: launch_pairs<2, false>(o, ev); break;
-    default: launch_pairs<2, true>(o, ev); break;
+  // A4 + A5: near field (S^1 functions for the EFIE)
+  if (o.efie) {
+    efie_pair_kernels(o, ev);
+  } else {
+    switch (o.d * 2 + (o.cplx ? 1 : 0)) {
+      case 0: launch_pairs<0, false>(o, ev); break;
+      case 1: launch_pairs<0, true>(o, ev); break;
+      case 2: launch_pairs<1, false>(o, ev); break;
+      case 3: launch_pairs<1, true>(o, ev); break;
+      case 4: launch_pairs<2, false>(o, ev); break;
+      default: launch_pairs<2, true>(o, ev); break;
+    }
   }
   // A6: coupling
   if (o.nfar > 0) {

@@ -204,6 +204,17 @@ struct Buf {
 void rhs_device(const Op& o, int kind, const double* params, int nrhs, int G, void* b) {
   const cudaStream_t s = o.stream;
   const int C = o.cplx ? 2 : 1;
+  if (o.efie) {
+    // EFIE: plane waves E_inc = pol exp(-i kappa dir . x), 6 parameters per column
+    Buf gt(sizeof(double) * 2 * G), pr(sizeof(double) * 6 * nrhs), bl(sizeof(double) * o.nlocal * nrhs * 2);
+    gauss_table(G, static_cast<double*>(gt.p), s);
+    cuda_check(cudaMemcpyAsync(pr.p, params, sizeof(double) * 6 * nrhs, cudaMemcpyHostToDevice, s), "params");
+    const double* gx = static_cast<double*>(gt.p);
+    efie_rhs_local(o, gx, gx + G, G, static_cast<const double*>(pr.p), nrhs, static_cast<double*>(bl.p), s);
+    scatter_to_global(o, static_cast<double*>(bl.p), static_cast<double*>(b), nrhs, s);
+    cuda_check(cudaStreamSynchronize(s), "rhs sync");
+    return;
+  }
   Buf gt(sizeof(double) * 2 * G), pr(sizeof(double) * 3 * nrhs), bl(sizeof(double) * o.nlocal * nrhs * C);
   gauss_table(G, static_cast<double*>(gt.p), s);
   cuda_check(cudaMemcpyAsync(pr.p, params, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, s), "params");
@@ -241,6 +252,10 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
   const double* gx = static_cast<double*>(gt.p);
   const double* gw = gx + G;
   gather_to_local(o, static_cast<const double*>(rho), static_cast<double*>(rl.p), nrhs, s);
+  if (o.efie) {
+    efie_field(o, static_cast<double*>(rl.p), gx, gw, G, pts, npts, nrhs, static_cast<double*>(out), s);
+    return;
+  }
   const int64_t nq = o.nelem * G2;
   k_tab_points<<<int((nq + 255) / 256), 256, 0, s>>>(o.geom, o.L, o.nelem, G, gx, o.h, static_cast<double*>(Y.p));
   launched("kernel");

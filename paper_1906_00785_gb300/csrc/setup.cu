@@ -14,6 +14,7 @@
 //   element-local Bernstein basis.
 #include <algorithm>
 #include <array>
+#include <map>
 #include <cstring>
 #include <thread>
 #include <unordered_map>
@@ -124,11 +125,6 @@ void solve_small(int n, std::vector<double> A, std::vector<double>& x) {
   for (int r = 0; r < n; ++r) x[r] = A[r * (n + 1) + n] / A[r * (n + 1) + r];
 }
 
-struct Ball {
-  double c[3];
-  double r;
-};
-
 template <typename T>
 T* upload(const std::vector<T>& v) {
   if (v.empty()) return nullptr;
@@ -136,6 +132,158 @@ T* upload(const std::vector<T>& v) {
   cuda_check(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
   return p;
 }
+
+// 1-D Bezier extraction of the open-knot B-splines of degree deg with nel1
+// uniform elements: B-spline (i + j) restricted to element i equals
+// sum_k ex[(i (deg+1) + j) (deg+1) + k] Bern_k((x - x_i) nel1), found by
+// interpolation at deg + 1 interior points of the element.
+std::vector<double> extraction_1d(int deg, int nel1) {
+  const int n = deg + 1;
+  std::vector<double> ex((size_t)nel1 * n * n);
+  std::vector<double> A(n * (n + 1)), sol;
+  for (int i = 0; i < nel1; ++i)
+    for (int j = 0; j < n; ++j) {
+      for (int r = 0; r < n; ++r) {
+        const double u = (r + 0.5) / n;
+        for (int k = 0; k < n; ++k) A[r * (n + 1) + k] = bernstein_h(deg, k, u);
+        A[r * (n + 1) + n] = bspline_h(deg, nel1, i + j, (i + u) / nel1);
+      }
+      solve_small(n, A, sol);
+      for (int k = 0; k < n; ++k) ex[((size_t)i * n + j) * n + k] = sol[k];
+    }
+  return ex;
+}
+
+// S^1 space of App. E on the six patches: global numbering with the edge glue
+// (normal continuity) and the signed extraction E (element-local Bernstein
+// functions <- global dofs) as CSR, plus its transpose.
+//  patch-local index: first component i1 + np j2 (i1 < np, j2 < nq), then
+//  second component np nq + j1 + nq i2 (j1 < nq, i2 < np), np = 2^L + p, nq = np - 1;
+//  global numbers follow patches and patch-local indices in order; an edge
+//  function whose partner on the neighbouring patch already has a number takes
+//  it with coefficient -sign_own * sign_partner (sign +1 on the sides s = 1,
+//  t = 1 and -1 on s = 0, t = 0: equal and opposite outward fluxes);
+//  element-local functions: first component k1 + (p+1) k2 (k1 <= p, k2 < p),
+//  second p (p+1) + k1 + p k2 (k1 < p, k2 <= p).
+void build_s1_space(Op& o) {
+  const int p = o.d, nel1 = o.nel1;
+  const int np = nel1 + p, nq = nel1 + p - 1;
+  const int per_patch = 2 * np * nq;
+  auto c1 = [&](int i1, int j2) { return i1 + np * j2; };
+  auto c2 = [&](int j1, int i2) { return np * nq + j1 + nq * i2; };
+  // sides: 0 s=0, 1 s=1, 2 t=0, 3 t=1; edge functions along the side and the flux sign
+  auto side_fun = [&](int sd, std::vector<int>& f) {
+    f.clear();
+    for (int j = 0; j < nq; ++j)
+      f.push_back(sd < 2 ? c1(sd == 0 ? 0 : np - 1, j) : c2(j, sd == 2 ? 0 : np - 1));
+    return (sd == 1 || sd == 3) ? 1 : -1;
+  };
+  using Key = std::array<long long, 3>;
+  auto key_of = [&](int patch, double s0, double t0) {
+    double x[3];
+    gamma_eval(o.geom, patch, s0, t0, x);
+    return Key{llround(x[0] * 1e9), llround(x[1] * 1e9), llround(x[2] * 1e9)};
+  };
+  const double ends[4][4] = {{0, 0, 0, 1}, {1, 0, 1, 1}, {0, 0, 1, 0}, {0, 1, 1, 1}};
+  std::map<std::pair<Key, Key>, std::vector<std::array<int, 3>>> sides;  // (min key, max key) -> (patch, side, forward)
+  for (int P = 0; P < 6; ++P)
+    for (int sd = 0; sd < 4; ++sd) {
+      const Key a = key_of(P, ends[sd][0], ends[sd][1]), b = key_of(P, ends[sd][2], ends[sd][3]);
+      const bool fwd = a < b;
+      sides[fwd ? std::make_pair(a, b) : std::make_pair(b, a)].push_back({P, sd, fwd ? 1 : 0});
+    }
+  // partner of each edge function: (patch, local) -> (patch', local', coefficient)
+  std::vector<std::array<int, 3>> partner((size_t)6 * per_patch, {-1, -1, 0});
+  std::vector<int> fa, fb;
+  for (auto& kv : sides) {
+    if (kv.second.size() != 2) fail(BEMBEL_EINVAL, "S^1 space: every patch edge must be shared by two patches");
+    const auto A = kv.second[0], B = kv.second[1];
+    const int sa = side_fun(A[1], fa), sb = side_fun(B[1], fb);
+    if (A[2] != B[2]) std::reverse(fb.begin(), fb.end());
+    for (int j = 0; j < nq; ++j) {
+      partner[(size_t)A[0] * per_patch + fa[j]] = {B[0], fb[j], -sa * sb};
+      partner[(size_t)B[0] * per_patch + fb[j]] = {A[0], fa[j], -sa * sb};
+    }
+  }
+  std::vector<long long> gid((size_t)6 * per_patch, -1);
+  std::vector<double> gco((size_t)6 * per_patch, 0.0);
+  long long n = 0;
+  for (int P = 0; P < 6; ++P)
+    for (int l = 0; l < per_patch; ++l) {
+      const size_t at = (size_t)P * per_patch + l;
+      if (gid[at] >= 0) continue;
+      gid[at] = n;
+      gco[at] = 1.0;
+      const auto& pr = partner[at];
+      if (pr[0] >= 0) {
+        const size_t bt = (size_t)pr[0] * per_patch + pr[1];
+        gid[bt] = n;
+        gco[bt] = pr[2];
+      }
+      ++n;
+    }
+  o.ndofs = n;
+  // extraction rows per element-local function
+  const std::vector<double> exp_ = extraction_1d(p, nel1), exq = extraction_1d(p - 1, nel1);
+  const int n1p = p + 1, n1q = p;
+  const int64_t per = int64_t(nel1) * nel1;
+  std::vector<int> rptr(o.nlocal + 1, 0), rcol;
+  std::vector<double> rval;
+  rcol.reserve(o.nlocal * n1p * n1q);
+  rval.reserve(o.nlocal * n1p * n1q);
+  for (int64_t e = 0; e < o.nelem; ++e) {
+    const int P = int(e / per);
+    uint32_t i1, i2;
+    morton_decode(uint32_t(e % per), i1, i2);
+    for (int k = 0; k < o.nloc; ++k) {
+      const bool first = k < n1p * n1q;
+      const int kk = first ? k : k - n1p * n1q;
+      const int k1 = first ? kk % n1p : kk % n1q, k2 = first ? kk / n1p : kk / n1q;
+      // first: degree p in s (n1p functions), p-1 in t; second: the reverse
+      const int na = first ? n1p : n1q, nb = first ? n1q : n1p;
+      const std::vector<double>& ea = first ? exp_ : exq;
+      const std::vector<double>& eb = first ? exq : exp_;
+      for (int b = 0; b < nb; ++b) {
+        const double cb = eb[((size_t)i2 * nb + b) * nb + k2];
+        if (cb == 0.0) continue;
+        for (int a = 0; a < na; ++a) {
+          const double ca = ea[((size_t)i1 * na + a) * na + k1];
+          if (ca == 0.0) continue;
+          const int loc = first ? c1(int(i1) + a, int(i2) + b) : c2(int(i1) + a, int(i2) + b);
+          const size_t at = (size_t)P * per_patch + loc;
+          rcol.push_back(int(gid[at]));
+          rval.push_back(ca * cb * gco[at]);
+        }
+      }
+      rptr[e * o.nloc + k + 1] = int(rcol.size());
+    }
+  }
+  // transpose
+  std::vector<int> tptr(n + 1, 0), tcol(rcol.size());
+  std::vector<double> tval(rcol.size());
+  for (int c : rcol) ++tptr[c + 1];
+  for (long long g = 0; g < n; ++g) tptr[g + 1] += tptr[g];
+  {
+    std::vector<int> fill(tptr.begin(), tptr.end() - 1);
+    for (int64_t r = 0; r < o.nlocal; ++r)
+      for (int k = rptr[r]; k < rptr[r + 1]; ++k) {
+        const int at = fill[rcol[k]]++;
+        tcol[at] = int(r);
+        tval[at] = rval[k];
+      }
+  }
+  o.d_e_ptr = upload(rptr);
+  o.d_e_col = upload(rcol);
+  o.d_e_val = upload(rval);
+  o.d_et_ptr = upload(tptr);
+  o.d_et_col = upload(tcol);
+  o.d_et_val = upload(tval);
+}
+
+struct Ball {
+  double c[3];
+  double r;
+};
 
 struct KeyHash {
   size_t operator()(const std::array<long long, 3>& k) const {
@@ -242,11 +390,13 @@ void build_structure(Op& o) {
   const int64_t per_patch = int64_t(nel1) * nel1;
   o.nel1 = nel1;
   o.h = 1.0 / nel1;
-  o.nloc = (d + 1) * (d + 1);
+  // S^2: (d+1)^2 Bernstein functions per element; S^1 (EFIE): 2 p (p+1)
+  o.nloc = o.efie ? 2 * d * (d + 1) : (d + 1) * (d + 1);
   o.n1 = nel1 + d;
   o.nelem = 6 * per_patch;
   o.ndofs = 6 * int64_t(o.n1) * o.n1;
   o.nlocal = o.nelem * o.nloc;
+  if (o.efie) build_s1_space(o);  // sets ndofs (glued S^1 dofs) and the CSR extraction
   o.m = 1 << (L - o.leaf);
   o.nld = o.m * o.m * o.nloc;
   o.q2 = o.q * o.q;
@@ -449,23 +599,8 @@ void build_structure(Op& o) {
   }
 
   debug_mark("setup: Bezier extraction");
-  // ---- Bezier extraction (1-D, per element index) ----------------------------------
-  {
-    const int n = d + 1;
-    std::vector<double> ex((size_t)nel1 * n * n);
-    std::vector<double> A(n * (n + 1)), sol;
-    for (int i = 0; i < nel1; ++i)
-      for (int j = 0; j < n; ++j) {
-        for (int r = 0; r < n; ++r) {
-          const double u = (r + 0.5) / n;
-          for (int k = 0; k < n; ++k) A[r * (n + 1) + k] = bernstein_h(d, k, u);
-          A[r * (n + 1) + n] = bspline_h(d, nel1, i + j, (i + u) / nel1);
-        }
-        solve_small(n, A, sol);
-        for (int k = 0; k < n; ++k) ex[((size_t)i * n + j) * n + k] = sol[k];
-      }
-    o.d_ex = upload(ex);
-  }
+  // ---- Bezier extraction (1-D, per element index); S^1: signed CSR with glue ------
+  if (!o.efie) o.d_ex = upload(extraction_1d(d, nel1));
 
   debug_mark("setup: moments and transfers");
   // ---- moments and transfers (geometry independent) --------------------------------
@@ -547,8 +682,8 @@ void build_structure(Op& o) {
     std::vector<double> gx, gw;
     gauss01(o.g_reg, gx, gw);
     const int G = o.g_reg, G2 = G * G;
-    std::vector<double> BW((size_t)G2 * nloc);
-    for (int p2 = 0; p2 < G; ++p2)
+    std::vector<double> BW((size_t)G2 * nloc, 0.0);
+    for (int p2 = 0; p2 < G && !o.efie; ++p2)
       for (int p1 = 0; p1 < G; ++p1)
         for (int k2 = 0; k2 <= d; ++k2)
           for (int k1 = 0; k1 <= d; ++k1)
@@ -557,14 +692,16 @@ void build_structure(Op& o) {
     o.d_BW = upload(BW);
     std::vector<double> rg;
     gauss01(G, gx, gw);
+    o.gauss_off[kRegular] = 0;
     rg.insert(rg.end(), gx.begin(), gx.end());
+    rg.insert(rg.end(), gw.begin(), gw.end());
     for (int k = kIdentical; k <= kVertex; ++k) {
       o.gauss_off[k] = int(rg.size());
       gauss01(o.g_kind[k], gx, gw);
       rg.insert(rg.end(), gx.begin(), gx.end());
       rg.insert(rg.end(), gw.begin(), gw.end());
     }
-    o.d_gauss = upload(rg);  // [g_reg nodes] then per singular kind [nodes][weights]
+    o.d_gauss = upload(rg);  // per kind (regular first) [nodes][weights]
   }
 
   debug_mark("setup: report");

@@ -58,8 +58,11 @@ def test_binding_loads_and_reports_errors(built_lib):
         bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=[1.0, 2.0])
     g = bem.bembel_geom_create()
     with pytest.raises(bem.BembelError) as ei:
-        bem.bembel_assemble(g, bem.BEMBEL_MAXWELL_SL, 4.0, 2, 2, 0)
+        bem.bembel_assemble(g, bem.BEMBEL_MAXWELL_SL, 4.0, 2, 2, 4)  # compressed EFIE: not provided
     assert ei.value.code == bem.BEMBEL_EUNSUPPORTED
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_assemble(g, bem.BEMBEL_MAXWELL_SL, 0.0, 2, 2, 0)  # EFIE needs kappa != 0
+    assert ei.value.code == bem.BEMBEL_EINVAL
     with pytest.raises(bem.BembelError) as ei:
         bem.bembel_assemble(g, bem.BEMBEL_LAPLACE_SL, 0.0, 2, 3, 0)
     assert ei.value.code == bem.BEMBEL_EINVAL

@@ -1,0 +1,129 @@
+"""EFIE (App. B (MS), S^1 space of App. E) through the C ABI.
+
+Parity: the dense EFIE Galerkin matrix, load vectors and scattered fields
+against the oracle with the same quadrature rules (rounding only: 1e-12 on
+entries, 1e-10 on fields).  End to end: the GPU solution's scattered field
+against the Mie series of a perfectly conducting sphere (discretisation error,
+decreasing under refinement)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1906_00785_gb300 as bem
+from mie import scattered_pec
+from oracle.efie import EfieAssembler, efie_field, efie_rhs
+from oracle.geometry import Sphere6
+from oracle.space_s1 import S1Space
+
+pytestmark = pytest.mark.gpu
+MAX = bem.BEMBEL_MAXWELL_SL
+
+
+@pytest.fixture(scope="module")
+def geom():
+    return bem.bembel_geom_create()
+
+
+def gpu_matrix(op, n):
+    eye = torch.eye(n, dtype=torch.complex128, device="cuda")
+    out = torch.empty_like(eye)
+    bem.bembel_matvec(op, eye, out, n)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().T
+
+
+def plane(k, d=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0)):
+    return np.array([list(d) + list(pol)])
+
+
+def einc_fun(k, d=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0)):
+    d, pol = np.array(d), np.array(pol)
+    return lambda x: pol[None, :] * np.exp(-1j * k * (x @ d))[:, None]
+
+
+@pytest.mark.parametrize("L,p,k", [(0, 1, 2.0), (1, 1, 2.0), (1, 2, 1.5 + 0.2j), (0, 2, 3.0)])
+def test_efie_matrix_parity(geom, L, p, k):
+    op = bem.bembel_assemble(geom, MAX, k, L, p, 0, g_regular=4, g_singular=5)
+    sp = S1Space(Sphere6(), L, p)
+    assert bem.bembel_ndofs(op) == sp.ndofs
+    A_ref = EfieAssembler(sp, k, 4, 5).dense()
+    A = gpu_matrix(op, sp.ndofs)
+    assert np.max(np.abs(A - A_ref)) / np.max(np.abs(A_ref)) < 1e-12
+
+
+def test_efie_rhs_and_field_parity(geom):
+    k = 2.0
+    L, p = 1, 2
+    op = bem.bembel_assemble(geom, MAX, k, L, p, 0)
+    sp = S1Space(Sphere6(), L, p)
+    n = sp.ndofs
+    prm = np.array([[0.0, 0.0, 1.0, 1.0, 0.0, 0.0], [0.6, 0.0, 0.8, 0.0, 1.0, 0.0]])
+    b = torch.empty((2, n), dtype=torch.complex128, device="cuda")
+    bem.bembel_rhs(op, bem.BEMBEL_RHS_EFIE_PLANE_WAVE, prm, b, g=6)
+    for r in range(2):
+        ref = efie_rhs(sp, einc_fun(k, prm[r, :3], prm[r, 3:]), g=6)
+        np.testing.assert_allclose(b[r].cpu().numpy(), ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+    rho = np.random.default_rng(5).standard_normal(n) + 1j * np.random.default_rng(6).standard_normal(n)
+    pts = np.array([[0.0, 0.0, 3.0], [2.0, -1.5, 0.5], [-2.2, 0.3, -1.9]])
+    out = torch.empty((1, 3, 3), dtype=torch.complex128, device="cuda")
+    bem.bembel_eval(op, torch.from_numpy(pts).cuda(), torch.from_numpy(rho).cuda(), out, 1, g=6)
+    ref = efie_field(sp, rho, pts, k, g=6)
+    np.testing.assert_allclose(out[0].cpu().numpy(), ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def mie_error(geom, L, p, k, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI, precision=bem.BEMBEL_PREC_FP64, tol=1e-6):
+    """Solve to tol (the EFIE's condition number grows like h^-2; 1e-6 is far
+    below the discretisation error measured here) and compare with Mie."""
+    op = bem.bembel_assemble(geom, MAX, k, L, p, 0, precision=precision)
+    n = bem.bembel_ndofs(op)
+    b = torch.empty(n, dtype=torch.complex128, device="cuda")
+    bem.bembel_rhs(op, bem.BEMBEL_RHS_EFIE_PLANE_WAVE, plane(k), b)
+    x = torch.empty_like(b)
+    info = bem.bembel_solve(op, b, x, 1, tol=tol, precond=precond, restart=100, max_iter=3000)
+    assert info["converged"], info
+    rng = np.random.default_rng(4)
+    pts = rng.standard_normal((40, 3))
+    pts *= (3.0 / np.linalg.norm(pts, axis=1))[:, None]
+    out = torch.empty((1, 40, 3), dtype=torch.complex128, device="cuda")
+    bem.bembel_eval(op, torch.from_numpy(pts).cuda(), x, out, 1, g=6)
+    ref = scattered_pec(pts, k)
+    return np.linalg.norm(out[0].cpu().numpy() - ref) / np.linalg.norm(ref), info
+
+
+def test_efie_solution_converges_to_mie(geom):
+    e2, _ = mie_error(geom, 2, 1, 2.0)
+    e3, _ = mie_error(geom, 3, 1, 2.0)
+    e3p2, _ = mie_error(geom, 3, 2, 2.0)
+    assert e2 < 0.02 and e3 < e2 / 3.0 and e3p2 < e3
+
+
+def test_efie_mixed_precision_matches_fp64(geom):
+    e64, _ = mie_error(geom, 3, 2, 2.0)
+    emx, info = mie_error(geom, 3, 2, 2.0, precision=bem.BEMBEL_PREC_MIXED)
+    assert info["refinements"] >= 1
+    assert abs(emx - e64) < 0.05 * e64  # mixed precision keeps the discretisation accuracy
+
+
+def test_efie_level4_degree2_k4(geom):
+    """The k = 4, degree-2, level-4 sphere (3,468 dofs): near the (k j_2)' = 0
+    resonance at 3.87, so GMRES needs more steps; the field still matches Mie."""
+    err, info = mie_error(geom, 4, 2, 4.0)
+    assert err < 5e-3, (err, info)
+
+
+def test_efie_invalid(geom):
+    with pytest.raises(bem.BembelError):
+        bem.bembel_assemble(geom, MAX, 2.0, 2, 1, 4)  # compressed EFIE not provided
+    with pytest.raises(bem.BembelError):
+        bem.bembel_assemble(geom, MAX, 0.0, 2, 1, 0)  # kappa = 0
+    with pytest.raises(bem.BembelError):
+        bem.bembel_assemble(geom, MAX, 2.0, 2, 0, 0)  # S^1 needs p >= 1
+    from inputs import perturbed_sphere_coeffs
+
+    per = bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=perturbed_sphere_coeffs(1000))
+    with pytest.raises(bem.BembelError):
+        bem.bembel_assemble(per, MAX, 2.0, 1, 1, 0)
+    op = bem.bembel_assemble(geom, MAX, 2.0, 1, 1, 0)
+    b = torch.empty(bem.bembel_ndofs(op), dtype=torch.complex128, device="cuda")
+    with pytest.raises(bem.BembelError):
+        bem.bembel_rhs(op, bem.BEMBEL_RHS_PLANE_WAVE, np.array([[0.0, 0.0, 1.0]]), b)
