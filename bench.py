@@ -223,6 +223,9 @@ def main():
         o = bem.bembel_opts_default()
         for f in ("g_regular", "g_singular", "g_identical", "g_edge", "g_vertex", "bsr_chunk"):
             setattr(o, f, getattr(tuned_opts, f))
+        for f in ("g_identical_var", "g_edge_var", "g_vertex_var"):
+            for i in range(4):
+                getattr(o, f)[i] = getattr(tuned_opts, f)[i]
         return bem.bembel_assemble(geom, bem.BEMBEL_LAPLACE_SL, 0.0, w["level"], w["p"], w["q"], opts=o,
                                    eta=w["eta"], leaf_level=w["leaf"], precision=precision,
                                    stream=stream.cuda_stream)
@@ -339,10 +342,14 @@ def main():
     names = ["tabulation", "near_regular", "singular_identical", "singular_edge", "singular_vertex", "coupling",
              "fp32_copies"]
     # rule points actually integrated (identical pairs: half of the 8 sub-domains, by symmetry)
+    def npts4(kind):  # Gauss points of one sub-domain: per-variable orders when tuned so
+        v = tune[f"g_{kind}_var"]
+        return int(np.prod(v)) if all(v) else tune[f"g_{kind}"] ** 4
+
     pts_phase = {"near_regular": opinfo["n_pairs_regular"] * tune["g_regular"] ** 4,
-                 "singular_identical": opinfo["n_pairs_identical"] * 4 * tune["g_identical"] ** 4,
-                 "singular_edge": opinfo["n_pairs_edge"] * 6 * tune["g_edge"] ** 4,
-                 "singular_vertex": opinfo["n_pairs_vertex"] * 4 * tune["g_vertex"] ** 4}
+                 "singular_identical": opinfo["n_pairs_identical"] * 4 * npts4("identical"),
+                 "singular_edge": opinfo["n_pairs_edge"] * 6 * npts4("edge"),
+                 "singular_vertex": opinfo["n_pairs_vertex"] * 4 * npts4("vertex")}
     flops_phase = {k: v * (FLOPS_REG_POINT[w["p"]] if k == "near_regular" else FLOPS_SING_POINT[w["p"]])
                    for k, v in pts_phase.items()}
     dom = max(flops_phase, key=lambda k: ph[names.index(k)])
@@ -375,8 +382,9 @@ def main():
         "config": {"workload": "laplace_h2_sphere6_L6_p1_q4_eta1.6", "ndofs": n1, "nrhs": 1, "level": w["level"],
                    "degree": w["p"], "q": w["q"], "eta": w["eta"], "leaf_level": w["leaf"],
                    "quadrature": f"autotuned for {w['quad_tol']:g} relative block accuracy: regular "
-                                 f"{tune['g_regular']}^2 per element, Duffy {tune['g_identical']}/{tune['g_edge']}/"
-                                 f"{tune['g_vertex']} per variable (identical/edge/vertex)",
+                                 f"{tune['g_regular']}^2 per element, Duffy per-variable orders identical "
+                                 f"{tuple(tune['g_identical_var'])}, edge {tuple(tune['g_edge_var'])}, "
+                                 f"vertex {tuple(tune['g_vertex_var'])}",
                    "precision": "mixed (FP64 quadrature, "
                    "FP32 inner GMRES with block-Jacobi, FP64 refinement)", "l2": "working set > L2 (near+far FP64 storage "
                    f"{matvec_bytes / 1e9:.2f} GB per step)", "parallelism": f"replicas x{world}"},

@@ -107,6 +107,15 @@ typedef struct {
   int tensor_cores;  /* MIXED, q = 4: coupling for 8..128 right-hand sides on tcgen05 (1)    */
   int precision;     /* enum bembel_precision (FP64)                                         */
   void* stream;      /* cudaStream_t used by every call on the operator (NULL: default)      */
+  /* Per-variable Gauss orders of the Duffy rules, in the order of each rule's
+   * variables: identical (xi, eta, u1, u2), common edge (xi, eta1, eta2, u),
+   * common vertex (xi, eta1, eta2, eta3).  All four > 0 override the class's
+   * single order; zeros keep it (default: zeros).  The rules must not depend on
+   * which element of a pair comes first, which needs edge eta1 = eta2 and vertex
+   * eta1 = eta2 = eta3 (EINVAL otherwise). */
+  int g_identical_var[4];
+  int g_edge_var[4];
+  int g_vertex_var[4];
 } bembel_opts;
 
 /* Counters describing an assembled operator (host struct). */
@@ -165,6 +174,7 @@ typedef struct {
   double err_far;                                 /* relative error of sampled far blocks    */
   double chunk_ms[5];                             /* FP64 matvec ms for chunks 8..128         */
   double tune_ms;                                 /* host wall time of the call              */
+  int g_identical_var[4], g_edge_var[4], g_vertex_var[4]; /* chosen per-variable Duffy orders  */
 } bembel_tune_report;
 
 /* Defaults: tol 1e-8, restart 30, max_iter 1000, NONE, refine 1. */

@@ -32,8 +32,10 @@ def green(op: str, kappa: complex, x: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 def pair_rule(kind: str, g_reg: int, g_sing):
     """Rule for a pair kind; g_sing is one order for all Duffy rules or a triple
-    (identical, edge, vertex)."""
+    (identical, edge, vertex) whose entries are an order or four per-variable
+    orders."""
     gi, ge, gv = (g_sing, g_sing, g_sing) if isinstance(g_sing, int) else tuple(g_sing)
+    gi, ge, gv = (tuple(v) if not isinstance(v, (int, np.integer)) else v for v in (gi, ge, gv))
     if kind == "regular":
         return Q.rule_regular(g_reg)
     if kind == "identical":

@@ -21,7 +21,12 @@ g points per variable on [0,1]^4, in canonical position:
 
 Each rule returns (S, T, W): points on the first element (n,2), on the second
 element (n,2) and weights (n,) so that sum_k W_k f(S_k, T_k) approximates
-int_{[0,1]^2} int_{[0,1]^2} f(s, t) ds dt.
+int_{[0,1]^2} int_{[0,1]^2} f(s, t) ds dt.  The Duffy rules take one Gauss
+order g or four per-variable orders, in the order the variables are listed
+above: identical (xi, eta, u1, u2), edge (xi, eta1, eta2, u), vertex
+(xi, eta1, eta2, eta3).  The transformed integrands are smooth but not equally
+so in every variable (the u variables run along the element and need the
+fewest points), which the autotuner exploits.
 """
 from __future__ import annotations
 
@@ -43,11 +48,26 @@ def rule_regular(g: int):
     return S, T, W
 
 
-def _grid4(g: int):
-    x, w = gauss_legendre01(g)
-    pts = np.array(list(itertools.product(x, x, x, x)))
-    wts = np.array([a * b * c * d for a, b, c, d in itertools.product(w, w, w, w)])
+def _orders(g):
+    """One Gauss order for all four variables, or a tuple of four (per variable)."""
+    gs = (g, g, g, g) if isinstance(g, (int, np.integer)) else tuple(int(v) for v in g)
+    if len(gs) != 4:
+        raise ValueError("four per-variable orders expected")
+    return gs
+
+
+@functools.lru_cache(maxsize=None)
+def grid4(g):
+    """Tensor Gauss rule on [0,1]^4; variable v gets order g[v] (or g for all).
+    Points (n, 4) in the order of the rules' variables, weights (n,)."""
+    rules = [gauss_legendre01(gv) for gv in _orders(g)]
+    pts = np.array(list(itertools.product(*[x for x, _ in rules])))
+    wts = np.array([np.prod(c) for c in itertools.product(*[w for _, w in rules])])
     return pts, wts
+
+
+def _grid4(g):
+    return grid4(g if isinstance(g, (int, np.integer)) else _orders(g))
 
 
 @functools.lru_cache(maxsize=None)

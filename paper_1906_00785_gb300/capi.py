@@ -49,7 +49,8 @@ class Opts(C.Structure):
     _fields_ = [("eta", C.c_double), ("leaf_level", C.c_int), ("g_regular", C.c_int), ("g_singular", C.c_int),
                 ("g_identical", C.c_int), ("g_edge", C.c_int), ("g_vertex", C.c_int), ("bsr_chunk", C.c_int),
                 ("tensor_cores", C.c_int),
-                ("precision", C.c_int), ("stream", C.c_void_p)]
+                ("precision", C.c_int), ("stream", C.c_void_p), ("g_identical_var", C.c_int * 4),
+                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4)]
 
 
 class OpInfo(C.Structure):
@@ -64,7 +65,8 @@ class TuneReport(C.Structure):
     _fields_ = [("g_regular", C.c_int), ("g_identical", C.c_int), ("g_edge", C.c_int), ("g_vertex", C.c_int),
                 ("q", C.c_int), ("bsr_chunk", C.c_int), ("err_regular", C.c_double), ("err_identical", C.c_double),
                 ("err_edge", C.c_double), ("err_vertex", C.c_double), ("err_far", C.c_double),
-                ("chunk_ms", C.c_double * 5), ("tune_ms", C.c_double)]
+                ("chunk_ms", C.c_double * 5), ("tune_ms", C.c_double), ("g_identical_var", C.c_int * 4),
+                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4)]
 
 
 class BatchItem(C.Structure):
@@ -199,11 +201,20 @@ def bembel_geom_create(kind: int = BEMBEL_GEOM_SPHERE6, coeffs=None, amplitude: 
     return Geometry(h)
 
 
+def _apply(o, overrides):
+    for key, v in overrides.items():
+        if key.endswith("_var"):
+            arr = getattr(o, key)
+            for i, x in enumerate(v):
+                arr[i] = int(x)
+        else:
+            setattr(o, key, v)
+    return o
+
+
 def bembel_assemble(geom: Geometry, op: int, k: complex, level: int, p: int, q: int, opts: Opts | None = None,
                     **overrides) -> Operator:
-    o = opts if opts is not None else bembel_opts_default()
-    for key, v in overrides.items():
-        setattr(o, key, v)
+    o = _apply(opts if opts is not None else bembel_opts_default(), overrides)
     h = C.c_void_p()
     k = complex(k)
     _check(lib().bembel_assemble(geom.handle, op, k.real, k.imag, level, p, q, C.byref(o), C.byref(h)))
@@ -212,9 +223,7 @@ def bembel_assemble(geom: Geometry, op: int, k: complex, level: int, p: int, q: 
 
 def bembel_assemble_batch(items, op: int, p: int, q: int, opts: Opts | None = None, **overrides) -> list:
     """items: sequence of (geometry, k, level).  Returns one Operator per item."""
-    o = opts if opts is not None else bembel_opts_default()
-    for key, v in overrides.items():
-        setattr(o, key, v)
+    o = _apply(opts if opts is not None else bembel_opts_default(), overrides)
     n = len(items)
     arr = (BatchItem * max(1, n))()
     for i, (geom, k, level) in enumerate(items):
@@ -231,15 +240,14 @@ def bembel_assemble_batch(items, op: int, p: int, q: int, opts: Opts | None = No
 def bembel_autotune(geom: Geometry, op: int, k: complex, level: int, p: int, quad_tol: float = 1e-8,
                     far_tol: float = 1e-5, q_max: int = 8, opts: Opts | None = None, **overrides):
     """Returns (options with the chosen orders, report dict incl. the chosen q)."""
-    o = opts if opts is not None else bembel_opts_default()
-    for key, v in overrides.items():
-        setattr(o, key, v)
+    o = _apply(opts if opts is not None else bembel_opts_default(), overrides)
     rep = TuneReport()
     k = complex(k)
     _check(lib().bembel_autotune(geom.handle, op, k.real, k.imag, level, p, quad_tol, far_tol, q_max, C.byref(o),
                                  C.byref(rep)))
     out = {f: getattr(rep, f) for f, _ in TuneReport._fields_}
-    out["chunk_ms"] = list(rep.chunk_ms)
+    for key in ("chunk_ms", "g_identical_var", "g_edge_var", "g_vertex_var"):
+        out[key] = list(getattr(rep, key))
     return o, out
 
 

@@ -10,6 +10,7 @@
 //   compared on the host with a converged tensor-Gauss integration of the same
 //   element pairs; the smallest q with relative error <= far_tol is chosen.
 // * Chunk size of the block-sparse products: the fastest of a few by timing.
+#include <algorithm>
 #include <chrono>
 #include <complex>
 #include <vector>
@@ -155,20 +156,53 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
     // quadrature orders per kind
     const int kinds[4] = {kRegular, kIdentical, kEdge, kVertex};
     int chosen[4] = {o.g_regular, o.g_singular, o.g_singular, o.g_singular};
+    int chosen_var[4][4] = {};
     double errs[4] = {0, 0, 0, 0};
     for (int ki = 0; ki < 4; ++ki) {
       const int kind = kinds[ki];
       if (opr.npairs[kind] == 0) continue;
       const int g_ref = kMaxG;
+      const int max_pairs = kind == kRegular ? 4096 : 512;
+      std::vector<double> ref;  // reference blocks at order g_ref, computed once per kind
       int best = kMaxG - 1;
       double err_best = 0.0;
       for (int gg = 2; gg < g_ref; ++gg) {
-        const double e = sample_pair_error(opr, kind, gg, g_ref, kind == kRegular ? 4096 : 512);
+        const int g4[4] = {gg, gg, gg, gg};
+        const double e = sample_pair_error(opr, kind, g4, g_ref, max_pairs, &ref);
         best = gg;
         err_best = e;
         if (e <= quad_tol) break;
       }
-      chosen[ki] = best;
+      int gv[4] = {best, best, best, best};
+      // Duffy rules: lower the orders of groups of variables in turn (the
+      // variables along the element first: they are the smoothest) while the
+      // sample still meets the target.  Groups keep the rule symmetric under
+      // exchanging the two elements: identical (u1 u2) (eta) (xi); edge (u)
+      // (eta1 eta2) (xi); vertex (eta1 eta2 eta3) (xi).
+      if (kind != kRegular && err_best <= quad_tol) {
+        static const unsigned groups[4][3] = {{0, 0, 0}, {0xC, 0x2, 0x1}, {0x8, 0x6, 0x1}, {0xE, 0x1, 0}};
+        for (unsigned mask : groups[kind]) {
+          if (!mask) continue;
+          for (;;) {
+            int lo = kMaxG;
+            for (int v = 0; v < 4; ++v)
+              if (mask >> v & 1) lo = std::min(lo, gv[v]);
+            if (lo <= 2) break;
+            for (int v = 0; v < 4; ++v)
+              if (mask >> v & 1) --gv[v];
+            const double e = sample_pair_error(opr, kind, gv, g_ref, max_pairs, &ref);
+            if (e <= quad_tol) {
+              err_best = e;
+            } else {
+              for (int v = 0; v < 4; ++v)
+                if (mask >> v & 1) ++gv[v];
+              break;
+            }
+          }
+        }
+      }
+      chosen[ki] = std::max(std::max(gv[0], gv[1]), std::max(gv[2], gv[3]));
+      for (int v = 0; v < 4; ++v) chosen_var[ki][v] = gv[v];
       errs[ki] = err_best;
     }
     // interpolation order from sampled leaf-level far blocks
@@ -234,6 +268,11 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
     inout->g_identical = chosen[1];
     inout->g_edge = chosen[2];
     inout->g_vertex = chosen[3];
+    for (int v = 0; v < 4; ++v) {
+      inout->g_identical_var[v] = r.g_identical_var[v] = chosen_var[1][v];
+      inout->g_edge_var[v] = r.g_edge_var[v] = chosen_var[2][v];
+      inout->g_vertex_var[v] = r.g_vertex_var[v] = chosen_var[3][v];
+    }
     inout->g_singular = std::max(chosen[1], std::max(chosen[2], chosen[3]));
     inout->bsr_chunk = best_chunk;
     r.g_regular = chosen[0];

@@ -2,6 +2,7 @@
 //
 // Every entry point catches the library's internal errors and turns them into
 // status codes plus a thread-local message; no exception crosses the ABI.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -253,6 +254,32 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
   res->g_kind[kIdentical] = opts.g_identical > 0 ? opts.g_identical : opts.g_singular;
   res->g_kind[kEdge] = opts.g_edge > 0 ? opts.g_edge : opts.g_singular;
   res->g_kind[kVertex] = opts.g_vertex > 0 ? opts.g_vertex : opts.g_singular;
+  const int* var[4] = {nullptr, opts.g_identical_var, opts.g_edge_var, opts.g_vertex_var};
+  for (int k = kRegular; k <= kVertex; ++k) {
+    for (int v = 0; v < 4; ++v) res->g_var[k][v] = k == kRegular ? res->g_reg : res->g_kind[k];
+    if (!var[k]) continue;
+    int set = 0;
+    for (int v = 0; v < 4; ++v) {
+      if (var[k][v] < 0 || var[k][v] > kMaxG) fail(BEMBEL_EINVAL, "assemble: per-variable orders must be in [0, 10]");
+      set += var[k][v] > 0;
+    }
+    if (set != 0 && set != 4) fail(BEMBEL_EINVAL, "assemble: give all four per-variable orders of a class or none");
+    // the rule must not depend on which element of the pair comes first: exchanging
+    // the elements swaps eta1 and eta2 of the edge rule and permutes all three eta
+    // of the vertex rule, so those orders must be equal
+    if (set == 4 && ((k == kEdge && var[k][1] != var[k][2]) ||
+                     (k == kVertex && (var[k][1] != var[k][2] || var[k][2] != var[k][3]))))
+      fail(BEMBEL_EINVAL, "assemble: per-variable Duffy orders must keep the rule symmetric (edge eta1 = eta2, "
+                          "vertex eta1 = eta2 = eta3)");
+    if (set == 4) {
+      int mx = 0;
+      for (int v = 0; v < 4; ++v) {
+        res->g_var[k][v] = var[k][v];
+        mx = std::max(mx, var[k][v]);
+      }
+      res->g_kind[k] = mx;
+    }
+  }
   res->stream = static_cast<cudaStream_t>(opts.stream);
   res->bsr_chunk = opts.bsr_chunk > 0 ? opts.bsr_chunk : 32;
   return res;

@@ -130,20 +130,16 @@ __device__ __forceinline__ void comp_fun(int comp, int n, const Comp1D<P>& f, do
 
 template <int P, int KIND>
 __global__ void __launch_bounds__(32 * kEfieWarps) k_efie_pairs(const PairRec* __restrict__ pairs, int64_t npairs,
-                                                                int L, int G, const double* __restrict__ gauss,
+                                                                int L, int4 G, const double* __restrict__ gauss,
                                                                 double kre, double kim, double* __restrict__ N,
                                                                 int nld) {
   constexpr int NH = P * (P + 1);  // local functions per component
   constexpr int NSUB = KIND == kIdentical ? 8 : (KIND == kEdge ? 6 : (KIND == kVertex ? 4 : 1));
-  __shared__ double gx[kMaxG], gw[kMaxG];
-  if (threadIdx.x < G) {
-    gx[threadIdx.x] = gauss[threadIdx.x];
-    gw[threadIdx.x] = gauss[G + threadIdx.x];
-  }
+  __shared__ double gx[4][kMaxG], gw[4][kMaxG];
+  load_rule_tables(gauss, G, gx, gw);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int G2 = G * G, G4 = G2 * G2;
-  const int npts = NSUB * G4;
+  const int npts = NSUB * G.x * G.y * G.z * G.w;
   const int64_t per = int64_t(1) << (2 * L);
   const double h = ldexp(1.0, -L);
   const double hinv = 1.0 / h;
@@ -165,26 +161,21 @@ __global__ void __launch_bounds__(32 * kEfieWarps) k_efie_pairs(const PairRec* _
 #pragma unroll
       for (int k = 0; k < NH * NH; ++k) ar[k] = ai[k] = 0.0;
       for (int idx = lane; idx < npts; idx += 32) {
-        const int sub = idx / G4;
-        int rem = idx - sub * G4;
-        const int i0 = rem % G;
-        rem /= G;
-        const int i1 = rem % G;
-        rem /= G;
-        const int i2 = rem % G;
-        const int i3 = rem / G;
+        int sub, i0, i1, i2, i3;
+        rule_index(idx, G, sub, i0, i1, i2, i3);
         double ls1, ls2, lt1, lt2, wt;
+        const double w4 = gw[0][i0] * gw[1][i1] * gw[2][i2] * gw[3][i3];
         if (KIND == kRegular) {
-          ls1 = gx[i0];
-          ls2 = gx[i1];
-          lt1 = gx[i2];
-          lt2 = gx[i3];
-          wt = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+          ls1 = gx[0][i0];
+          ls2 = gx[1][i1];
+          lt1 = gx[2][i2];
+          lt2 = gx[3][i3];
+          wt = w4;
         } else {
           double s1, s2, t1, t2;
-          const double jac = duffy_point<KIND == kRegular ? kIdentical : KIND>(sub, gx[i0], gx[i1], gx[i2], gx[i3],
-                                                                                s1, s2, t1, t2);
-          wt = jac * gw[i0] * gw[i1] * gw[i2] * gw[i3];
+          const double jac = duffy_point<KIND == kRegular ? kIdentical : KIND>(sub, gx[0][i0], gx[1][i1], gx[2][i2],
+                                                                                gx[3][i3], s1, s2, t1, t2);
+          wt = jac * w4;
           apply_cmap(ce, s1, s2, ls1, ls2);
           apply_cmap(cf, t1, t2, lt1, lt2);
         }
@@ -400,6 +391,10 @@ __global__ void k_efie_field(const double* __restrict__ pts, const double* __res
   }
 }
 
+int4 orders(const Op& o, int kind) {
+  return make_int4(o.g_var[kind][0], o.g_var[kind][1], o.g_var[kind][2], o.g_var[kind][3]);
+}
+
 template <int P>
 void launch_efie_pairs(Op& o, cudaEvent_t* ev) {
   const cudaStream_t s = o.stream;
@@ -407,27 +402,27 @@ void launch_efie_pairs(Op& o, cudaEvent_t* ev) {
   auto grid_of = [](int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + kEfieWarps - 1) / kEfieWarps, 152 * 64))); };
   if (o.npairs[kRegular] > 0) {
     k_efie_pairs<P, kRegular><<<grid_of(o.npairs[kRegular]), threads, 0, s>>>(
-        o.d_pairs[kRegular], o.npairs[kRegular], o.L, o.g_reg, o.d_gauss + o.gauss_off[kRegular], o.kre, o.kim, o.d_N, o.nld);
+        o.d_pairs[kRegular], o.npairs[kRegular], o.L, orders(o, kRegular), o.d_gauss + o.gauss_off[kRegular], o.kre, o.kim, o.d_N, o.nld);
     launched("k_efie_pairs regular");
   }
   cuda_check(cudaEventRecord(ev[2], s), "event");
   if (o.npairs[kIdentical] > 0) {
     k_efie_pairs<P, kIdentical><<<grid_of(o.npairs[kIdentical]), threads, 0, s>>>(
-        o.d_pairs[kIdentical], o.npairs[kIdentical], o.L, o.g_kind[kIdentical], o.d_gauss + o.gauss_off[kIdentical],
+        o.d_pairs[kIdentical], o.npairs[kIdentical], o.L, orders(o, kIdentical), o.d_gauss + o.gauss_off[kIdentical],
         o.kre, o.kim, o.d_N, o.nld);
     launched("k_efie_pairs identical");
   }
   cuda_check(cudaEventRecord(ev[3], s), "event");
   if (o.npairs[kEdge] > 0) {
     k_efie_pairs<P, kEdge><<<grid_of(o.npairs[kEdge]), threads, 0, s>>>(
-        o.d_pairs[kEdge], o.npairs[kEdge], o.L, o.g_kind[kEdge], o.d_gauss + o.gauss_off[kEdge], o.kre, o.kim,
+        o.d_pairs[kEdge], o.npairs[kEdge], o.L, orders(o, kEdge), o.d_gauss + o.gauss_off[kEdge], o.kre, o.kim,
         o.d_N, o.nld);
     launched("k_efie_pairs edge");
   }
   cuda_check(cudaEventRecord(ev[4], s), "event");
   if (o.npairs[kVertex] > 0) {
     k_efie_pairs<P, kVertex><<<grid_of(o.npairs[kVertex]), threads, 0, s>>>(
-        o.d_pairs[kVertex], o.npairs[kVertex], o.L, o.g_kind[kVertex], o.d_gauss + o.gauss_off[kVertex], o.kre,
+        o.d_pairs[kVertex], o.npairs[kVertex], o.L, orders(o, kVertex), o.d_gauss + o.gauss_off[kVertex], o.kre,
         o.kim, o.d_N, o.nld);
     launched("k_efie_pairs vertex");
   }

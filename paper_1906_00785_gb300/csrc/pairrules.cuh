@@ -70,4 +70,36 @@ __device__ __forceinline__ double duffy_point(int sub, double x0, double x1, dou
   }
 }
 
+// Gauss tables of a rule with per-variable orders g = (g0, g1, g2, g3): at tab,
+// for v = 0..3, the g_v nodes then the g_v weights on [0,1].  Block-cooperative
+// (needs blockDim.x >= 4 kMaxG); the caller synchronises afterwards.
+__device__ __forceinline__ void load_rule_tables(const double* __restrict__ tab, int4 g, double (*gx)[kMaxG],
+                                                 double (*gw)[kMaxG]) {
+  const int t = threadIdx.x;
+  if (t < 4 * kMaxG) {
+    const int v = t / kMaxG, i = t % kMaxG;
+    const int gv[4] = {g.x, g.y, g.z, g.w};
+    int off = 0;
+    for (int u = 0; u < v; ++u) off += 2 * gv[u];
+    if (i < gv[v]) {
+      gx[v][i] = tab[off + i];
+      gw[v][i] = tab[off + gv[v] + i];
+    }
+  }
+}
+
+// rule point idx of NSUB sub-domains x g0 g1 g2 g3 tensor points:
+// sub-domain and the four Gauss indices (variable 0 fastest)
+__device__ __forceinline__ void rule_index(int idx, int4 g, int& sub, int& i0, int& i1, int& i2, int& i3) {
+  const int g4 = g.x * g.y * g.z * g.w;
+  sub = idx / g4;
+  int rem = idx - sub * g4;
+  i0 = rem % g.x;
+  rem /= g.x;
+  i1 = rem % g.y;
+  rem /= g.y;
+  i2 = rem % g.z;
+  i3 = rem / g.z;
+}
+
 }  // namespace bembel

@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_regular(const PairRec* __r
 // One touching pair per warp; lanes stride over the nsub * g^4 rule points and
 // accumulate the (D+1)^2 x (D+1)^2 block in registers, reduced over the warp.
 template <int D, bool CPLX, int KIND>
-__device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geom, int L, int G,
-                                              const double* __restrict__ gx, const double* __restrict__ gw,
+__device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geom, int L, int4 G,
+                                              const double (*gx)[kMaxG], const double (*gw)[kMaxG],
                                               double kre, double kim, double* __restrict__ N, int nld, int lane) {
   constexpr int D1 = D + 1;
   constexpr int NL = D1 * D1;
@@ -149,8 +149,7 @@ __device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geo
   // -sigma with the same weight), so half the sub-domains are integrated and
   // the block is symmetrised at the end: A = M + M^T.
   constexpr int NSUB = KIND == kIdentical ? 4 : (KIND == kEdge ? 6 : 4);
-  const int G2 = G * G, G4 = G2 * G2;
-  const int npts = NSUB * G4;
+  const int npts = NSUB * G.x * G.y * G.z * G.w;
   const int64_t per = int64_t(1) << (2 * L);
   const double h = ldexp(1.0, -L);
   const int pe = int(pr.e / per), pf = int(pr.f / per);
@@ -162,19 +161,13 @@ __device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geo
 #pragma unroll
   for (int k = 0; k < NL * NL; ++k) ar[k] = ai[k] = 0.0;
   for (int idx = lane; idx < npts; idx += 32) {
-    const int sub0 = idx / G4;
-    int rem = idx - sub0 * G4;
+    int sub0, i0, i1, i2, i3;
+    rule_index(idx, G, sub0, i0, i1, i2, i3);
     // identical: sub-domains with sigma_1 = +1 only (sub & 1 == 0 -> quadrants (+,+), (+,-))
     const int sub = KIND == kIdentical ? (((sub0 & 1) << 1) | ((sub0 >> 1) << 2)) : sub0;
-    const int i0 = rem % G;
-    rem /= G;
-    const int i1 = rem % G;
-    rem /= G;
-    const int i2 = rem % G;
-    const int i3 = rem / G;
     double s1, s2, t1, t2;
-    const double jac = duffy_point<KIND>(sub, gx[i0], gx[i1], gx[i2], gx[i3], s1, s2, t1, t2);
-    const double wt = jac * gw[i0] * gw[i1] * gw[i2] * gw[i3];
+    const double jac = duffy_point<KIND>(sub, gx[0][i0], gx[1][i1], gx[2][i2], gx[3][i3], s1, s2, t1, t2);
+    const double wt = jac * gw[0][i0] * gw[1][i1] * gw[2][i2] * gw[3][i3];
     double ls1, ls2, lt1, lt2;
     apply_cmap(ce, s1, s2, ls1, ls2);
     apply_cmap(cf, t1, t2, lt1, lt2);
@@ -242,14 +235,11 @@ __device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geo
 
 template <int D, bool CPLX, int KIND>
 __global__ void __launch_bounds__(32 * kWarps) k_near_singular(const PairRec* __restrict__ pairs, int64_t npairs,
-                                                               Geom geom, int L, int G,
+                                                               Geom geom, int L, int4 G,
                                                                const double* __restrict__ gauss, double kre,
                                                                double kim, double* __restrict__ N, int nld) {
-  __shared__ double gx[kMaxG], gw[kMaxG];
-  if (threadIdx.x < G) {
-    gx[threadIdx.x] = gauss[threadIdx.x];
-    gw[threadIdx.x] = gauss[G + threadIdx.x];
-  }
+  __shared__ double gx[4][kMaxG], gw[4][kMaxG];
+  load_rule_tables(gauss, G, gx, gw);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < npairs; w += (int64_t)gridDim.x * kWarps)
@@ -294,6 +284,10 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
     b[i] = float(a[i]);
 }
 
+int4 rule_orders(const Op& o, int kind) {
+  return make_int4(o.g_var[kind][0], o.g_var[kind][1], o.g_var[kind][2], o.g_var[kind][3]);
+}
+
 int grid_for(int64_t work, int per_block) {
   int64_t g = (work + per_block - 1) / per_block;
   return int(std::min<int64_t>(std::max<int64_t>(g, 1), 1 << 30));
@@ -320,21 +314,21 @@ void launch_pairs(Op& o, cudaEvent_t* ev) {
   auto grid_of = [](int64_t n) { return int(std::min<int64_t>((n + kWarps - 1) / kWarps, 152 * 64)); };
   if (o.npairs[kIdentical] > 0) {
     k_near_singular<D, CPLX, kIdentical><<<grid_of(o.npairs[kIdentical]), threads, 0, s>>>(
-        o.d_pairs[kIdentical], o.npairs[kIdentical], o.geom, o.L, o.g_kind[kIdentical], o.d_gauss + o.gauss_off[kIdentical], o.kre,
+        o.d_pairs[kIdentical], o.npairs[kIdentical], o.geom, o.L, rule_orders(o, kIdentical), o.d_gauss + o.gauss_off[kIdentical], o.kre,
         o.kim, o.d_N, o.nld);
     launched("k_near_singular identical");
   }
   cuda_check(cudaEventRecord(ev[3], s), "event");
   if (o.npairs[kEdge] > 0) {
     k_near_singular<D, CPLX, kEdge><<<grid_of(o.npairs[kEdge]), threads, 0, s>>>(
-        o.d_pairs[kEdge], o.npairs[kEdge], o.geom, o.L, o.g_kind[kEdge], o.d_gauss + o.gauss_off[kEdge], o.kre,
+        o.d_pairs[kEdge], o.npairs[kEdge], o.geom, o.L, rule_orders(o, kEdge), o.d_gauss + o.gauss_off[kEdge], o.kre,
         o.kim, o.d_N, o.nld);
     launched("k_near_singular edge");
   }
   cuda_check(cudaEventRecord(ev[4], s), "event");
   if (o.npairs[kVertex] > 0) {
     k_near_singular<D, CPLX, kVertex><<<grid_of(o.npairs[kVertex]), threads, 0, s>>>(
-        o.d_pairs[kVertex], o.npairs[kVertex], o.geom, o.L, o.g_kind[kVertex], o.d_gauss + o.gauss_off[kVertex], o.kre,
+        o.d_pairs[kVertex], o.npairs[kVertex], o.geom, o.L, rule_orders(o, kVertex), o.d_gauss + o.gauss_off[kVertex], o.kre,
         o.kim, o.d_N, o.nld);
     launched("k_near_singular vertex");
   }
@@ -477,24 +471,18 @@ __global__ void __launch_bounds__(32 * kWarps) k_assemble_multi(const MeshWork* 
                                                                 const Segment* __restrict__ segs_g, int nseg,
                                                                 long long nitems, unsigned long long* __restrict__ next,
                                                                 int G2,
-                                                                const double* __restrict__ gauss, int3 gk, int3 goff,
-                                                                int q2) {
+                                                                const double* __restrict__ gauss, int4 gi, int4 ge,
+                                                                int4 gv, int3 goff, int q2) {
   constexpr int NL = (D + 1) * (D + 1);
   constexpr int C = CPLX ? 2 : 1;
   extern __shared__ double sh[];
   double* ubuf = sh + (threadIdx.x >> 5) * G2 * NL * C;
-  __shared__ double gx[3][kMaxG], gw[3][kMaxG];
+  __shared__ double gx[3][4][kMaxG], gw[3][4][kMaxG];
   __shared__ Segment segs[kMaxSegments];
   for (int i = threadIdx.x; i < nseg; i += blockDim.x) segs[i] = segs_g[i];
-  if (threadIdx.x < 3 * kMaxG) {
-    const int k = threadIdx.x / kMaxG, i = threadIdx.x % kMaxG;
-    const int g = k == 0 ? gk.x : (k == 1 ? gk.y : gk.z);
-    const int o = k == 0 ? goff.x : (k == 1 ? goff.y : goff.z);
-    if (i < g) {
-      gx[k][i] = gauss[o + i];
-      gw[k][i] = gauss[o + g + i];
-    }
-  }
+  load_rule_tables(gauss + goff.x, gi, gx[0], gw[0]);
+  load_rule_tables(gauss + goff.y, ge, gx[1], gw[1]);
+  load_rule_tables(gauss + goff.z, gv, gx[2], gw[2]);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -515,17 +503,17 @@ __global__ void __launch_bounds__(32 * kWarps) k_assemble_multi(const MeshWork* 
         break;
       case kIdentical:
         for (long long w = first; w < last; ++w)
-          singular_pair<D, CPLX, kIdentical>(m.pairs[kIdentical][w], m.geom, m.L, gk.x, gx[0], gw[0], m.kre, m.kim,
+          singular_pair<D, CPLX, kIdentical>(m.pairs[kIdentical][w], m.geom, m.L, gi, gx[0], gw[0], m.kre, m.kim,
                                              m.N, m.nld, lane);
         break;
       case kEdge:
         for (long long w = first; w < last; ++w)
-          singular_pair<D, CPLX, kEdge>(m.pairs[kEdge][w], m.geom, m.L, gk.y, gx[1], gw[1], m.kre, m.kim, m.N,
+          singular_pair<D, CPLX, kEdge>(m.pairs[kEdge][w], m.geom, m.L, ge, gx[1], gw[1], m.kre, m.kim, m.N,
                                         m.nld, lane);
         break;
       case kVertex:
         for (long long w = first; w < last; ++w)
-          singular_pair<D, CPLX, kVertex>(m.pairs[kVertex][w], m.geom, m.L, gk.z, gx[2], gw[2], m.kre, m.kim, m.N,
+          singular_pair<D, CPLX, kVertex>(m.pairs[kVertex][w], m.geom, m.L, gv, gx[2], gw[2], m.kre, m.kim, m.N,
                                           m.nld, lane);
         break;
       default: {
@@ -556,10 +544,10 @@ void launch_multi(const std::vector<Op*>& ops, const MeshWork* d_ms, const Segme
   cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
   const long long want = (nitems + kWarps - 1) / kWarps;
   const int grid = int(std::max<long long>(1, std::min<long long>(want, (long long)std::max(1, per_sm) * nsm)));
-  const int3 gk = make_int3(o.g_kind[kIdentical], o.g_kind[kEdge], o.g_kind[kVertex]);
   const int3 goff = make_int3(int(o.gauss_off[kIdentical]), int(o.gauss_off[kEdge]), int(o.gauss_off[kVertex]));
   k_assemble_multi<D, CPLX><<<grid, 32 * kWarps, shm, s>>>(d_ms, d_seg, nseg, nitems, d_next, G2, o.d_gauss,
-                                                           gk, goff, o.q2);
+                                                           rule_orders(o, kIdentical), rule_orders(o, kEdge),
+                                                           rule_orders(o, kVertex), goff, o.q2);
   launched("k_assemble_multi");
 }
 
@@ -676,13 +664,21 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
 namespace {
 
 template <int D, bool CPLX>
-void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, int g, double* out) {
+void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, const int gv[4], double* out) {
   const cudaStream_t s = o.stream;
   const int nloc = (D + 1) * (D + 1);
+  const int g = gv[0];  // regular pairs: one order
   std::vector<double> gx, gw;
   gauss01(g, gx, gw);
-  std::vector<double> tab(gx);
-  tab.insert(tab.end(), gw.begin(), gw.end());
+  // per-variable tables (nodes, weights) for the Duffy rules
+  std::vector<double> tab;
+  for (int v = 0; v < 4; ++v) {
+    std::vector<double> x, w;
+    gauss01(kind == kRegular ? g : gv[v], x, w);
+    tab.insert(tab.end(), x.begin(), x.end());
+    tab.insert(tab.end(), w.begin(), w.end());
+  }
+  const int4 g4 = make_int4(gv[0], gv[1], gv[2], gv[3]);
   double* d_tab = static_cast<double*>(dev_alloc(sizeof(double) * tab.size()));
   cuda_check(cudaMemcpy(d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice), "tab");
   const int threads = 32 * kWarps;
@@ -711,15 +707,15 @@ void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, int g, dou
     dev_free(Xq);
     dev_free(d_BW);
   } else if (kind == kIdentical) {
-    k_near_singular<D, CPLX, kIdentical><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g, d_tab, o.kre, o.kim,
+    k_near_singular<D, CPLX, kIdentical><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g4, d_tab, o.kre, o.kim,
                                                                   out, nloc);
     launched("k_near_singular");
   } else if (kind == kEdge) {
-    k_near_singular<D, CPLX, kEdge><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g, d_tab, o.kre, o.kim, out,
+    k_near_singular<D, CPLX, kEdge><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g4, d_tab, o.kre, o.kim, out,
                                                              nloc);
     launched("k_near_singular");
   } else {
-    k_near_singular<D, CPLX, kVertex><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g, d_tab, o.kre, o.kim,
+    k_near_singular<D, CPLX, kVertex><<<grid, threads, 0, s>>>(d_sample, ns, o.geom, o.L, g4, d_tab, o.kre, o.kim,
                                                                out, nloc);
     launched("k_near_singular");
   }
@@ -729,7 +725,7 @@ void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, int g, dou
 
 }  // namespace
 
-double sample_pair_error(Op& o, int kind, int g, int g_ref, int max_pairs) {
+double sample_pair_error(Op& o, int kind, const int g[4], int g_ref, int max_pairs, std::vector<double>* ref_cache) {
   const int64_t ns = std::min<int64_t>(o.npairs[kind], max_pairs);
   if (ns == 0) return 0.0;
   const int C = o.cplx ? 2 : 1;
@@ -747,7 +743,7 @@ double sample_pair_error(Op& o, int kind, int g, int g_ref, int max_pairs) {
   const size_t nb = (size_t)ns * nloc * nloc * C;
   double* d_a = static_cast<double*>(dev_alloc(sizeof(double) * nb));
   double* d_b = static_cast<double*>(dev_alloc(sizeof(double) * nb));
-  auto run = [&](int gg, double* out) {
+  auto run = [&](const int* gg, double* out) {
     switch (o.d * 2 + (o.cplx ? 1 : 0)) {
       case 0: run_sample<0, false>(o, kind, d_sample, ns, gg, out); break;
       case 1: run_sample<0, true>(o, kind, d_sample, ns, gg, out); break;
@@ -758,10 +754,17 @@ double sample_pair_error(Op& o, int kind, int g, int g_ref, int max_pairs) {
     }
   };
   run(g, d_a);
-  run(g_ref, d_b);
-  std::vector<double> a(nb), b(nb);
+  std::vector<double> a(nb), b;
   cuda_check(cudaMemcpy(a.data(), d_a, sizeof(double) * nb, cudaMemcpyDeviceToHost), "sample down");
-  cuda_check(cudaMemcpy(b.data(), d_b, sizeof(double) * nb, cudaMemcpyDeviceToHost), "sample down");
+  if (ref_cache && ref_cache->size() == nb) {
+    b = *ref_cache;  // reference blocks of this sample at g_ref, computed earlier
+  } else {
+    const int gr[4] = {g_ref, g_ref, g_ref, g_ref};
+    run(gr, d_b);
+    b.resize(nb);
+    cuda_check(cudaMemcpy(b.data(), d_b, sizeof(double) * nb, cudaMemcpyDeviceToHost), "sample down");
+    if (ref_cache) *ref_cache = b;
+  }
   dev_free(d_sample);
   dev_free(d_a);
   dev_free(d_b);

@@ -690,18 +690,18 @@ void build_structure(Op& o) {
             BW[(size_t)(p1 + G * p2) * nloc + k1 + (d + 1) * k2] =
                 gw[p1] * gw[p2] * o.h * o.h * bernstein_h(d, k1, gx[p1]) * bernstein_h(d, k2, gx[p2]);
     o.d_BW = upload(BW);
+    // per kind (regular first) and per variable: nodes then weights; the
+    // regular kind repeats g_reg four times (its first nodes tabulate gamma)
     std::vector<double> rg;
-    gauss01(G, gx, gw);
-    o.gauss_off[kRegular] = 0;
-    rg.insert(rg.end(), gx.begin(), gx.end());
-    rg.insert(rg.end(), gw.begin(), gw.end());
-    for (int k = kIdentical; k <= kVertex; ++k) {
+    for (int k = kRegular; k <= kVertex; ++k) {
       o.gauss_off[k] = int(rg.size());
-      gauss01(o.g_kind[k], gx, gw);
-      rg.insert(rg.end(), gx.begin(), gx.end());
-      rg.insert(rg.end(), gw.begin(), gw.end());
+      for (int v = 0; v < 4; ++v) {
+        gauss01(o.g_var[k][v], gx, gw);
+        rg.insert(rg.end(), gx.begin(), gx.end());
+        rg.insert(rg.end(), gw.begin(), gw.end());
+      }
     }
-    o.d_gauss = upload(rg);  // per kind (regular first) [nodes][weights]
+    o.d_gauss = upload(rg);
   }
 
   debug_mark("setup: report");

@@ -41,12 +41,14 @@ def einc_fun(k, d=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0)):
     return lambda x: pol[None, :] * np.exp(-1j * k * (x @ d))[:, None]
 
 
-@pytest.mark.parametrize("L,p,k", [(0, 1, 2.0), (1, 1, 2.0), (1, 2, 1.5 + 0.2j), (0, 2, 3.0)])
-def test_efie_matrix_parity(geom, L, p, k):
-    op = bem.bembel_assemble(geom, MAX, k, L, p, 0, g_regular=4, g_singular=5)
+@pytest.mark.parametrize("L,p,k,var", [(0, 1, 2.0, None), (1, 1, 2.0, None), (1, 2, 1.5 + 0.2j, None),
+                                       (0, 2, 3.0, None), (1, 2, 2.0, ((4, 5, 3, 3), (4, 5, 5, 3), (5, 4, 4, 4)))])
+def test_efie_matrix_parity(geom, L, p, k, var):
+    kw = {} if var is None else dict(g_identical_var=var[0], g_edge_var=var[1], g_vertex_var=var[2])
+    op = bem.bembel_assemble(geom, MAX, k, L, p, 0, g_regular=4, g_singular=5, **kw)
     sp = S1Space(Sphere6(), L, p)
     assert bem.bembel_ndofs(op) == sp.ndofs
-    A_ref = EfieAssembler(sp, k, 4, 5).dense()
+    A_ref = EfieAssembler(sp, k, 4, 5 if var is None else var).dense()
     A = gpu_matrix(op, sp.ndofs)
     assert np.max(np.abs(A - A_ref)) / np.max(np.abs(A_ref)) < 1e-12
 

@@ -280,6 +280,24 @@ def test_per_class_orders_parity(geom):
     assert rel_err(gpu_matrix(gop, sp.ndofs), A_ref) < 1e-12
 
 
+@pytest.mark.parametrize("op,k,d", [("laplace", 0.0, 1), ("helmholtz", 2.5 + 0.3j, 2)])
+def test_per_variable_orders_parity(geom, op, k, d):
+    """Duffy rules with a Gauss order per variable (xi, eta.., u..) against the oracle's."""
+    var = ((4, 5, 3, 3), (4, 5, 5, 3), (5, 4, 4, 4))
+    gop = bem.bembel_assemble(geom, LAP if op == "laplace" else HEL, k, 2, d, 0, g_regular=3, g_singular=4,
+                              g_identical_var=var[0], g_edge_var=var[1], g_vertex_var=var[2])
+    sp = S2Space(Sphere6(), 2, d)
+    A_ref = Assembler(sp, op, k, 3, var).dense()
+    assert rel_err(gpu_matrix(gop, sp.ndofs), A_ref) < 1e-12
+
+
+def test_per_variable_orders_invalid(geom):
+    for kw in (dict(g_edge_var=(4, 0, 5, 3)), dict(g_edge_var=(4, 11, 11, 3)),
+               dict(g_edge_var=(4, 4, 5, 3)), dict(g_vertex_var=(5, 4, 4, 3))):  # partial, too large, asymmetric
+        with pytest.raises(bem.BembelError):
+            bem.bembel_assemble(geom, LAP, 0.0, 2, 1, 0, **kw)
+
+
 @pytest.mark.parametrize("op,k,d", [("laplace", 0.0, 1), ("helmholtz", 4.0, 2)])
 def test_autotune_meets_target(geom, op, k, d):
     """Tuned orders meet the accuracy target: the operator assembled with them

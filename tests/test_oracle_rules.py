@@ -78,3 +78,68 @@ def test_regular_rule_separated():
 def test_rules_stay_inside(rule):
     S, T, W = rule(5)
     assert np.all((S > 0) & (S < 1)) and np.all((T > 0) & (T < 1)) and np.all(W > 0)
+
+
+def test_grid4_per_variable_orders():
+    """Variable v of the 4-D grid carries its own Gauss order: monomials of
+    degree 2 g_v - 1 in variable v are exact, degree 2 g_v is not (so a
+    permuted order assignment fails)."""
+    from oracle.quadrature import grid4
+
+    orders = (2, 5, 3, 4)
+    P, W = grid4(orders)
+    assert len(W) == 2 * 5 * 3 * 4
+    for v, g in enumerate(orders):
+        for deg, exact in ((2 * g - 1, True), (2 * g, False)):
+            val = np.sum(W * P[:, v] ** deg)
+            assert (abs(val - 1.0 / (deg + 1)) < 1e-13) == exact, (v, g, deg)
+
+
+@pytest.mark.parametrize("kind,orders", [("identical", (6, 7, 4, 4)), ("edge", (6, 6, 7, 4)), ("vertex", (7, 7, 7, 7))])
+def test_anisotropic_rules_match_closed_forms(kind, orders):
+    """Per-variable orders (fewer points along the element) still reproduce the
+    closed forms of int int 1/|x-y| over flat unit squares in the canonical
+    configurations: identical; sharing the edge x1 = 0; sharing the vertex 0."""
+    from oracle.quadrature import rule_edge, rule_identical, rule_vertex
+
+    if kind == "identical":
+        S, T, W = rule_identical(orders)
+        x, y = S, T
+        exact = pair_integral(((0, 1), (0, 1)), ((0, 1), (0, 1)))
+    elif kind == "edge":
+        S, T, W = rule_edge(orders)
+        x, y = S * [-1.0, 1.0], T  # mirror the first square across the shared edge
+        exact = pair_integral(((-1, 0), (0, 1)), ((0, 1), (0, 1)))
+    else:
+        S, T, W = rule_vertex(orders)
+        x, y = -S, T  # squares meeting at the origin only
+        exact = pair_integral(((-1, 0), (-1, 0)), ((0, 1), (0, 1)))
+    val = np.sum(W / np.linalg.norm(x - y, axis=1))
+    assert abs(val - exact) < 1e-7 * exact
+
+
+def test_symmetric_per_variable_orders_do_not_depend_on_pair_order():
+    """Exchanging the two elements of a touching pair permutes the eta variables
+    of the edge and vertex rules; with equal eta orders the block of (f, e) is the
+    transpose of the block of (e, f), with unequal ones it is not."""
+    from oracle.galerkin import Assembler
+    from oracle.geometry import Sphere6
+    from oracle.space import S2Space
+
+    sp = S2Space(Sphere6(), 2, 1)
+    sym = Assembler(sp, "laplace", 0.0, 3, ((4, 5, 3, 3), (4, 5, 5, 3), (5, 4, 4, 4)))
+    asym = Assembler(sp, "laplace", 0.0, 3, ((4, 5, 3, 3), (4, 4, 5, 3), (5, 4, 4, 3)))
+    found = {"edge": False, "vertex": False}
+    for e in range(sp.nelem):
+        for f in range(sp.nelem):
+            kind = sym.classify(e, f)[0]
+            if kind not in found or found[kind]:
+                continue
+            a, b = sym.pair_block(e, f), sym.pair_block(f, e).T
+            assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()  # rounding only
+            c, d = asym.pair_block(e, f), asym.pair_block(f, e).T
+            assert np.abs(c - d).max() > 1e-9 * np.abs(c).max()
+            found[kind] = True
+        if all(found.values()):
+            break
+    assert all(found.values())
