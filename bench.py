@@ -221,7 +221,7 @@ def main():
 
     def assemble(precision):
         o = bem.bembel_opts_default()
-        for f in ("g_regular", "g_singular", "g_identical", "g_edge", "g_vertex", "bsr_chunk"):
+        for f in ("g_regular", "g_regular_far", "g_singular", "g_identical", "g_edge", "g_vertex", "bsr_chunk"):
             setattr(o, f, getattr(tuned_opts, f))
         for f in ("g_identical_var", "g_edge_var", "g_vertex_var"):
             for i in range(4):
@@ -346,7 +346,9 @@ def main():
         v = tune[f"g_{kind}_var"]
         return int(np.prod(v)) if all(v) else tune[f"g_{kind}"] ** 4
 
-    pts_phase = {"near_regular": opinfo["n_pairs_regular"] * tune["g_regular"] ** 4,
+    n_far = opinfo["n_pairs_regular_far"]
+    pts_phase = {"near_regular": (opinfo["n_pairs_regular"] - n_far) * tune["g_regular"] ** 4
+                 + n_far * tune["g_regular_far"] ** 4,
                  "singular_identical": opinfo["n_pairs_identical"] * 4 * npts4("identical"),
                  "singular_edge": opinfo["n_pairs_edge"] * 6 * npts4("edge"),
                  "singular_vertex": opinfo["n_pairs_vertex"] * 4 * npts4("vertex")}
@@ -381,8 +383,9 @@ def main():
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": "laplace_h2_sphere6_L6_p1_q4_eta1.6", "ndofs": n1, "nrhs": 1, "level": w["level"],
                    "degree": w["p"], "q": w["q"], "eta": w["eta"], "leaf_level": w["leaf"],
-                   "quadrature": f"autotuned for {w['quad_tol']:g} relative block accuracy: regular "
-                                 f"{tune['g_regular']}^2 per element, Duffy per-variable orders identical "
+                   "quadrature": f"autotuned for {w['quad_tol']:g} relative block accuracy: separated pairs "
+                                 f"{tune['g_regular']}^2 per element next to the touching pairs, "
+                                 f"{tune['g_regular_far']}^2 beyond, Duffy per-variable orders identical "
                                  f"{tuple(tune['g_identical_var'])}, edge {tuple(tune['g_edge_var'])}, "
                                  f"vertex {tuple(tune['g_vertex_var'])}",
                    "precision": "mixed (FP64 quadrature, "

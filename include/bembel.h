@@ -116,6 +116,10 @@ typedef struct {
   int g_identical_var[4];
   int g_edge_var[4];
   int g_vertex_var[4];
+  /* Gauss points per direction on separated pairs beyond the ring next to the
+   * touching pairs (no element holds a corner of both); g_regular then applies
+   * to the ring only.  0 = g_regular (default 0). */
+  int g_regular_far;
 } bembel_opts;
 
 /* Counters describing an assembled operator (host struct). */
@@ -144,6 +148,7 @@ typedef struct {
    * kernel (operators from bembel_assemble_batch: phases 0, 6 and 7 are the
    * whole batch's, 1-5 are zero) */
   double phase_ms[8];
+  int64_t n_pairs_regular_far; /* separated pairs integrated at g_regular_far      */
 } bembel_op_info;
 
 /* Solver options and report (Sec. 4.6: GMRES, restarted). */
@@ -175,6 +180,8 @@ typedef struct {
   double chunk_ms[5];                             /* FP64 matvec ms for chunks 8..128         */
   double tune_ms;                                 /* host wall time of the call              */
   int g_identical_var[4], g_edge_var[4], g_vertex_var[4]; /* chosen per-variable Duffy orders  */
+  int g_regular_far;                              /* separated pairs beyond the ring          */
+  double err_regular_far;
 } bembel_tune_report;
 
 /* Defaults: tol 1e-8, restart 30, max_iter 1000, NONE, refine 1. */

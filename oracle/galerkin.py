@@ -48,29 +48,46 @@ def pair_rule(kind: str, g_reg: int, g_sing):
 
 
 class Assembler:
-    """Element-pair integration on an S2Space."""
+    """Element-pair integration on an S2Space.
 
-    def __init__(self, space, op: str, kappa: complex = 0.0, g_reg: int = 4, g_sing: int = 6):
+    g_reg: Gauss points per direction on separated pairs, or a pair
+    (g_ring, g_far): g_ring for the ring next to the touching pairs (some element
+    holds a corner of each), g_far for pairs farther apart."""
+
+    def __init__(self, space, op: str, kappa: complex = 0.0, g_reg=4, g_sing: int = 6):
         self.space, self.op, self.kappa = space, op, kappa
-        self.g_reg, self.g_sing = g_reg, g_sing
+        self.g_ring, self.g_far = (g_reg, g_reg) if isinstance(g_reg, (int, np.integer)) else tuple(g_reg)
+        self.g_reg, self.g_sing = self.g_ring, g_sing
         self.ids = corner_ids(space)
         self.dtype = float if op == LAPLACE else complex
-        self._tab_cache: dict[int, tuple] = {}
+        self._tab_cache: dict[tuple, tuple] = {}
+        # vertex -> elements holding it
+        self._v2e: dict[int, list] = {}
+        for el, c in enumerate(self.ids):
+            for v in c:
+                self._v2e.setdefault(int(v), []).append(el)
 
     def classify(self, e: int, f: int):
         return canonical_maps(self.ids[e], self.ids[f])
 
-    def _tab(self, e: int):
+    def ring(self, e: int, f: int) -> bool:
+        """Separated pair in the ring next to the touching pairs: some element holds
+        a corner of e and a corner of f."""
+        cf = set(self.ids[f].tolist())
+        return any(cf & set(self.ids[g].tolist()) for v in self.ids[e] for g in self._v2e[int(v)])
+
+    def _tab(self, e: int, g: int | None = None):
         """Regular-rule data of element e: points gamma(s_p) (g^2, 3) and weighted basis (g^2, (d+1)^2)."""
-        if e not in self._tab_cache:
+        g = self.g_ring if g is None else g
+        if (e, g) not in self._tab_cache:
             from .gauss import tensor2
 
             sp = self.space
-            pts, w = tensor2(self.g_reg)
+            pts, w = tensor2(g)
             x = sp.geom.eval(sp.element(e)[0], sp.to_patch(e, pts))
             bw = sp.element_basis(e, pts) * (w * sp.h**2)[:, None]
-            self._tab_cache[e] = (x, bw)
-        return self._tab_cache[e]
+            self._tab_cache[(e, g)] = (x, bw)
+        return self._tab_cache[(e, g)]
 
     def pair_block(self, e: int, f: int, kind_maps=None) -> np.ndarray:
         """(d+1)^2 x (d+1)^2 block int_e int_f G phi_hat_i phi_hat_j for the pair (e, f)."""
@@ -78,8 +95,9 @@ class Assembler:
         kind, me, mf = kind_maps if kind_maps is not None else self.classify(e, f)
         if kind == "regular":
             # tensor Gauss on both elements: sum_pq w_p w_q G(x_p, y_q) phi_i(s_p) phi_j(t_q)
-            xe, be = self._tab(e)
-            xf, bf = self._tab(f)
+            g = self.g_ring if self.ring(e, f) else self.g_far
+            xe, be = self._tab(e, g)
+            xf, bf = self._tab(f, g)
             Gm = green(self.op, self.kappa, xe[:, None, :], xf[None, :, :])
             return be.T @ Gm @ bf
         S, T, W = pair_rule(kind, self.g_reg, self.g_sing)
@@ -101,14 +119,23 @@ class Assembler:
         """
         sp = self.space
         A = np.zeros((sp.ndofs, sp.ndofs), dtype=self.dtype)
-        X = np.stack([self._tab(e)[0] for e in range(sp.nelem)])  # (nelem, g^2, 3)
-        BW = np.stack([self._tab(e)[1] for e in range(sp.nelem)])  # (nelem, g^2, nloc)
+        tabs = {}
+        for g in {self.g_ring, self.g_far}:
+            tabs[g] = (np.stack([self._tab(e, g)[0] for e in range(sp.nelem)]),  # (nelem, g^2, 3)
+                       np.stack([self._tab(e, g)[1] for e in range(sp.nelem)]))  # (nelem, g^2, nloc)
         dofs = np.stack([sp.element_dofs(e) for e in range(sp.nelem)])
         singular: dict[tuple[int, int], np.ndarray] = {}
         for e in range(sp.nelem):
             with np.errstate(divide="ignore", invalid="ignore"):  # touching pairs are replaced below
-                Gm = green(self.op, self.kappa, X[e][:, None, None, :], X[None, :, :, :])  # (g2, nelem, g2)
-                blocks = np.einsum("pi,pfq,fqj->fij", BW[e], Gm, BW)
+                per_order = {}
+                for g, (X, BW) in tabs.items():
+                    Gm = green(self.op, self.kappa, X[e][:, None, None, :], X[None, :, :, :])  # (g2, nelem, g2)
+                    per_order[g] = np.einsum("pi,pfq,fqj->fij", BW[e], Gm, BW)
+            blocks = per_order[self.g_far].copy()
+            if self.g_far != self.g_ring:
+                near = {g for v in self.ids[e] for g in self._v2e[int(v)]}
+                ring_f = np.nonzero(np.isin(self.ids, np.unique(self.ids[list(near)])).any(axis=1))[0]
+                blocks[ring_f] = per_order[self.g_ring][ring_f]
             touching = np.nonzero(np.isin(self.ids, self.ids[e]).any(axis=1))[0]
             for f in touching:
                 if f >= e:

@@ -50,7 +50,7 @@ class Opts(C.Structure):
                 ("g_identical", C.c_int), ("g_edge", C.c_int), ("g_vertex", C.c_int), ("bsr_chunk", C.c_int),
                 ("tensor_cores", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p), ("g_identical_var", C.c_int * 4),
-                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4)]
+                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4), ("g_regular_far", C.c_int)]
 
 
 class OpInfo(C.Structure):
@@ -58,7 +58,8 @@ class OpInfo(C.Structure):
         "ndofs", "nlocal", "nelements", "n_clusters", "n_far_blocks", "n_near_blocks", "n_pairs_regular",
         "n_pairs_identical", "n_pairs_edge", "n_pairs_vertex", "near_bytes", "far_bytes")] + [
         ("leaf_level", C.c_int), ("q", C.c_int), ("degree", C.c_int), ("level", C.c_int),
-        ("assemble_ms", C.c_double), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 8)]
+        ("assemble_ms", C.c_double), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 8),
+        ("n_pairs_regular_far", C.c_int64)]
 
 
 class TuneReport(C.Structure):
@@ -66,7 +67,8 @@ class TuneReport(C.Structure):
                 ("q", C.c_int), ("bsr_chunk", C.c_int), ("err_regular", C.c_double), ("err_identical", C.c_double),
                 ("err_edge", C.c_double), ("err_vertex", C.c_double), ("err_far", C.c_double),
                 ("chunk_ms", C.c_double * 5), ("tune_ms", C.c_double), ("g_identical_var", C.c_int * 4),
-                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4)]
+                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4), ("g_regular_far", C.c_int),
+                ("err_regular_far", C.c_double)]
 
 
 class BatchItem(C.Structure):

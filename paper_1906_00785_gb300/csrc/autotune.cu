@@ -158,17 +158,31 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
     int chosen[4] = {o.g_regular, o.g_singular, o.g_singular, o.g_singular};
     int chosen_var[4][4] = {};
     double errs[4] = {0, 0, 0, 0};
+    int chosen_far = o.g_regular;
+    double err_far_reg = 0.0;
+    // separated pairs beyond the ring next to the touching pairs: own order
+    if (opr.npairs_regular_far > 0) {
+      std::vector<double> ref;
+      for (int gg = 2; gg < kMaxG; ++gg) {
+        const int g4[4] = {gg, gg, gg, gg};
+        const double e = sample_pair_error(opr, kRegular, g4, kMaxG, 4096, &ref, 1);
+        chosen_far = gg;
+        err_far_reg = e;
+        if (e <= quad_tol) break;
+      }
+    }
     for (int ki = 0; ki < 4; ++ki) {
       const int kind = kinds[ki];
       if (opr.npairs[kind] == 0) continue;
       const int g_ref = kMaxG;
       const int max_pairs = kind == kRegular ? 4096 : 512;
+      const int cls = kind == kRegular ? 0 : -1;  // separated: the ring next to the touching pairs
       std::vector<double> ref;  // reference blocks at order g_ref, computed once per kind
       int best = kMaxG - 1;
       double err_best = 0.0;
       for (int gg = 2; gg < g_ref; ++gg) {
         const int g4[4] = {gg, gg, gg, gg};
-        const double e = sample_pair_error(opr, kind, g4, g_ref, max_pairs, &ref);
+        const double e = sample_pair_error(opr, kind, g4, g_ref, max_pairs, &ref, cls);
         best = gg;
         err_best = e;
         if (e <= quad_tol) break;
@@ -190,7 +204,7 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
             if (lo <= 2) break;
             for (int v = 0; v < 4; ++v)
               if (mask >> v & 1) --gv[v];
-            const double e = sample_pair_error(opr, kind, gv, g_ref, max_pairs, &ref);
+            const double e = sample_pair_error(opr, kind, gv, g_ref, max_pairs, &ref, cls);
             if (e <= quad_tol) {
               err_best = e;
             } else {
@@ -265,6 +279,9 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
       dev_free(y);
     }
     inout->g_regular = chosen[0];
+    inout->g_regular_far = chosen_far;
+    r.g_regular_far = chosen_far;
+    r.err_regular_far = err_far_reg;
     inout->g_identical = chosen[1];
     inout->g_edge = chosen[2];
     inout->g_vertex = chosen[3];

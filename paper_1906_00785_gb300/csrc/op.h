@@ -76,6 +76,11 @@ struct Op {
   int g_reg = 4, g_sing = 5;
   int g_kind[4] = {4, 5, 5, 5};  // Gauss points per variable per pair kind (largest of g_var)
   int g_var[4][4] = {};          // per-variable orders per pair kind (regular: g_reg x 4)
+  int g_reg_far = 4;             // separated pairs beyond the ring next to the touching ones
+  int gauss_off_far = 0;         // its [nodes][weights] in d_gauss
+  int64_t npairs_regular_far = 0;
+  double* d_Xq_far = nullptr;    // gamma at the far order's points
+  double* d_BW_far = nullptr;
   double* d_Xq = nullptr;  // nelem * g_reg^2 * 3
   double* d_BW = nullptr;  // g_reg^2 * nloc: w_p h^2 B_k(u_p)
   double* d_gauss = nullptr;  // [g_reg nodes] then per singular kind [nodes, weights]
@@ -128,7 +133,8 @@ double chebyshev01(int q, int a);
 double lagrange01(int q, int a, double x);
 double bernstein_h(int d, int k, double u);
 // quad.cu: max over a sample of pairs of |B_g - B_ref|_F / |B_ref|_F for one pair kind
-double sample_pair_error(Op& o, int kind, const int g[4], int g_ref, int max_pairs, std::vector<double>* ref_cache);
+double sample_pair_error(Op& o, int kind, const int g[4], int g_ref, int max_pairs, std::vector<double>* ref_cache,
+                         int cls = -1);
 // autotune.cu
 int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
                   double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep);

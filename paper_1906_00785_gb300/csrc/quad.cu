@@ -13,6 +13,7 @@
 //   in duffy_point().
 // * k_coupling: far-field coupling K_ab = G(gamma(x_a^tau), gamma(x_b^sigma))
 //   at the cluster Chebyshev points (Sec. 2, interpolation on the unit square).
+#include <algorithm>
 #include <vector>
 
 #include "op.h"
@@ -119,21 +120,37 @@ __device__ __forceinline__ void regular_pair(const PairRec& pr, const double* __
   __syncwarp();
 }
 
+// Separated pairs: the ring next to the touching pairs (pad 0) at order G2 =
+// g^2 points per element, farther pairs (pad 1) at their own order G2f.
 template <int D, bool CPLX>
 __global__ void __launch_bounds__(32 * kWarps) k_near_regular(const PairRec* __restrict__ pairs, int64_t npairs,
                                                               const double* __restrict__ Xq,
-                                                              const double* __restrict__ BWg, int G2, double kre,
+                                                              const double* __restrict__ BWg, int G2,
+                                                              const double* __restrict__ Xqf,
+                                                              const double* __restrict__ BWfg, int G2f, double kre,
                                                               double kim, double* __restrict__ N, int nld) {
   constexpr int NL = (D + 1) * (D + 1);
   constexpr int C = CPLX ? 2 : 1;
   extern __shared__ double sh[];
-  double* BW = sh;                                                  // G2 * NL
-  double* ubuf = sh + G2 * NL + (threadIdx.x >> 5) * G2 * NL * C;  // per warp
+  const int gmax = max(G2, G2f);
+  double* BW = sh;                                                      // G2 * NL
+  double* BWf = sh + G2 * NL;                                           // G2f * NL
+  double* ubuf = BWf + G2f * NL + (threadIdx.x >> 5) * gmax * NL * C;  // per warp
   for (int i = threadIdx.x; i < G2 * NL; i += blockDim.x) BW[i] = BWg[i];
+  for (int i = threadIdx.x; i < G2f * NL; i += blockDim.x) BWf[i] = BWfg[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < npairs; w += (int64_t)gridDim.x * kWarps)
-    regular_pair<D, CPLX>(pairs[w], Xq, BW, ubuf, G2, kre, kim, N, nld, lane);
+  for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < npairs; w += (int64_t)gridDim.x * kWarps) {
+    const PairRec& pr = pairs[w];
+    if (pr.pad)
+      regular_pair<D, CPLX>(pr, Xqf, BWf, ubuf, G2f, kre, kim, N, nld, lane);
+    else
+      regular_pair<D, CPLX>(pr, Xq, BW, ubuf, G2, kre, kim, N, nld, lane);
+  }
+}
+
+size_t regular_smem(int G2, int G2f, int NL, int C) {
+  return sizeof(double) * ((size_t)G2 * NL + (size_t)G2f * NL + (size_t)kWarps * std::max(G2, G2f) * NL * C);
 }
 
 // One touching pair per warp; lanes stride over the nsub * g^4 rule points and
@@ -300,13 +317,14 @@ void launch_pairs(Op& o, cudaEvent_t* ev) {
   const int NL = (D + 1) * (D + 1);
   const int threads = 32 * kWarps;
   if (o.npairs[kRegular] > 0) {
-    const size_t shm = sizeof(double) * (G2 * NL + kWarps * G2 * NL * (CPLX ? 2 : 1));
+    const int G2f = o.g_reg_far * o.g_reg_far;
+    const size_t shm = regular_smem(G2, G2f, NL, CPLX ? 2 : 1);
     if (shm > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_near_regular<D, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm)),
                  "smem attr");
     const int grid = int(std::min<int64_t>((o.npairs[kRegular] + kWarps - 1) / kWarps, 152 * 64));
     k_near_regular<D, CPLX><<<grid, threads, shm, s>>>(o.d_pairs[kRegular], o.npairs[kRegular], o.d_Xq, o.d_BW,
-                                                       G2, o.kre, o.kim, o.d_N, o.nld);
+                                                       G2, o.d_Xq_far, o.d_BW_far, G2f, o.kre, o.kim, o.d_N, o.nld);
     launched("k_near_regular");
   }
   cuda_check(cudaEventRecord(ev[2], s), "event");
@@ -342,6 +360,7 @@ void alloc_assembly_outputs(Op& o) {
   const int64_t nN = o.nnear * (int64_t)o.nld * o.nld * C;
   const int64_t nK = o.nfar * (int64_t)o.q2 * o.q2;
   o.d_Xq = static_cast<double*>(dev_alloc(sizeof(double) * o.nelem * o.g_reg * o.g_reg * 3));
+  o.d_Xq_far = static_cast<double*>(dev_alloc(sizeof(double) * o.nelem * o.g_reg_far * o.g_reg_far * 3));
   o.d_N = static_cast<double*>(dev_alloc(sizeof(double) * std::max<int64_t>(nN, 1)));
   if (nK > 0) o.d_K = static_cast<double*>(dev_alloc(sizeof(double) * nK * C));
   if (o.opts.precision == BEMBEL_PREC_MIXED) {
@@ -364,6 +383,10 @@ void run_assembly_kernels(Op& o) {
   {
     const int64_t n = o.nelem * o.g_reg * o.g_reg;
     k_tabulate<<<grid_for(n, 256), 256, 0, s>>>(o.geom, o.L, o.nelem, o.g_reg, o.d_gauss, o.h, o.d_Xq);
+    launched("k_tabulate");
+    const int64_t nf = o.nelem * o.g_reg_far * o.g_reg_far;
+    k_tabulate<<<grid_for(nf, 256), 256, 0, s>>>(o.geom, o.L, o.nelem, o.g_reg_far, o.d_gauss + o.gauss_off_far, o.h,
+                                                 o.d_Xq_far);
     launched("k_tabulate");
   }
   cuda_check(cudaEventRecord(ev[1], s), "event");
@@ -427,6 +450,8 @@ struct MeshWork {
   Geom geom;
   int L, nld;
   const double* BW;  // regular basis x weight table (holds h^2: per level)
+  const double* BWf; // the same for the far separated order
+  double* Xqf;
   double kre, kim, h;
   int64_t nelem;
   double* Xq;
@@ -446,13 +471,13 @@ struct Segment {
 };
 
 __global__ void k_tabulate_multi(const MeshWork* __restrict__ ms, const long long* __restrict__ off, int nmesh, int G,
-                                 const double* __restrict__ gx) {
+                                 const double* __restrict__ gx, bool far) {
   const long long total = off[nmesh];
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
     int m = 0;
     while (id >= off[m + 1]) ++m;
-    tabulate_point(ms[m].geom, ms[m].L, G, gx, ms[m].h, id - off[m], ms[m].Xq);
+    tabulate_point(ms[m].geom, ms[m].L, G, gx, ms[m].h, id - off[m], far ? ms[m].Xqf : ms[m].Xq);
   }
 }
 
@@ -470,13 +495,13 @@ template <int D, bool CPLX>
 __global__ void __launch_bounds__(32 * kWarps) k_assemble_multi(const MeshWork* __restrict__ ms,
                                                                 const Segment* __restrict__ segs_g, int nseg,
                                                                 long long nitems, unsigned long long* __restrict__ next,
-                                                                int G2,
+                                                                int G2, int G2f,
                                                                 const double* __restrict__ gauss, int4 gi, int4 ge,
                                                                 int4 gv, int3 goff, int q2) {
   constexpr int NL = (D + 1) * (D + 1);
   constexpr int C = CPLX ? 2 : 1;
   extern __shared__ double sh[];
-  double* ubuf = sh + (threadIdx.x >> 5) * G2 * NL * C;
+  double* ubuf = sh + (threadIdx.x >> 5) * max(G2, G2f) * NL * C;
   __shared__ double gx[3][4][kMaxG], gw[3][4][kMaxG];
   __shared__ Segment segs[kMaxSegments];
   for (int i = threadIdx.x; i < nseg; i += blockDim.x) segs[i] = segs_g[i];
@@ -499,7 +524,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_assemble_multi(const MeshWork* 
     switch (sg.phase) {
       case kRegular:
         for (long long w = first; w < last; ++w)
-          regular_pair<D, CPLX>(m.pairs[kRegular][w], m.Xq, m.BW, ubuf, G2, m.kre, m.kim, m.N, m.nld, lane);
+          if (m.pairs[kRegular][w].pad)
+            regular_pair<D, CPLX>(m.pairs[kRegular][w], m.Xqf, m.BWf, ubuf, G2f, m.kre, m.kim, m.N, m.nld, lane);
+          else
+            regular_pair<D, CPLX>(m.pairs[kRegular][w], m.Xq, m.BW, ubuf, G2, m.kre, m.kim, m.N, m.nld, lane);
         break;
       case kIdentical:
         for (long long w = first; w < last; ++w)
@@ -532,7 +560,8 @@ void launch_multi(const std::vector<Op*>& ops, const MeshWork* d_ms, const Segme
   const Op& o = *ops[0];
   const int G2 = o.g_reg * o.g_reg;
   const int NL = (D + 1) * (D + 1);
-  const size_t shm = sizeof(double) * (kWarps * G2 * NL * (CPLX ? 2 : 1));
+  const int G2f = o.g_reg_far * o.g_reg_far;
+  const size_t shm = sizeof(double) * (kWarps * std::max(G2, G2f) * NL * (CPLX ? 2 : 1));
   if (shm > 48 * 1024)
     cuda_check(cudaFuncSetAttribute(k_assemble_multi<D, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm)),
                "smem attr");
@@ -545,7 +574,7 @@ void launch_multi(const std::vector<Op*>& ops, const MeshWork* d_ms, const Segme
   const long long want = (nitems + kWarps - 1) / kWarps;
   const int grid = int(std::max<long long>(1, std::min<long long>(want, (long long)std::max(1, per_sm) * nsm)));
   const int3 goff = make_int3(int(o.gauss_off[kIdentical]), int(o.gauss_off[kEdge]), int(o.gauss_off[kVertex]));
-  k_assemble_multi<D, CPLX><<<grid, 32 * kWarps, shm, s>>>(d_ms, d_seg, nseg, nitems, d_next, G2, o.d_gauss,
+  k_assemble_multi<D, CPLX><<<grid, 32 * kWarps, shm, s>>>(d_ms, d_seg, nseg, nitems, d_next, G2, G2f, o.d_gauss,
                                                            rule_orders(o, kIdentical), rule_orders(o, kEdge),
                                                            rule_orders(o, kVertex), goff, o.q2);
   launched("k_assemble_multi");
@@ -563,7 +592,7 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
   for (Op* o : ops) alloc_assembly_outputs(*o);
   // per-mesh descriptors and offsets of the tabulation and copy ranges
   std::vector<MeshWork> mw(nmesh);
-  std::vector<long long> tab_off(nmesh + 1, 0), cpy_off(nmesh + 1, 0);
+  std::vector<long long> tab_off(nmesh + 1, 0), tabf_off(nmesh + 1, 0), cpy_off(nmesh + 1, 0);
   for (int m = 0; m < nmesh; ++m) {
     const Op& o = *ops[m];
     MeshWork& w = mw[m];
@@ -571,6 +600,8 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
     w.L = o.L;
     w.nld = o.nld;
     w.BW = o.d_BW;
+    w.BWf = o.d_BW_far;
+    w.Xqf = o.d_Xq_far;
     w.kre = o.kre;
     w.kim = o.kim;
     w.h = o.h;
@@ -585,6 +616,7 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
     w.nodes = o.d_nodes;
     w.K = o.d_K;
     tab_off[m + 1] = tab_off[m] + o.nelem * (long long)o.g_reg * o.g_reg;
+    tabf_off[m + 1] = tabf_off[m] + o.nelem * (long long)o.g_reg_far * o.g_reg_far;
     cpy_off[m + 1] = cpy_off[m] + (mixed ? w.nN : 0);
   }
   // segments: most expensive phases first (edge, identical, vertex, regular, coupling)
@@ -607,7 +639,8 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
       seg.push_back(sg);
     }
   DevBuf dms(sizeof(MeshWork) * nmesh), dseg(sizeof(Segment) * std::max<size_t>(1, seg.size())),
-      dtab(sizeof(long long) * (nmesh + 1)), dcpy(sizeof(long long) * (nmesh + 1)), dnext(sizeof(unsigned long long));
+      dtab(sizeof(long long) * (nmesh + 1)), dtabf(sizeof(long long) * (nmesh + 1)),
+      dcpy(sizeof(long long) * (nmesh + 1)), dnext(sizeof(unsigned long long));
   cuda_check(cudaMemcpyAsync(dms.p, mw.data(), sizeof(MeshWork) * nmesh, cudaMemcpyHostToDevice, s), "mesh upload");
   if (!seg.empty())
     cuda_check(cudaMemcpyAsync(dseg.p, seg.data(), sizeof(Segment) * seg.size(), cudaMemcpyHostToDevice, s),
@@ -616,13 +649,19 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
              "offsets");
   cuda_check(cudaMemcpyAsync(dcpy.p, cpy_off.data(), sizeof(long long) * (nmesh + 1), cudaMemcpyHostToDevice, s),
              "offsets");
+  cuda_check(cudaMemcpyAsync(dtabf.p, tabf_off.data(), sizeof(long long) * (nmesh + 1), cudaMemcpyHostToDevice, s),
+             "offsets");
   cuda_check(cudaMemsetAsync(dnext.p, 0, sizeof(unsigned long long), s), "counter");
   const MeshWork* d_ms = static_cast<const MeshWork*>(dms.p);
   cudaEvent_t ev[4];
   for (auto& e : ev) cuda_check(cudaEventCreate(&e), "event");
   cuda_check(cudaEventRecord(ev[0], s), "event");
   k_tabulate_multi<<<grid_for(tab_off[nmesh], 256), 256, 0, s>>>(d_ms, static_cast<const long long*>(dtab.p), nmesh,
-                                                                  o0.g_reg, o0.d_gauss);
+                                                                  o0.g_reg, o0.d_gauss, false);
+  launched("k_tabulate_multi");
+  k_tabulate_multi<<<grid_for(tabf_off[nmesh], 256), 256, 0, s>>>(d_ms, static_cast<const long long*>(dtabf.p),
+                                                                   nmesh, o0.g_reg_far, o0.d_gauss + o0.gauss_off_far,
+                                                                   true);
   launched("k_tabulate_multi");
   cuda_check(cudaEventRecord(ev[1], s), "event");
   if (nitems > 0) {
@@ -697,11 +736,12 @@ void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, const int 
     cuda_check(cudaMemcpy(d_BW, BW.data(), sizeof(double) * BW.size(), cudaMemcpyHostToDevice), "BW");
     k_tabulate<<<grid_for(o.nelem * G2, 256), 256, 0, s>>>(o.geom, o.L, o.nelem, g, d_tab, o.h, Xq);
     launched("k_tabulate");
-    const size_t shm = sizeof(double) * (G2 * nloc + kWarps * G2 * nloc * (CPLX ? 2 : 1));
+    const size_t shm = regular_smem(G2, G2, nloc, CPLX ? 2 : 1);
     if (shm > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_near_regular<D, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm)),
                  "smem attr");
-    k_near_regular<D, CPLX><<<grid, threads, shm, s>>>(d_sample, ns, Xq, d_BW, G2, o.kre, o.kim, out, nloc);
+    k_near_regular<D, CPLX><<<grid, threads, shm, s>>>(d_sample, ns, Xq, d_BW, G2, Xq, d_BW, G2, o.kre, o.kim, out,
+                                                       nloc);
     launched("k_near_regular");
     cuda_check(cudaStreamSynchronize(s), "sample sync");
     dev_free(Xq);
@@ -725,15 +765,22 @@ void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, const int 
 
 }  // namespace
 
-double sample_pair_error(Op& o, int kind, const int g[4], int g_ref, int max_pairs, std::vector<double>* ref_cache) {
-  const int64_t ns = std::min<int64_t>(o.npairs[kind], max_pairs);
-  if (ns == 0) return 0.0;
+double sample_pair_error(Op& o, int kind, const int g[4], int g_ref, int max_pairs, std::vector<double>* ref_cache,
+                         int cls) {
   const int C = o.cplx ? 2 : 1;
   const int nloc = o.nloc;
-  // the first ns pairs of the list (built in parallel, so not ordered by
-  // position), each given a compact output block
-  std::vector<PairRec> all(ns);
-  cuda_check(cudaMemcpy(all.data(), o.d_pairs[kind], sizeof(PairRec) * ns, cudaMemcpyDeviceToHost), "sample");
+  // up to max_pairs pairs from the start of the list (built in parallel, so not
+  // ordered by position), of the given separation class (separated pairs; -1:
+  // any), each given a compact output block
+  const int64_t look = std::min<int64_t>(o.npairs[kind], cls < 0 ? max_pairs : 16 * (int64_t)max_pairs);
+  std::vector<PairRec> all(look);
+  if (look > 0)
+    cuda_check(cudaMemcpy(all.data(), o.d_pairs[kind], sizeof(PairRec) * look, cudaMemcpyDeviceToHost), "sample");
+  if (cls >= 0)
+    all.erase(std::remove_if(all.begin(), all.end(), [&](const PairRec& p) { return p.pad != cls; }), all.end());
+  if ((int64_t)all.size() > max_pairs) all.resize(max_pairs);
+  const int64_t ns = (int64_t)all.size();
+  if (ns == 0) return 0.0;
   for (int64_t i = 0; i < ns; ++i) {
     all[i].off1 = i * (long long)nloc * nloc;
     all[i].off2 = -1;

@@ -325,7 +325,7 @@ void parallel_for(int64_t n, F fn) {
 __global__ void k_build_pairs(const long long* __restrict__ nptr, const int* __restrict__ ncol,
                               const int* __restrict__ ntgt, int64_t nnear, const int* __restrict__ cid, int m2,
                               int nloc, int nld, int pass, unsigned long long* __restrict__ cnt, PairRec* out0,
-                              PairRec* out1, PairRec* out2, PairRec* out3) {
+                              PairRec* out1, PairRec* out2, PairRec* out3, const int* __restrict__ v2e) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= nnear * (int64_t)m2 * m2) return;
   const int64_t blk = id / ((int64_t)m2 * m2);
@@ -374,7 +374,27 @@ __global__ void k_build_pairs(const long long* __restrict__ nptr, const int* __r
   pr.e = int(e);
   pr.f = int(f);
   pr.code = kind | (me << 2) | (mf << 5);
+  // separated pairs: 0 if one element holds a corner of e and a corner of f
+  // (the ring next to the touching pairs), 1 if they lie farther apart
   pr.pad = 0;
+  if (kind == kRegular) {
+    int far = 1;
+    for (int a = 0; a < 4 && far; ++a) {
+      const int v = cid[e * 4 + a];
+      for (int sl = 0; sl < 4 && far; ++sl) {
+        const int g = v2e[v * 4 + sl];
+        if (g < 0) continue;
+        for (int c = 0; c < 4 && far; ++c)
+          for (int b = 0; b < 4; ++b)
+            if (cid[(int64_t)g * 4 + c] == cid[f * 4 + b]) {
+              far = 0;
+              break;
+            }
+      }
+    }
+    pr.pad = far;
+    if (far) atomicAdd(&cnt[4], 1ull);
+  }
   pr.off1 = blk * blk2 + (long long)(pe * nloc) * nld + pf * nloc;
   pr.off2 = (e == f) ? -1 : lo * blk2 + (long long)(pf * nloc) * nld + pe * nloc;
   const unsigned long long slot_out = atomicAdd(&cnt[kind], 1ull);
@@ -570,16 +590,30 @@ void build_structure(Op& o) {
   {
     std::vector<int> cid32(cid.begin(), cid.end());
     int* d_cid = upload(cid32);
-    unsigned long long* d_cnt = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * 4));
+    // vertex -> the (at most 4) elements holding it, -1 padded
+    int nvert = 0;
+    for (int v : cid32) nvert = std::max(nvert, v + 1);
+    std::vector<int> v2e((size_t)nvert * 4, -1);
+    for (int64_t e = 0; e < o.nelem; ++e)
+      for (int a = 0; a < 4; ++a) {
+        int* slot = &v2e[(size_t)cid32[e * 4 + a] * 4];
+        for (int k = 0; k < 4; ++k)
+          if (slot[k] < 0) {
+            slot[k] = int(e);
+            break;
+          }
+      }
+    int* d_v2e = upload(v2e);
+    unsigned long long* d_cnt = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * 5));
     const int64_t work = o.nnear * (int64_t)m2 * m2;
     const int tb = 256;
     const int grid = int(std::max<int64_t>(1, (work + tb - 1) / tb));
     PairRec* outs[4] = {nullptr, nullptr, nullptr, nullptr};
-    unsigned long long cnt[4];
+    unsigned long long cnt[5];
     for (int pass = 0; pass < 2; ++pass) {
-      cuda_check(cudaMemset(d_cnt, 0, sizeof(unsigned long long) * 4), "pair counters");
+      cuda_check(cudaMemset(d_cnt, 0, sizeof(unsigned long long) * 5), "pair counters");
       k_build_pairs<<<grid, tb>>>(o.d_near_ptr, o.d_near_col, o.d_near_tgt, o.nnear, d_cid, m2, o.nloc, o.nld,
-                                   pass, d_cnt, outs[0], outs[1], outs[2], outs[3]);
+                                   pass, d_cnt, outs[0], outs[1], outs[2], outs[3], d_v2e);
       launched("k_build_pairs");
       cuda_check(cudaMemcpy(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost), "pair counts");
       if (pass == 0)
@@ -592,6 +626,8 @@ void build_structure(Op& o) {
       if (cnt[k] != (unsigned long long)o.npairs[k]) fail(BEMBEL_EINVAL, "pair list build is inconsistent");
       o.d_pairs[k] = outs[k];
     }
+    o.npairs_regular_far = (int64_t)cnt[4];
+    dev_free(d_v2e);
     unsigned long long bad = 0;
     dev_free(d_cid);
     dev_free(d_cnt);
@@ -690,6 +726,20 @@ void build_structure(Op& o) {
             BW[(size_t)(p1 + G * p2) * nloc + k1 + (d + 1) * k2] =
                 gw[p1] * gw[p2] * o.h * o.h * bernstein_h(d, k1, gx[p1]) * bernstein_h(d, k2, gx[p2]);
     o.d_BW = upload(BW);
+    {
+      // separated pairs farther than the ring next to the touching pairs: own order
+      std::vector<double> fx, fw;
+      gauss01(o.g_reg_far, fx, fw);
+      const int F = o.g_reg_far, F2 = F * F;
+      std::vector<double> BWf((size_t)F2 * nloc, 0.0);
+      for (int p2 = 0; p2 < F && !o.efie; ++p2)
+        for (int p1 = 0; p1 < F; ++p1)
+          for (int k2 = 0; k2 <= d; ++k2)
+            for (int k1 = 0; k1 <= d; ++k1)
+              BWf[(size_t)(p1 + F * p2) * nloc + k1 + (d + 1) * k2] =
+                  fw[p1] * fw[p2] * o.h * o.h * bernstein_h(d, k1, fx[p1]) * bernstein_h(d, k2, fx[p2]);
+      o.d_BW_far = upload(BWf);
+    }
     // per kind (regular first) and per variable: nodes then weights; the
     // regular kind repeats g_reg four times (its first nodes tabulate gamma)
     std::vector<double> rg;
@@ -701,6 +751,10 @@ void build_structure(Op& o) {
         rg.insert(rg.end(), gw.begin(), gw.end());
       }
     }
+    o.gauss_off_far = int(rg.size());  // nodes then weights of the far separated order
+    gauss01(o.g_reg_far, gx, gw);
+    rg.insert(rg.end(), gx.begin(), gx.end());
+    rg.insert(rg.end(), gw.begin(), gw.end());
     o.d_gauss = upload(rg);
   }
 
@@ -717,6 +771,7 @@ void build_structure(Op& o) {
   in.n_pairs_identical = o.npairs[kIdentical];
   in.n_pairs_edge = o.npairs[kEdge];
   in.n_pairs_vertex = o.npairs[kVertex];
+  in.n_pairs_regular_far = o.npairs_regular_far;
   in.near_bytes = o.nnear * blk2 * 8 * (o.cplx ? 2 : 1);
   in.far_bytes = o.nfar * (int64_t)o.q2 * o.q2 * 8 * (o.cplx ? 2 : 1);
   in.leaf_level = o.leaf;

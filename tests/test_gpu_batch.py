@@ -31,7 +31,7 @@ def test_batch_equals_single(kind, k, p):
     per = bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=perturbed_sphere_coeffs(2001))
     items = [(sph, k, 2), (per, 1.5 * k, 3), (sph, 0.5 * k + 0.2j * (kind == HEL), 4), (per, k, 2)]
     kw = dict(g_regular=3, g_singular=4, g_edge=5, eta=1.6, precision=bem.BEMBEL_PREC_MIXED,
-              g_identical_var=(4, 5, 3, 3) if kind == HEL else (0, 0, 0, 0))
+              g_identical_var=(4, 5, 3, 3) if kind == HEL else (0, 0, 0, 0), g_regular_far=2 if kind == LAP else 0)
     ops = bem.bembel_assemble_batch(items, kind, p, 4, **kw)
     assert len(ops) == len(items)
     for (g, kk, L), op in zip(items, ops):

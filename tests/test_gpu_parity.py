@@ -291,6 +291,20 @@ def test_per_variable_orders_parity(geom, op, k, d):
     assert rel_err(gpu_matrix(gop, sp.ndofs), A_ref) < 1e-12
 
 
+@pytest.mark.parametrize("op,k,d", [("laplace", 0.0, 1), ("helmholtz", 1.5, 0)])
+def test_graded_separated_orders_parity(geom, op, k, d):
+    """Separated pairs beyond the ring next to the touching pairs at their own order."""
+    gop = bem.bembel_assemble(geom, LAP if op == "laplace" else HEL, k, 3, d, 0, g_regular=4, g_regular_far=2,
+                              g_singular=4)
+    sp = S2Space(Sphere6(), 3, d)
+    asm = Assembler(sp, op, k, (4, 2), 4)
+    info = bem.bembel_op_info_get(gop)
+    far = sum(1 for e in range(sp.nelem) for f in range(e + 1, sp.nelem)
+              if asm.classify(e, f)[0] == "regular" and not asm.ring(e, f))
+    assert info["n_pairs_regular_far"] == far > 0
+    assert rel_err(gpu_matrix(gop, sp.ndofs), asm.dense()) < 1e-12
+
+
 def test_per_variable_orders_invalid(geom):
     for kw in (dict(g_edge_var=(4, 0, 5, 3)), dict(g_edge_var=(4, 11, 11, 3)),
                dict(g_edge_var=(4, 4, 5, 3)), dict(g_vertex_var=(5, 4, 4, 3))):  # partial, too large, asymmetric
