@@ -23,6 +23,9 @@ def main():
     ap.add_argument("--q", type=int, default=4)
     ap.add_argument("--g-regular", type=int, default=4)
     ap.add_argument("--g-singular", type=int, default=5)
+    ap.add_argument("--g-regular-far", type=int, default=0, help="separated pairs beyond the ring (0: g-regular)")
+    for cls in ("identical", "edge", "vertex"):
+        ap.add_argument(f"--g-{cls}-var", type=str, default="", help="four per-variable Duffy orders, e.g. 4,5,3,3")
     ap.add_argument("--matvecs", type=int, default=3)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--fp32", action="store_true", help="assemble MIXED and time the FP32 matvec")
@@ -33,8 +36,11 @@ def main():
     geom = bem.bembel_geom_create(bem.BEMBEL_GEOM_SPHERE6)
     op_kind = bem.BEMBEL_LAPLACE_SL if a.op == "laplace" else bem.BEMBEL_HELMHOLTZ_SL
     prec = bem.BEMBEL_PREC_MIXED if a.fp32 else bem.BEMBEL_PREC_FP64
+    var = {f"g_{c}_var": [int(v) for v in getattr(a, f"g_{c}_var").split(",")]
+           for c in ("identical", "edge", "vertex") if getattr(a, f"g_{c}_var")}
     op = bem.bembel_assemble(geom, op_kind, a.k if a.op == "helmholtz" else 0.0, a.level, a.degree, a.q,
-                             g_regular=a.g_regular, g_singular=a.g_singular, precision=prec)
+                             g_regular=a.g_regular, g_singular=a.g_singular, g_regular_far=a.g_regular_far,
+                             precision=prec, **var)
     n = bem.bembel_ndofs(op)
     cplx = a.op == "helmholtz"
     dt = (torch.complex64 if a.fp32 else torch.complex128) if cplx else (torch.float32 if a.fp32 else torch.float64)
