@@ -54,7 +54,8 @@ extern "C" {
 /* ---- enumerations ---------------------------------------------------------- */
 enum bembel_geom_kind {
   BEMBEL_GEOM_SPHERE6 = 0,          /* unit sphere, 6 cube-face patches gamma = c/|c| */
-  BEMBEL_GEOM_PERTURBED_SPHERE = 1  /* r(x) = 1 + amp * sum a_lm Y_lm(x), 1 <= l <= 4   */
+  BEMBEL_GEOM_PERTURBED_SPHERE = 1, /* r(x) = 1 + amp * sum a_lm Y_lm(x), 1 <= l <= 4   */
+  BEMBEL_GEOM_NURBS = 2             /* six rational B-spline patches (Sec. 4.1, App. C) */
 };
 enum bembel_op_kind {
   BEMBEL_LAPLACE_SL = 0,   /* App. B (LS): G = 1/(4 pi r)                 */
@@ -92,6 +93,16 @@ typedef struct {
   int n_coeffs;          /* PERTURBED_SPHERE: number of a_lm, must be 24 (l = 1..4)  */
   const double* coeffs;  /* PERTURBED_SPHERE: a_lm ordered (l, m = -l..l), host ptr   */
   double amplitude;      /* PERTURBED_SPHERE: amp (0.1 in the perturbed workload)     */
+  /* NURBS: gamma_P(s,t) = sum N_a(s) N_b(t) w_ab P_ab / sum N_a(s) N_b(t) w_ab with
+   * B-splines N on open knot vectors over [0,1] (App. C).  Six patches in the
+   * order and orientation of the cube-face sphere (patch 0 faces +x, 1 -x, 2 +y,
+   * 3 -y, 4 +z, 5 -z; d_s gamma x d_t gamma outward), meeting at full edges with
+   * matching parametrisations (App. D).  Host arrays, read during the call:    */
+  int n_patches;          /* must be 6                                              */
+  const int* degrees;     /* (p1, p2) per patch, 1 <= p <= 4                        */
+  const int* n_ctrl;      /* (k1, k2) control points per direction per patch       */
+  const double* knots;    /* per patch: k1 + p1 + 1 knots in s, then k2 + p2 + 1 in t */
+  const double* ctrl;     /* per patch: k1 k2 points (x, y, z, w > 0), index i1 + k1 i2 */
 } bembel_geom_desc;
 
 /* Assembly options.  Fill with bembel_opts_default, then override. */
@@ -197,7 +208,9 @@ int64_t bembel_kernel_launches(void);
 /* Create a geometry (App. D: patches with outward normals meeting at full
  * edges or vertices; the matching condition holds for both kinds by
  * construction).  desc and desc->coeffs are read during the call only.
- * Errors: EINVAL (NULL pointers, unknown kind, wrong n_coeffs), ENOMEM. */
+ * Errors: EINVAL (NULL pointers, unknown kind, wrong n_coeffs, NURBS data that is
+ * not 6 patches of degree 1..4 on open knot vectors with positive weights),
+ * ENOMEM, ECUDA.  The geometry must outlive every operator assembled on it. */
 int bembel_geom_create(const bembel_geom_desc* desc, bembel_geom** out);
 int bembel_geom_destroy(bembel_geom* g);
 

@@ -88,3 +88,43 @@ WORKLOADS = {
     "efie_L4_p2_q6": dict(op="maxwell", k=4.0, level=4, p=2, q=6, n_eval=100, eval_radius=3.0,
                           eval_seed=4),
 }
+
+
+# (o, e1, e2) per cube face, e1 x e2 = o, in the patch order of the cube-face
+# sphere: +x, -x, +y, -y, +z, -z (neighbouring faces then run the same way
+# along every shared edge).
+CUBE_FACES = (
+    ((1, 0, 0), (0, 1, 0), (0, 0, 1)),
+    ((-1, 0, 0), (0, 0, 1), (0, 1, 0)),
+    ((0, 1, 0), (0, 0, 1), (1, 0, 0)),
+    ((0, -1, 0), (1, 0, 0), (0, 0, 1)),
+    ((0, 0, 1), (1, 0, 0), (0, 1, 0)),
+    ((0, 0, -1), (0, 1, 0), (1, 0, 0)),
+)
+
+
+def nurbs_pillow_box(degree: int = 2, segments: int = 2, bulge: float = 0.3, weight: float = 1.6):
+    """Six NURBS patches forming a closed 'pillow box' around the cube [-1, 1]^3.
+
+    Each face is a degree-``degree`` B-spline patch with ``segments`` uniform knot
+    spans per direction; control points sit at the Greville abscissae g of the
+    face, pushed outward by bulge * b(g1) b(g2) (b(g) = 4 g (1 - g)) with weights
+    1 + (weight - 1) b(g1) b(g2).  Boundary control points lie on the cube edges
+    with weight 1, so neighbouring faces share their edge curves exactly.
+    Returns six dicts: degrees, knots (s, t) and ctrl[i2, i1] = (x, y, z, w)."""
+    p = degree
+    kn = np.concatenate([np.zeros(p + 1), np.arange(1, segments) / segments, np.ones(p + 1)])
+    k = segments + p
+    grev = np.array([kn[i + 1 : i + p + 1].mean() for i in range(k)])
+    bump = 4.0 * grev * (1.0 - grev)
+    patches = []
+    for o, e1, e2 in CUBE_FACES:
+        o, e1, e2 = (np.array(v, dtype=float) for v in (o, e1, e2))
+        ctrl = np.zeros((k, k, 4))
+        for i2 in range(k):
+            for i1 in range(k):
+                b = bump[i1] * bump[i2]
+                ctrl[i2, i1, :3] = o * (1.0 + bulge * b) + (2 * grev[i1] - 1) * e1 + (2 * grev[i2] - 1) * e2
+                ctrl[i2, i1, 3] = 1.0 + (weight - 1.0) * b
+        patches.append({"degrees": (p, p), "knots": (kn.copy(), kn.copy()), "ctrl": ctrl})
+    return patches

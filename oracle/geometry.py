@@ -113,3 +113,38 @@ class PerturbedSphere(Sphere6):
             d[a] = h
             cols.append((self.eval(patch, st + d) - self.eval(patch, st - d)) / (2 * h))
         return np.stack(cols, axis=-1)
+
+
+class NurbsSurface:
+    """Patches gamma(s,t) = sum N_a(s) N_b(t) w_ab P_ab / sum N_a(s) N_b(t) w_ab (rational
+    tensor B-splines, Sec. 4.1 / App. C), B-spline values from scipy's design matrix.
+    ``patches``: dicts with degrees (p1, p2), knots (s, t) and ctrl[i2, i1] = (x, y, z, w)."""
+
+    def __init__(self, patches):
+        self.patches = patches
+        self.npatch = len(patches)
+
+    def eval(self, patch: int, st: np.ndarray) -> np.ndarray:
+        from scipy.interpolate import BSpline
+
+        pt = self.patches[patch]
+        (p1, p2), (k1s, k2s), ctrl = pt["degrees"], pt["knots"], np.asarray(pt["ctrl"], dtype=float)
+        st = np.atleast_2d(np.asarray(st, dtype=float))
+        Ns = BSpline.design_matrix(np.clip(st[:, 0], 0.0, 1.0), k1s, p1).toarray()  # (n, k1)
+        Nt = BSpline.design_matrix(np.clip(st[:, 1], 0.0, 1.0), k2s, p2).toarray()  # (n, k2)
+        w = ctrl[..., 3]
+        num = np.einsum("na,nb,ba,bac->nc", Ns, Nt, w, ctrl[..., :3])
+        den = np.einsum("na,nb,ba->n", Ns, Nt, w)
+        return num / den[:, None]
+
+    def jacobian(self, patch: int, st: np.ndarray, h: float = 1e-6) -> np.ndarray:
+        """Central differences, one-sided at the patch boundary."""
+        st = np.atleast_2d(np.asarray(st, dtype=float))
+        cols = []
+        for a in range(2):
+            d = np.zeros(2)
+            d[a] = h
+            lo = np.clip(st - d, 0.0, 1.0)
+            hi = np.clip(st + d, 0.0, 1.0)
+            cols.append((self.eval(patch, hi) - self.eval(patch, lo)) / (hi[:, a] - lo[:, a])[:, None])
+        return np.stack(cols, axis=-1)

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbembel.so")
 
 BEMBEL_OK, BEMBEL_EINVAL, BEMBEL_ENOMEM, BEMBEL_ECUDA, BEMBEL_ENOTCONV, BEMBEL_ETIMEOUT, BEMBEL_EUNSUPPORTED = range(7)
-BEMBEL_GEOM_SPHERE6, BEMBEL_GEOM_PERTURBED_SPHERE = 0, 1
+BEMBEL_GEOM_SPHERE6, BEMBEL_GEOM_PERTURBED_SPHERE, BEMBEL_GEOM_NURBS = 0, 1, 2
 BEMBEL_LAPLACE_SL, BEMBEL_HELMHOLTZ_SL, BEMBEL_MAXWELL_SL = 0, 1, 2
 BEMBEL_PREC_FP64, BEMBEL_PREC_MIXED = 0, 1
 BEMBEL_RHS_POINT_SOURCE, BEMBEL_RHS_PLANE_WAVE, BEMBEL_RHS_EFIE_PLANE_WAVE = 0, 1, 2
@@ -42,7 +42,9 @@ class BembelError(RuntimeError):
 
 class GeomDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_coeffs", C.c_int), ("coeffs", C.POINTER(C.c_double)),
-                ("amplitude", C.c_double)]
+                ("amplitude", C.c_double), ("n_patches", C.c_int), ("degrees", C.POINTER(C.c_int)),
+                ("n_ctrl", C.POINTER(C.c_int)), ("knots", C.POINTER(C.c_double)),
+                ("ctrl", C.POINTER(C.c_double))]
 
 
 class Opts(C.Structure):
@@ -189,7 +191,10 @@ def bembel_solve_opts_default() -> SolveOpts:
     return o
 
 
-def bembel_geom_create(kind: int = BEMBEL_GEOM_SPHERE6, coeffs=None, amplitude: float = 0.1) -> Geometry:
+def bembel_geom_create(kind: int = BEMBEL_GEOM_SPHERE6, coeffs=None, amplitude: float = 0.1,
+                       patches=None) -> Geometry:
+    """patches (NURBS): six dicts with "degrees" (p1, p2), "knots" (s knots, t knots) and
+    "ctrl" of shape (k2, k1, 4) = (x, y, z, weight) indexed [i2, i1]."""
     d = GeomDesc()
     d.kind = kind
     keep = None
@@ -198,6 +203,18 @@ def bembel_geom_create(kind: int = BEMBEL_GEOM_SPHERE6, coeffs=None, amplitude: 
         d.n_coeffs = keep.size
         d.coeffs = keep.ctypes.data_as(C.POINTER(C.c_double))
     d.amplitude = amplitude
+    if patches is not None:
+        deg = np.ascontiguousarray([v for pt in patches for v in pt["degrees"]], dtype=np.int32)
+        nct = np.ascontiguousarray([v for pt in patches for v in (np.shape(pt["ctrl"])[1], np.shape(pt["ctrl"])[0])],
+                                   dtype=np.int32)
+        kn = np.ascontiguousarray(np.concatenate([np.concatenate(pt["knots"]) for pt in patches]), dtype=np.float64)
+        cp = np.ascontiguousarray(np.concatenate([np.asarray(pt["ctrl"], dtype=np.float64).ravel() for pt in patches]))
+        keep = (keep, deg, nct, kn, cp)
+        d.n_patches = len(patches)
+        d.degrees = deg.ctypes.data_as(C.POINTER(C.c_int))
+        d.n_ctrl = nct.ctypes.data_as(C.POINTER(C.c_int))
+        d.knots = kn.ctypes.data_as(C.POINTER(C.c_double))
+        d.ctrl = cp.ctypes.data_as(C.POINTER(C.c_double))
     h = C.c_void_p()
     _check(lib().bembel_geom_create(C.byref(d), C.byref(h)))
     return Geometry(h)

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <stdexcept>
 
@@ -194,6 +195,44 @@ int bembel_geom_create(const bembel_geom_desc* desc, bembel_geom** out) {
           if (m != 0) nlm *= std::sqrt(2.0);
           g->g.w[idx] = desc->amplitude * desc->coeffs[idx] * nlm;
         }
+    } else if (desc->kind == BEMBEL_GEOM_NURBS) {
+      std::unique_ptr<GeomHandle> own(g);
+      if (desc->n_patches != 6 || !desc->degrees || !desc->n_ctrl || !desc->knots || !desc->ctrl)
+        fail(BEMBEL_EINVAL, "geom_create: NURBS needs 6 patches with degrees, control-net sizes, knots and points");
+      std::vector<double>& buf = g->nurbs;
+      buf.assign(6, 0.0);
+      const double* kn = desc->knots;
+      const double* cp = desc->ctrl;
+      for (int P = 0; P < 6; ++P) {
+        const int p1 = desc->degrees[2 * P], p2 = desc->degrees[2 * P + 1];
+        const int k1 = desc->n_ctrl[2 * P], k2 = desc->n_ctrl[2 * P + 1];
+        if (p1 < 1 || p2 < 1 || p1 > kMaxNurbsDeg || p2 > kMaxNurbsDeg || k1 < p1 + 1 || k2 < p2 + 1 || k1 > 4096 ||
+            k2 > 4096)
+          fail(BEMBEL_EINVAL, "geom_create: NURBS degrees must be in [1, 4] with at least degree + 1 points");
+        buf[P] = double(buf.size());
+        buf.insert(buf.end(), {double(p1), double(p2), double(k1), double(k2)});
+        for (int dir = 0; dir < 2; ++dir) {
+          const int p = dir ? p2 : p1, k = dir ? k2 : k1, n = k + p + 1;
+          for (int i = 0; i < n; ++i) {
+            if (i > 0 && kn[i] < kn[i - 1]) fail(BEMBEL_EINVAL, "geom_create: NURBS knots must not decrease");
+            if ((i <= p && kn[i] != 0.0) || (i >= k && kn[i] != 1.0))
+              fail(BEMBEL_EINVAL, "geom_create: NURBS knot vectors must be open on [0, 1]");
+          }
+          buf.insert(buf.end(), kn, kn + n);
+          kn += n;
+        }
+        for (int i = 0; i < k1 * k2; ++i)
+          if (!(cp[4 * i + 3] > 0.0)) fail(BEMBEL_EINVAL, "geom_create: NURBS weights must be positive");
+        buf.insert(buf.end(), cp, cp + 4 * k1 * k2);
+        cp += 4 * k1 * k2;
+      }
+      cuda_check(cudaMalloc(&g->nurbs_dev, sizeof(double) * buf.size()), "nurbs alloc");
+      cuda_check(cudaMemcpy(g->nurbs_dev, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice),
+                 "nurbs upload");
+      g->g.kind = kNurbs;
+      g->g.nurbs_host = buf.data();
+      g->g.nurbs_dev = g->nurbs_dev;
+      own.release();
     } else {
       delete g;
       fail(BEMBEL_EINVAL, "geom_create: unknown geometry kind");

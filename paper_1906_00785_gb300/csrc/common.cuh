@@ -25,12 +25,71 @@ constexpr int kMaxBatch = 64;                                        // meshes p
 // ---------------------------------------------------------------------------
 // Geometry
 // ---------------------------------------------------------------------------
-enum GeomKind { kSphere6 = 0, kPerturbedSphere = 1 };
+enum GeomKind { kSphere6 = 0, kPerturbedSphere = 1, kNurbs = 2 };
+constexpr int kMaxNurbsDeg = 4;
 
 struct Geom {
   int kind;
   double w[24];  // amp * a_lm * N_l|m| for the perturbed sphere (see sph_sum)
+  // NURBS patches: one buffer, host and device copies (owned by the geometry
+  // handle).  doubles [0..5]: offset of patch P's record; record: p1, p2, k1,
+  // k2, the k1 + p1 + 1 knots in s, the k2 + p2 + 1 knots in t, then k1 k2
+  // control points (x, y, z, weight), index i1 + k1 i2.
+  const double* nurbs_host;
+  const double* nurbs_dev;
 };
+
+// The p + 1 B-splines of degree p (open knot vector kn of n = k + p + 1 knots)
+// that are non-zero at x, by the two-term recursion of App. C restricted to the
+// knot span holding x (x = 1 in the last non-empty span): T[j][r] holds the
+// degree-j function with index span - j + r.  Returns the index of the first.
+BEMBEL_HD int nurbs_basis(const double* kn, int k, int p, double x, double* N) {
+  int span = p;  // kn[span] <= x < kn[span + 1]
+  while (span < k - 1 && x >= kn[span + 1]) ++span;
+  double T[kMaxNurbsDeg + 1][kMaxNurbsDeg + 1];
+  T[0][0] = 1.0;
+  for (int j = 1; j <= p; ++j)
+    for (int r = 0; r <= j; ++r) {
+      const int i = span - j + r;
+      double v = 0.0;
+      if (r >= 1) {  // (x - kn_i) / (kn_{i+j} - kn_i) B_{i, j-1}
+        const double den = kn[i + j] - kn[i];
+        if (den > 0.0) v += (x - kn[i]) / den * T[j - 1][r - 1];
+      }
+      if (r <= j - 1) {  // (kn_{i+j+1} - x) / (kn_{i+j+1} - kn_{i+1}) B_{i+1, j-1}
+        const double den = kn[i + j + 1] - kn[i + 1];
+        if (den > 0.0) v += (kn[i + j + 1] - x) / den * T[j - 1][r];
+      }
+      T[j][r] = v;
+    }
+  for (int r = 0; r <= p; ++r) N[r] = T[p][r];
+  return span - p;
+}
+
+// Rational tensor-product patch: x = sum N_a(s) N_b(t) w_ab P_ab / sum N_a N_b w_ab.
+BEMBEL_HD void nurbs_eval(const double* buf, int patch, double s, double t, double x[3]) {
+  const double* r = buf + (long long)buf[patch];
+  const int p1 = int(r[0]), p2 = int(r[1]), k1 = int(r[2]), k2 = int(r[3]);
+  const double* kn1 = r + 4;
+  const double* kn2 = kn1 + k1 + p1 + 1;
+  const double* cp = kn2 + k2 + p2 + 1;
+  double N1[kMaxNurbsDeg + 1], N2[kMaxNurbsDeg + 1];
+  const int a0 = nurbs_basis(kn1, k1, p1, s, N1);
+  const int b0 = nurbs_basis(kn2, k2, p2, t, N2);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b <= p2; ++b)
+    for (int a = 0; a <= p1; ++a) {
+      const double* P = cp + 4 * ((long long)(a0 + a) + (long long)k1 * (b0 + b));
+      const double c = N1[a] * N2[b] * P[3];
+      acc[0] += c * P[0];
+      acc[1] += c * P[1];
+      acc[2] += c * P[2];
+      acc[3] += c;
+    }
+  x[0] = acc[0] / acc[3];
+  x[1] = acc[1] / acc[3];
+  x[2] = acc[2] / acc[3];
+}
 
 // Cube face of patch p: c(s,t) = o + (2s-1) e1 + (2t-1) e2 with e1 x e2 = o.
 // Patch order +x, -x, +y, -y, +z, -z.  Each axis vector is +-1 on a single
@@ -84,6 +143,14 @@ BEMBEL_HD double sph_sum(const double* w, double x, double y, double z) {
 
 // gamma_p(s, t) in FP64.
 BEMBEL_HD void gamma_eval(const Geom& g, int p, double s, double t, double x[3]) {
+  if (g.kind == kNurbs) {
+#ifdef __CUDA_ARCH__
+    nurbs_eval(g.nurbs_dev, p, s, t, x);
+#else
+    nurbs_eval(g.nurbs_host, p, s, t, x);
+#endif
+    return;
+  }
   double c[3];
   cube_point(p, s, t, c);
   const double n2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];

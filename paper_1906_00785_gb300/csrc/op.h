@@ -124,6 +124,11 @@ struct Op {
 
 struct GeomHandle {
   Geom g;
+  std::vector<double> nurbs;  // host copy of the NURBS buffer (g.nurbs_host points here)
+  double* nurbs_dev = nullptr;
+  ~GeomHandle() {
+    if (nurbs_dev) cudaFree(nurbs_dev);
+  }
 };
 
 // setup.cu
