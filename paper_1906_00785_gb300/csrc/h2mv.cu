@@ -671,6 +671,7 @@ size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32) {
 
 void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s) {
   ensure_scratch(const_cast<Op&>(o), matvec_scratch_bytes(o, nrhs, fp32));
+  if (fp32) tc_prepare(const_cast<Op&>(o), nrhs);
   if (fp32) {
     if (!o.d_N32) fail(BEMBEL_EINVAL, "FP32 matvec needs an operator assembled with precision MIXED");
     matvec_impl<float>(o, static_cast<const float*>(x), static_cast<float*>(y), nrhs, s, o.d_K32, o.d_N32, o.d_V32,

@@ -170,7 +170,9 @@ void local_gather(const Op& o, const void* x, void* xl, int nrhs, bool fp32, cud
 void local_scatter(const Op& o, const void* yl, void* y, int nrhs, bool fp32, cudaStream_t s);
 void blockdiag_apply(const Op& o, const void* Dinv, const void* xl, void* yl, int nrhs, bool fp32, cudaStream_t s);
 // tc_coupling.cu
-bool tc_coupling_usable(const Op& o, int nrhs);
+bool tc_coupling_usable(const Op& o, int nrhs);  // groups built and the product wide enough
+bool tc_coupling_wanted(const Op& o, int nrhs);  // operator and width qualify
+void tc_prepare(Op& o, int nrhs);                // build the groups if wanted (never under capture)
 void tc_coupling(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s);
 void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vector<int>& fsrc);
 double tc_selftest(int N);

@@ -285,6 +285,40 @@ struct Ball {
   double r;
 };
 
+struct LevelTable {
+  long long off[16];  // first cluster id of each level, then the total
+};
+
+// Bounding ball of each cluster: centre gamma(square midpoint), radius the
+// largest distance to gamma on a 9 x 9 grid of the cluster square (corners
+// included).  Output: (c0, c1, c2, r) per cluster.
+__global__ void k_cluster_balls(Geom g, LevelTable lt, int64_t n, double* __restrict__ out) {
+  const int64_t gc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gc >= n) return;
+  int l = 0;
+  while (gc >= lt.off[l + 1]) ++l;
+  const int64_t nper = int64_t(1) << (2 * l);
+  const int64_t c = gc - lt.off[l];
+  const double H = ldexp(1.0, -l);
+  const int patch = int(c / nper);
+  uint32_t j1, j2;
+  morton_decode(uint32_t(c % nper), j1, j2);
+  double ctr[3];
+  gamma_eval(g, patch, (j1 + 0.5) * H, (j2 + 0.5) * H, ctr);
+  double r = 0.0;
+  for (int k2 = 0; k2 <= 8; ++k2)
+    for (int k1 = 0; k1 <= 8; ++k1) {
+      double x[3];
+      gamma_eval(g, patch, (j1 + k1 / 8.0) * H, (j2 + k2 / 8.0) * H, x);
+      const double dx = x[0] - ctr[0], dy = x[1] - ctr[1], dz = x[2] - ctr[2];
+      r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+  out[gc * 4 + 0] = ctr[0];
+  out[gc * 4 + 1] = ctr[1];
+  out[gc * 4 + 2] = ctr[2];
+  out[gc * 4 + 3] = r;
+}
+
 struct KeyHash {
   size_t operator()(const std::array<long long, 3>& k) const {
     return std::hash<long long>()(k[0] * 73856093LL ^ k[1] * 19349663LL ^ k[2] * 83492791LL);
@@ -456,32 +490,16 @@ void build_structure(Op& o) {
   for (int l = 0; l <= o.leaf; ++l) o.lvl_off[l + 1] = o.lvl_off[l] + 6 * (int64_t(1) << (2 * l));
   o.nclusters = o.lvl_off[o.leaf + 1];
   std::vector<Ball> balls(o.nclusters);
-  std::vector<int> clevel(o.nclusters);
-  for (int l = 0; l <= o.leaf; ++l)
-    for (int64_t c = o.lvl_off[l]; c < o.lvl_off[l + 1]; ++c) clevel[c] = l;
-  parallel_for(o.nclusters, [&](int64_t c0, int64_t c1) {
-    for (int64_t gc = c0; gc < c1; ++gc) {
-      const int l = clevel[gc];
-      const int64_t nper = int64_t(1) << (2 * l);
-      const int64_t c = gc - o.lvl_off[l];
-      const double H = std::ldexp(1.0, -l);
-      const int patch = int(c / nper);
-      uint32_t j1, j2;
-      morton_decode(uint32_t(c % nper), j1, j2);
-      Ball bl;
-      gamma_eval(o.geom, patch, (j1 + 0.5) * H, (j2 + 0.5) * H, bl.c);
-      double r = 0.0;
-      for (int k2 = 0; k2 <= 8; ++k2)
-        for (int k1 = 0; k1 <= 8; ++k1) {
-          double x[3];
-          gamma_eval(o.geom, patch, (j1 + k1 / 8.0) * H, (j2 + k2 / 8.0) * H, x);
-          const double dx = x[0] - bl.c[0], dy = x[1] - bl.c[1], dz = x[2] - bl.c[2];
-          r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz));
-        }
-      bl.r = r;
-      balls[gc] = bl;
-    }
-  });
+  if (o.q > 0) {  // only the admissibility test uses them
+    static_assert(sizeof(Ball) == 4 * sizeof(double), "Ball is four doubles");
+    if (o.leaf > 14) fail(BEMBEL_EINVAL, "assemble: leaf level above 14");
+    LevelTable lt{};
+    for (int l = 0; l <= o.leaf + 1; ++l) lt.off[l] = o.lvl_off[l];
+    DevBuf db(sizeof(Ball) * o.nclusters);
+    k_cluster_balls<<<int((o.nclusters + 127) / 128), 128>>>(o.geom, lt, o.nclusters, static_cast<double*>(db.p));
+    launched("k_cluster_balls");
+    cuda_check(cudaMemcpy(balls.data(), db.p, sizeof(Ball) * o.nclusters, cudaMemcpyDeviceToHost), "balls");
+  }
 
   debug_mark("setup: block tree");
   // ---- block tree, level by level ------------------------------------------------
@@ -568,8 +586,6 @@ void build_structure(Op& o) {
   }
   o.d_near_ptr = upload(nptr);
   o.d_near_col = upload(ncol);
-  debug_mark("setup: tensor-core groups");
-  if (o.opts.precision == BEMBEL_PREC_MIXED && o.q == 4 && o.opts.tensor_cores) tc_build_groups(o, fptr, fsrc);
   {
     std::vector<int> diag(o.nleaf, -1), ids(o.nleaf), ntgt(o.nnear);
     for (int64_t t = 0; t < o.nleaf; ++t) {

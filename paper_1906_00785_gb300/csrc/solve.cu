@@ -101,58 +101,80 @@ __global__ void k_dots(const T* __restrict__ V, int64_t vstride, const int* __re
   }
 }
 
-// h[i][r] += sum_n conj(V_i[n, r]) w[n, r] for i < *dj + 1: grid (blocks along n,
-// nrhs); each thread reads w once per group of 8 basis vectors, sums are
-// reduced per block and added atomically (h cleared before the launch).
+// h[i][r] += sum_n conj(V_i[n, r]) w[n, r] for i < *dj + 1.  Grid (blocks
+// along n, nrhs, groups of 8 basis vectors): every group runs at once; each
+// thread reads w once per group, sums are reduced per block and added
+// atomically (h cleared before the launch).  Groups at or beyond *dj + 1 exit.
 template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256) k_mdots(const T* __restrict__ V, int64_t vstride, const int* __restrict__ dj,
                                                const T* __restrict__ w, int64_t n, int nrhs, cd_t* __restrict__ h) {
   constexpr int G = 8;
   const int r = blockIdx.y;
   const int nv = *dj + 1;
+  const int i0 = blockIdx.z * G;
+  if (i0 >= nv) return;
   const int C = CPLX ? 2 : 1;
   __shared__ double red[G][2][8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i0 = 0; i0 < nv; i0 += G) {
-    double sr[G], si[G];
+  double sr[G], si[G];
 #pragma unroll
-    for (int g = 0; g < G; ++g) sr[g] = si[g] = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-      const T* wk = w + ((int64_t)r * n + k) * C;
-      const double wr = wk[0], wi = CPLX ? (double)wk[1] : 0.0;
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        if (i0 + g < nv) {
-          const T* v = V + (int64_t)(i0 + g) * vstride + ((int64_t)r * n + k) * C;
-          const double vr = v[0], vi = CPLX ? (double)v[1] : 0.0;
-          sr[g] += vr * wr + vi * wi;
-          if (CPLX) si[g] += vr * wi - vi * wr;
-        }
-      }
-    }
+  for (int g = 0; g < G; ++g) sr[g] = si[g] = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const T* wk = w + ((int64_t)r * n + k) * C;
+    const double wr = wk[0], wi = CPLX ? (double)wk[1] : 0.0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      for (int o = 16; o > 0; o >>= 1) {
-        sr[g] += __shfl_xor_sync(0xffffffffu, sr[g], o);
-        if (CPLX) si[g] += __shfl_xor_sync(0xffffffffu, si[g], o);
-      }
-      if (lane == 0) {
-        red[g][0][warp] = sr[g];
-        red[g][1][warp] = si[g];
+      if (i0 + g < nv) {
+        const T* v = V + (int64_t)(i0 + g) * vstride + ((int64_t)r * n + k) * C;
+        const double vr = v[0], vi = CPLX ? (double)v[1] : 0.0;
+        sr[g] += vr * wr + vi * wi;
+        if (CPLX) si[g] += vr * wi - vi * wr;
       }
     }
-    __syncthreads();
-    if (threadIdx.x < G && i0 + (int)threadIdx.x < nv) {
-      double a = 0.0, b = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        a += red[threadIdx.x][0][k];
-        b += red[threadIdx.x][1][k];
-      }
-      cd_t* hp = h + (i0 + threadIdx.x) * nrhs + r;
-      atomicAdd(&hp->r, a);
-      if (CPLX) atomicAdd(&hp->i, b);
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    for (int o = 16; o > 0; o >>= 1) {
+      sr[g] += __shfl_xor_sync(0xffffffffu, sr[g], o);
+      if (CPLX) si[g] += __shfl_xor_sync(0xffffffffu, si[g], o);
     }
-    __syncthreads();
+    if (lane == 0) {
+      red[g][0][warp] = sr[g];
+      red[g][1][warp] = si[g];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < G && i0 + (int)threadIdx.x < nv) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[threadIdx.x][0][k];
+      b += red[threadIdx.x][1][k];
+    }
+    cd_t* hp = h + (i0 + threadIdx.x) * nrhs + r;
+    atomicAdd(&hp->r, a);
+    if (CPLX) atomicAdd(&hp->i, b);
+  }
+}
+
+// hn[r].r += sum_n |w[n, r]|^2: grid (blocks along n, nrhs), block sums added
+// atomically (hn cleared before the launch).
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256) k_norm2(const T* __restrict__ w, int64_t n, cd_t* __restrict__ hn) {
+  const int r = blockIdx.y;
+  const int C = CPLX ? 2 : 1;
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n * C; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[(int64_t)r * n * C + k];
+    s += v * v;
+  }
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += red[k];
+    atomicAdd(&hn[r].r, a);
   }
 }
 
@@ -394,6 +416,7 @@ int gmres_run(const Op& o, const double* b, double* x, int nrhs, double tol, int
   const int tb = 256;
   // FP64 bytes cover the FP32 products too; reserved before the graphs capture the address
   ensure_scratch(const_cast<Op&>(o), matvec_scratch_bytes(o, nrhs, false));
+  if (fp32) tc_prepare(const_cast<Op&>(o), nrhs);  // tensor-core groups, if used, before capture
   DevBuf Vbuf(sizeof(T) * vstride * (m + 1)), wbuf(sizeof(T) * vstride), zbuf(sizeof(T) * vstride),
       rbuf(sizeof(double) * vstride), ubuf(sizeof(double) * vstride);
   T* V = static_cast<T*>(Vbuf.p);
@@ -445,7 +468,9 @@ int gmres_run(const Op& o, const double* b, double* x, int nrhs, double tol, int
     }
   } eg{exec};
   long long kernels_per_step = 0;
-  const int dots_blocks = int(std::max<int64_t>(1, std::min<int64_t>(64, (n + 1023) / 1024)));
+  // blocks along n for the reductions: about two elements per thread
+  const int dots_blocks = int(std::max<int64_t>(1, std::min<int64_t>(256, (n * C + 511) / 512)));
+  const int groups = (m + 1 + 7) / 8;
   for (int c = 0; c < 2; ++c) {
     cudaGraph_t graph;
     capture_begin(s);
@@ -455,16 +480,17 @@ int gmres_run(const Op& o, const double* b, double* x, int nrhs, double tol, int
     matvec_device(o, prec ? static_cast<const void*>(z) : static_cast<const void*>(w), prec ? w : z, nrhs, fp32, s);
     T* av = prec ? w : z;  // A v_j (or A M^-1 v_j)
     cuda_check(cudaMemsetAsync(st.h1, 0, sizeof(cd_t) * 2 * (m + 1) * nrhs, s), "h clear");  // h1 and h2
-    k_mdots<T, CPLX><<<dim3(dots_blocks, nrhs), 256, 0, s>>>(V, vstride, st.j, av, n, nrhs, st.h1);
+    k_mdots<T, CPLX><<<dim3(dots_blocks, nrhs, groups), 256, 0, s>>>(V, vstride, st.j, av, n, nrhs, st.h1);
     launched("k_mdots");
     k_orth<T, CPLX><<<nblk(n * nrhs, tb), tb, 0, s>>>(V, vstride, st.j, av, n, nrhs, st.h1);
     launched("k_orth");
-    k_mdots<T, CPLX><<<dim3(dots_blocks, nrhs), 256, 0, s>>>(V, vstride, st.j, av, n, nrhs, st.h2);
+    k_mdots<T, CPLX><<<dim3(dots_blocks, nrhs, groups), 256, 0, s>>>(V, vstride, st.j, av, n, nrhs, st.h2);
     launched("k_mdots");
     k_orth<T, CPLX><<<nblk(n * nrhs, tb), tb, 0, s>>>(V, vstride, st.j, av, n, nrhs, st.h2);
     launched("k_orth");
-    k_dots<T, CPLX><<<nrhs, 256, 0, s>>>(av, 0, nullptr, 1, av, n, nrhs, st.hn);
-    launched("k_dots");
+    cuda_check(cudaMemsetAsync(st.hn, 0, sizeof(cd_t) * nrhs, s), "hn clear");
+    k_norm2<T, CPLX><<<dim3(dots_blocks, nrhs), 256, 0, s>>>(av, n, st.hn);
+    launched("k_norm2");
     k_givens<<<nrhs, 32, sizeof(cd_t) * (3 * m + 1), s>>>(st, tol, st.ctr);
     launched("k_givens");
     k_scale_next<T><<<nblk(vstride, tb), tb, 0, s>>>(av, V, vstride, st.j, n * C, nrhs, st.alpha, m);

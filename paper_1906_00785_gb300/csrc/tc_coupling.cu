@@ -364,12 +364,28 @@ __global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restric
 
 }  // namespace
 
-bool tc_coupling_usable(const Op& o, int nrhs) {
+bool tc_coupling_wanted(const Op& o, int nrhs) {
   const int ncol = nrhs * (o.cplx ? 2 : 1);
   // below these widths the CUDA-core product is as fast (measured on the
   // level-6 sphere: real 32 columns 1.4x, complex 64 columns 1.15x faster here)
   const int min_cols = o.cplx ? 64 : 32;
-  return o.d_tc_gptr != nullptr && o.q2 == 16 && ncol >= min_cols && ncol <= 256 && ncol % 16 == 0;
+  return o.opts.precision == BEMBEL_PREC_MIXED && o.opts.tensor_cores && o.q2 == 16 && !o.efie && o.nfar > 0 &&
+         ncol >= min_cols && ncol <= 256 && ncol % 16 == 0;
+}
+
+bool tc_coupling_usable(const Op& o, int nrhs) { return o.d_tc_gptr != nullptr && tc_coupling_wanted(o, nrhs); }
+
+// Sibling groups are built on first use (from the far lists on the device), not
+// during assembly: most operators never see a wide enough product.
+void tc_prepare(Op& o, int nrhs) {
+  if (o.d_tc_gptr || !tc_coupling_wanted(o, nrhs) || capturing()) return;
+  std::vector<long long> fptr(o.nclusters + 1);
+  std::vector<int> fsrc(o.nfar);
+  cuda_check(cudaStreamSynchronize(o.stream), "tc groups sync");
+  cuda_check(cudaMemcpy(fptr.data(), o.d_far_ptr, sizeof(long long) * fptr.size(), cudaMemcpyDeviceToHost),
+             "far ptr");
+  cuda_check(cudaMemcpy(fsrc.data(), o.d_far_src, sizeof(int) * fsrc.size(), cudaMemcpyDeviceToHost), "far src");
+  tc_build_groups(o, fptr, fsrc);
 }
 
 // CTAs per SM that the TMEM accumulators allow (512 columns per SM), and the
