@@ -227,8 +227,11 @@ int bembel_geom_destroy(bembel_geom* g);
  * i1 + np j2 (i1 < np = 2^L+p, j2 < np-1), then the second component
  * np (np-1) + j1 + (np-1) i2; a function glued to one numbered earlier shares
  * its number, with sign -s_own s_partner (s = +1 on the sides s = 1, t = 1,
- * -1 on s = 0, t = 0).  This release assembles the EFIE densely (q = 0) on the
- * cube-face sphere; bembel_eval returns the scattered field (MS) at the points,
+ * -1 on s = 0, t = 0).  The EFIE is available on the cube-face sphere, dense
+ * (q = 0) or H^2-compressed (q > 0, FP64: the kernel times the Jacobian dot
+ * products and G itself are interpolated per far block, the three moment
+ * channels int phi^1 L_a, int phi^2 L_a, int div phi L_a run through the same
+ * nested transfers); bembel_eval returns the scattered field (MS) at the points,
  * 3 complex values per point (out: [rhs][point][3] interleaved complex).
  * bembel_autotune, bembel_assemble_batch and the learned preconditioner are
  * for the scalar operators only (EUNSUPPORTED). */
@@ -245,7 +248,8 @@ int bembel_geom_destroy(bembel_geom* g);
  * runs the tabulation, near-field (regular + singular) quadrature and
  * coupling kernels.  The geometry must outlive the operator.
  * Errors: EINVAL (bad sizes, 0 <= level <= 10 required, EFIE with k = 0 or
- * p = 0), EUNSUPPORTED (EFIE with q > 0 or on another geometry), ENOMEM, ECUDA. */
+ * p = 0), EUNSUPPORTED (EFIE with q > 0 and MIXED, or on another geometry),
+ * ENOMEM, ECUDA. */
 int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q,
                     const bembel_opts* o, bembel_op** out);
 

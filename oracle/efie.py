@@ -115,3 +115,97 @@ def efie_field(space, rho: np.ndarray, pts: np.ndarray, kappa: complex, g: int =
         gradG = (G * (-1j * kappa - 1.0 / r) / r)[..., None] * d
         E += np.einsum("pk,kc->pc", G, jv) + np.einsum("pkc,k->pc", gradG, dv) / kappa**2
     return E
+
+
+class EfieH2Oracle:
+    """Dense reconstruction of the H^2-compressed EFIE (test infrastructure).
+
+    Same block tree, Chebyshev nodes and Lagrange polynomials as ``oracle.h2``.
+    On a far block (tau, sigma) the kernel is interpolated on the parameter
+    squares with the Jacobian factors kept inside the interpolated functions:
+      G(x,y) d_alpha gamma(s) . d_beta gamma(t) ~ sum_ab L_a(s) K^{ab}_{alpha beta} L_b(t),
+      K^{ab}_{alpha beta} = G(x_a, y_b) d_alpha gamma(x_a) . d_beta gamma(y_b),
+      G(x,y) ~ sum_ab L_a(s) G(x_a, y_b) L_b(t),
+    so the Galerkin block of elements e in tau, f in sigma is
+      sum_{alpha beta} M^alpha_e K_{alpha beta} (M^beta_f)^T - kappa^-2 M^div_e K (M^div_f)^T
+    with the geometry-independent moments M^alpha_e[i, a] = int_e phi_hat_i^alpha L_a ds and
+    M^div_e[i, a] = int_e div phi_hat_i L_a ds (parameter measure), integrated
+    directly on every cluster (no nested transfers).  Near blocks: EfieAssembler."""
+
+    def __init__(self, space, kappa, q=4, eta=1.6, leaf_level=None, g_reg=4, g_sing=5):
+        from .h2 import block_tree, chebyshev_nodes01
+
+        self.space, self.kappa, self.q = space, complex(kappa), q
+        self.leaf = max(0, space.level - 1) if leaf_level is None else leaf_level
+        self.asm = EfieAssembler(space, kappa, g_reg, g_sing)
+        self.far, self.near, _ = block_tree(space.geom, self.leaf, eta)
+        self.nodes = chebyshev_nodes01(q)
+        self._mom: dict = {}
+        self._pair: dict = {}
+
+    def cluster_nodes(self, c):
+        patch, lev, i1, i2 = c
+        H = 2.0 ** -lev
+        X1, X2 = np.meshgrid((i1 + self.nodes) * H, (i2 + self.nodes) * H, indexing="xy")
+        return np.stack([X1.ravel(), X2.ravel()], 1)
+
+    def couplings(self, t, s):
+        """(K_{alpha beta} for alpha, beta in {1, 2} as a (2, 2, q^2, q^2) array, K_div = G)."""
+        sp = self.space
+        st, ss = self.cluster_nodes(t), self.cluster_nodes(s)
+        xt, xs = sp.geom.eval(t[0], st), sp.geom.eval(s[0], ss)
+        Jt, Js = sp.geom.jacobian(t[0], st), sp.geom.jacobian(s[0], ss)
+        G = green_h(self.kappa, xt[:, None, :], xs[None, :, :])
+        K = np.einsum("ab,acx,bcy->xyab", G, Jt, Js)
+        return K, G
+
+    def moments(self, e, c):
+        """(M^1, M^2, M^div) of element e on cluster c, each (nloc, q^2)."""
+        key = (e, c)
+        if key not in self._mom:
+            from .h2 import lagrange
+
+            sp = self.space
+            pts, w = tensor2(sp.p + self.q)
+            st = sp.to_patch(e, pts)
+            H = 2.0 ** -c[1]
+            l1 = lagrange(self.nodes, st[:, 0] / H - c[2])
+            l2 = lagrange(self.nodes, st[:, 1] / H - c[3])
+            L = np.einsum("pa,pb->pba", l1, l2).reshape(len(w), -1)
+            V, D = sp.element_basis(e, pts)
+            wt = (w * sp.h**2)[:, None]
+            self._mom[key] = ((V[:, :, 0] * wt).T @ L, (V[:, :, 1] * wt).T @ L, (D * wt).T @ L)
+        return self._mom[key]
+
+    def pair(self, e, f):
+        if e <= f:
+            if (e, f) not in self._pair:
+                self._pair[(e, f)] = self.asm.pair_block(e, f)
+            return self._pair[(e, f)]
+        return self.pair(f, e).T
+
+    def dense(self):
+        from .h2 import cluster_elements
+
+        sp = self.space
+        A = np.zeros((sp.ndofs, sp.ndofs), dtype=complex)
+        dofs = [sp.element_dofs(e) for e in range(sp.nelem)]
+
+        def add(e, f, blk):
+            ge, ce = dofs[e]
+            gf, cf = dofs[f]
+            np.add.at(A, (ge[:, None], gf[None, :]), blk * np.outer(ce, cf))
+
+        for t, s in self.near:
+            for e in cluster_elements(sp, t):
+                for f in cluster_elements(sp, s):
+                    add(e, f, self.pair(e, f))
+        for t, s in self.far:
+            K, G = self.couplings(t, s)
+            for e in cluster_elements(sp, t):
+                Me = self.moments(e, t)
+                for f in cluster_elements(sp, s):
+                    Mf = self.moments(f, s)
+                    blk = sum(Me[a] @ K[a, b] @ Mf[b].T for a in range(2) for b in range(2))
+                    add(e, f, blk - (Me[2] @ G @ Mf[2].T) / self.kappa**2)
+        return A

@@ -113,6 +113,9 @@ class S1Space:
         i2, i1 = divmod(r, self.n_el)
         return patch, i1, i2
 
+    def element_index(self, patch: int, i1: int, i2: int) -> int:
+        return patch * self.n_el**2 + i2 * self.n_el + i1
+
     def to_patch(self, e: int, st_local: np.ndarray) -> np.ndarray:
         _, i1, i2 = self.element(e)
         return (np.array([i1, i2], dtype=float) + np.asarray(st_local, dtype=float)) * self.h

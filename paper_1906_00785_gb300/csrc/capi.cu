@@ -47,7 +47,7 @@ void free_op(Op* o) {
   if (!o) return;
   void* ptrs[] = {o->d_far_ptr, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
-                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_BW_far,   o->d_nodes, o->d_scratch, o->d_bj,
+                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_BW_far, o->d_nodes_jac,   o->d_nodes, o->d_scratch, o->d_bj,
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
                   o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
                   o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val};
@@ -255,7 +255,8 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
     fail(BEMBEL_EINVAL, "assemble: unknown operator");
   if (op == BEMBEL_MAXWELL_SL) {
     if (p < 1 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: the EFIE needs the S^1 degree p in [1, 2]");
-    if (q != 0) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE is assembled densely (q = 0)");
+    if (q != 0 && o && o->precision == BEMBEL_PREC_MIXED)
+      fail(BEMBEL_EUNSUPPORTED, "assemble: the compressed EFIE (q > 0) is FP64 only");
     if (reinterpret_cast<GeomHandle*>(g)->g.kind != BEMBEL_GEOM_SPHERE6)
       fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE is available on the cube-face sphere");
     if (k_re == 0.0 && k_im == 0.0) fail(BEMBEL_EINVAL, "assemble: the EFIE needs a nonzero wavenumber");

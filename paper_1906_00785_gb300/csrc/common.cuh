@@ -141,6 +141,31 @@ BEMBEL_HD double sph_sum(const double* w, double x, double y, double z) {
   return r;
 }
 
+// gamma and its parameter derivatives on the cube-face sphere: gamma = c / |c|,
+// d gamma = (dc - gamma (gamma . dc)) / |c| with dc/ds, dc/dt constant per patch.
+BEMBEL_HD void sphere6_jac(int patch, double s, double t, double x[3], double ds[3], double dt[3]) {
+  double c[3], c00[3], c10[3], c01[3];
+  cube_point(patch, s, t, c);
+  cube_point(patch, 0.0, 0.0, c00);
+  cube_point(patch, 1.0, 0.0, c10);
+  cube_point(patch, 0.0, 1.0, c01);
+#ifdef __CUDA_ARCH__
+  const double inv = rsqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+#else
+  const double inv = 1.0 / std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+#endif
+  double gs = 0.0, gt = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    x[k] = c[k] * inv;
+    gs += x[k] * (c10[k] - c00[k]);
+    gt += x[k] * (c01[k] - c00[k]);
+  }
+  for (int k = 0; k < 3; ++k) {
+    ds[k] = ((c10[k] - c00[k]) - x[k] * gs) * inv;
+    dt[k] = ((c01[k] - c00[k]) - x[k] * gt) * inv;
+  }
+}
+
 // gamma_p(s, t) in FP64.
 BEMBEL_HD void gamma_eval(const Geom& g, int p, double s, double t, double x[3]) {
   if (g.kind == kNurbs) {

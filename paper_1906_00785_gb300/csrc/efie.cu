@@ -32,28 +32,6 @@ namespace {
 
 constexpr int kEfieWarps = 4;
 
-// gamma and its parameter derivatives on the cube-face sphere: gamma = c / |c|,
-// d gamma = (dc - gamma (gamma . dc)) / |c| with dc/ds, dc/dt constant per patch.
-__device__ __forceinline__ void sphere6_jac(int patch, double s, double t, double x[3], double ds[3],
-                                            double dt[3]) {
-  double c[3], c00[3], c10[3], c01[3];
-  cube_point(patch, s, t, c);
-  cube_point(patch, 0.0, 0.0, c00);
-  cube_point(patch, 1.0, 0.0, c10);
-  cube_point(patch, 0.0, 1.0, c01);
-  const double inv = rsqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
-  double gs = 0.0, gt = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    x[k] = c[k] * inv;
-    gs += x[k] * (c10[k] - c00[k]);
-    gt += x[k] * (c01[k] - c00[k]);
-  }
-  for (int k = 0; k < 3; ++k) {
-    ds[k] = ((c10[k] - c00[k]) - x[k] * gs) * inv;
-    dt[k] = ((c01[k] - c00[k]) - x[k] * gt) * inv;
-  }
-}
-
 // Bernstein values and derivatives d/du of degree D at u
 template <int D>
 __device__ __forceinline__ void bern_d(double u, double b[D + 1], double db[D + 1]) {
@@ -395,6 +373,82 @@ int4 orders(const Op& o, int kind) {
   return make_int4(o.g_var[kind][0], o.g_var[kind][1], o.g_var[kind][2], o.g_var[kind][3]);
 }
 
+// Far-field coupling of the compressed EFIE, per far block and cluster points
+// (a, b): K[blk][c][a][b] = G(x_a, y_b) d_alpha gamma(x_a) . d_beta gamma(y_b)
+// for c = 2 alpha + beta (alpha, beta: 0 = d_s, 1 = d_t) and K[blk][4] =
+// -kappa^-2 G(x_a, y_b); complex interleaved, G with its 1/(4 pi).
+__global__ void k_efie_coupling(const int* __restrict__ tgt, const int* __restrict__ src, int64_t nfar,
+                                const double* __restrict__ nodes, const double* __restrict__ jac, int q2, double kre,
+                                double kim, double* __restrict__ K) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)q2 * q2;
+  if (id >= nfar * per) return;
+  const int64_t blk = id / per;
+  const int a = int(id % per) / q2, b = int(id % per) % q2;
+  const int64_t pa = (int64_t)tgt[blk] * q2 + a, pb = (int64_t)src[blk] * q2 + b;
+  const double* xa = nodes + pa * 3;
+  const double* xb = nodes + pb * 3;
+  const double* Ja = jac + pa * 6;
+  const double* Jb = jac + pb * 6;
+  const double d0 = xa[0] - xb[0], d1 = xa[1] - xb[1], d2 = xa[2] - xb[2];
+  double gr, gi;
+  kernel_value(true, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+  gr *= kInv4Pi;
+  gi *= kInv4Pi;
+  const double kk_r = kre * kre - kim * kim, kk_i = 2.0 * kre * kim, kk_n = kk_r * kk_r + kk_i * kk_i;
+  const double cr = -kk_r / kk_n, ci = kk_i / kk_n;  // -kappa^-2
+  double* out = K + ((blk * 5) * per + (int64_t)a * q2 + b) * 2;
+  for (int al = 0; al < 2; ++al)
+    for (int be = 0; be < 2; ++be) {
+      const double g = Ja[3 * al] * Jb[3 * be] + Ja[3 * al + 1] * Jb[3 * be + 1] + Ja[3 * al + 2] * Jb[3 * be + 2];
+      out[(2 * al + be) * per * 2] = gr * g;
+      out[(2 * al + be) * per * 2 + 1] = gi * g;
+    }
+  out[4 * per * 2] = gr * cr - gi * ci;
+  out[4 * per * 2 + 1] = gr * ci + gi * cr;
+}
+
+// yh[t][a][co ncol + 2r] = sum over far sources s of t, points b and input channels:
+// channels 0, 1 (the two components) couple through K[0..3], channel 2 (the
+// divergence) through K[4].  One thread per (target cluster, a, output channel, rhs).
+__global__ void k_efie_coupling_mv(const long long* __restrict__ fptr, const int* __restrict__ fsrc,
+                                   int64_t nclusters, const double* __restrict__ K, int q2,
+                                   const double* __restrict__ xh, double* __restrict__ yh, int nrhs) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nclusters * q2 * 3 * nrhs) return;
+  const int r = int(id % nrhs);
+  const int co = int((id / nrhs) % 3);
+  const int a = int((id / (3 * nrhs)) % q2);
+  const int64_t t = id / ((int64_t)3 * nrhs * q2);
+  const int ncol = 2 * nrhs, ncolh = 3 * ncol;
+  const int64_t per = (int64_t)q2 * q2;
+  double ar = 0.0, ai = 0.0;
+  for (long long k = fptr[t]; k < fptr[t + 1]; ++k) {
+    const int64_t sc = fsrc[k];
+    const double* Kb = K + (int64_t)k * 5 * per * 2;
+    const double* xs = xh + sc * q2 * ncolh + 2 * r;
+    for (int b = 0; b < q2; ++b) {
+      const double* xb = xs + (int64_t)b * ncolh;
+      if (co < 2) {
+        for (int ci = 0; ci < 2; ++ci) {
+          const double* kc = Kb + ((int64_t)(2 * co + ci) * per + (int64_t)a * q2 + b) * 2;
+          const double xr = xb[ci * ncol], xi = xb[ci * ncol + 1];
+          ar += kc[0] * xr - kc[1] * xi;
+          ai += kc[0] * xi + kc[1] * xr;
+        }
+      } else {
+        const double* kc = Kb + ((int64_t)4 * per + (int64_t)a * q2 + b) * 2;
+        const double xr = xb[2 * ncol], xi = xb[2 * ncol + 1];
+        ar += kc[0] * xr - kc[1] * xi;
+        ai += kc[0] * xi + kc[1] * xr;
+      }
+    }
+  }
+  double* y = yh + (t * q2 + a) * ncolh + co * ncol + 2 * r;
+  y[0] = ar;
+  y[1] = ai;
+}
+
 template <int P>
 void launch_efie_pairs(Op& o, cudaEvent_t* ev) {
   const cudaStream_t s = o.stream;
@@ -436,6 +490,21 @@ void efie_pair_kernels(Op& o, cudaEvent_t* ev) {
     launch_efie_pairs<1>(o, ev);
   else
     launch_efie_pairs<2>(o, ev);
+}
+
+void efie_coupling_assemble(Op& o) {
+  const int64_t n = o.nfar * (int64_t)o.q2 * o.q2;
+  if (n == 0) return;
+  k_efie_coupling<<<int((n + 255) / 256), 256, 0, o.stream>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes,
+                                                              o.d_nodes_jac, o.q2, o.kre, o.kim, o.d_K);
+  launched("k_efie_coupling");
+}
+
+void efie_coupling_apply(const Op& o, const double* xh, double* yh, int nrhs, cudaStream_t s) {
+  const int64_t n = o.nclusters * (int64_t)o.q2 * 3 * nrhs;
+  k_efie_coupling_mv<<<int((n + 127) / 128), 128, 0, s>>>(o.d_far_ptr, o.d_far_src, o.nclusters, o.d_K, o.q2, xh, yh,
+                                                          nrhs);
+  launched("k_efie_coupling_mv");
 }
 
 void efie_rhs_local(const Op& o, const double* gx, const double* gw, int G, const double* prm_dev, int nrhs,

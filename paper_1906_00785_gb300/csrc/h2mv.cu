@@ -146,6 +146,40 @@ void scatter_l(const Op& o, const T* yl, T* y, int ncol, int C, cudaStream_t s) 
   launched("k_scatter");
 }
 
+// Compressed EFIE, three moment channels stored as extra columns of the
+// cluster vectors: xh[leaf][a][ch ncol + col] = sum_i V[ch][i][a] xl[leaf nld + i][col]
+__global__ void k_leaf_up_ch(const double* __restrict__ xl, double* __restrict__ xh, const double* __restrict__ V,
+                             int64_t nleaf, int nld, int q2, int ncol) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nleaf * q2 * 3 * ncol) return;
+  const int col = int(id % ncol);
+  const int ch = int((id / ncol) % 3);
+  const int a = int((id / (3 * ncol)) % q2);
+  const int64_t lf = id / ((int64_t)3 * ncol * q2);
+  const double* Vc = V + (int64_t)ch * nld * q2;
+  const double* x = xl + lf * nld * ncol + col;
+  double acc = 0.0;
+  for (int i = 0; i < nld; ++i) acc += Vc[(int64_t)i * q2 + a] * x[(int64_t)i * ncol];
+  xh[(lf * q2 + a) * 3 * ncol + ch * ncol + col] = acc;
+}
+
+// yl[leaf nld + i][col] = sum_ch sum_a V[ch][i][a] yh[leaf][a][ch ncol + col]
+__global__ void k_leaf_down_ch(const double* __restrict__ yh, const double* __restrict__ V, double* __restrict__ yl,
+                               int64_t nleaf, int nld, int q2, int ncol) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nleaf * nld * ncol) return;
+  const int col = int(id % ncol);
+  const int i = int((id / ncol) % nld);
+  const int64_t lf = id / ((int64_t)ncol * nld);
+  double acc = 0.0;
+  for (int ch = 0; ch < 3; ++ch) {
+    const double* Vc = V + (int64_t)ch * nld * q2 + (int64_t)i * q2;
+    const double* y = yh + lf * q2 * 3 * ncol + ch * ncol + col;
+    for (int a = 0; a < q2; ++a) acc += Vc[a] * y[(int64_t)a * 3 * ncol];
+  }
+  yl[id] = acc;
+}
+
 // xh[leaf][a][col] = sum_i V[i][a] xl[leaf*nld + i][col]
 template <typename T>
 __global__ void k_leaf_up(const T* __restrict__ xl, T* __restrict__ xh, const T* __restrict__ V, int64_t nleaf,
@@ -565,7 +599,36 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
   T* yh = xh + o.nclusters * q2 * ncol;
   const int tb = 256;
   gather_l<T>(o, x, xl, ncol, C, s);
-  if (q2 > 0) {
+  if (q2 > 0 && o.efie) {
+    // compressed EFIE (FP64): channel moments, transfers on 3 ncol columns, coupling, back
+    if (sizeof(T) != sizeof(double)) fail(BEMBEL_EUNSUPPORTED, "compressed EFIE: FP64 products only");
+    const int nch = 3 * ncol;
+    T* xhe = xh;
+    T* yhe = xh + o.nclusters * q2 * nch;
+    const int64_t leaf_off = o.lvl_off[o.leaf];
+    const size_t tsh = sizeof(T) * 4 * q2 * q2;
+    k_leaf_up_ch<<<blocks_for(o.nleaf * q2 * nch, tb), tb, 0, s>>>(
+        reinterpret_cast<const double*>(xl), reinterpret_cast<double*>(xhe + leaf_off * q2 * nch),
+        reinterpret_cast<const double*>(V), o.nleaf, o.nld, q2, ncol);
+    launched("k_leaf_up_ch");
+    for (int l = o.leaf - 1; l >= 0; --l) {
+      const int64_t np = o.lvl_off[l + 1] - o.lvl_off[l];
+      k_up<T><<<blocks_for(np * q2 * nch, tb), tb, tsh, s>>>(xhe + o.lvl_off[l] * q2 * nch,
+                                                             xhe + o.lvl_off[l + 1] * q2 * nch, Tm, np, q2, nch);
+      launched("k_up");
+    }
+    efie_coupling_apply(o, reinterpret_cast<const double*>(xhe), reinterpret_cast<double*>(yhe), nrhs, s);
+    for (int l = 1; l <= o.leaf; ++l) {
+      const int64_t nc = o.lvl_off[l + 1] - o.lvl_off[l];
+      k_down<T><<<blocks_for(nc * q2 * nch, tb), tb, tsh, s>>>(yhe + o.lvl_off[l] * q2 * nch,
+                                                               yhe + o.lvl_off[l - 1] * q2 * nch, Tm, nc, q2, nch);
+      launched("k_down");
+    }
+    k_leaf_down_ch<<<blocks_for(o.nleaf * o.nld * ncol, tb), tb, 0, s>>>(
+        reinterpret_cast<const double*>(yhe + leaf_off * q2 * nch), reinterpret_cast<const double*>(V),
+        reinterpret_cast<double*>(yl), o.nleaf, o.nld, q2, ncol);
+    launched("k_leaf_down_ch");
+  } else if (q2 > 0) {
     const int64_t leaf_off = o.lvl_off[o.leaf];
     const int ls = std::max(0, o.leaf - 3);
     const int nsub = 1 << (2 * (o.leaf - ls));
@@ -666,7 +729,8 @@ void scatter_to_global(const Op& o, const double* yl, double* y, int nrhs, cudaS
 size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32) {
   const int C = o.cplx ? 2 : 1;
   const size_t el = fp32 ? sizeof(float) : sizeof(double);
-  return el * (size_t)nrhs * C * (2 * (size_t)o.nlocal + 2 * (size_t)o.nclusters * o.q2);
+  const size_t channels = o.efie ? 3 : 1;  // compressed EFIE: three moment channels
+  return el * (size_t)nrhs * C * (2 * (size_t)o.nlocal + 2 * channels * (size_t)o.nclusters * o.q2);
 }
 
 void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s) {

@@ -80,6 +80,7 @@ struct Op {
   int gauss_off_far = 0;         // its [nodes][weights] in d_gauss
   int64_t npairs_regular_far = 0;
   double* d_Xq_far = nullptr;    // gamma at the far order's points
+  double* d_nodes_jac = nullptr; // EFIE: d_s gamma, d_t gamma at the cluster points
   double* d_BW_far = nullptr;
   double* d_Xq = nullptr;  // nelem * g_reg^2 * 3
   double* d_BW = nullptr;  // g_reg^2 * nloc: w_p h^2 B_k(u_p)
@@ -152,6 +153,8 @@ void run_assembly_batch(const std::vector<Op*>& ops);
 // efie.cu: S^1 element-pair quadrature (phases 1-4 with events ev[2..5]),
 // local load vectors of plane waves, and the scattered field at points
 void efie_pair_kernels(Op& o, cudaEvent_t* ev);
+void efie_coupling_assemble(Op& o);  // compressed EFIE: 5 coupling matrices per far block
+void efie_coupling_apply(const Op& o, const double* xh, double* yh, int nrhs, cudaStream_t s);
 void efie_rhs_local(const Op& o, const double* gx, const double* gw, int G, const double* prm_dev, int nrhs,
                     double* bl, cudaStream_t s);
 void efie_field(const Op& o, const double* rl, const double* gx, const double* gw, int G, const double* pts,

@@ -358,7 +358,7 @@ void launch_pairs(Op& o, cudaEvent_t* ev) {
 void alloc_assembly_outputs(Op& o) {
   const int C = o.cplx ? 2 : 1;
   const int64_t nN = o.nnear * (int64_t)o.nld * o.nld * C;
-  const int64_t nK = o.nfar * (int64_t)o.q2 * o.q2;
+  const int64_t nK = o.nfar * (int64_t)o.q2 * o.q2 * (o.efie ? 5 : 1);  // EFIE: five coupling matrices
   o.d_Xq = static_cast<double*>(dev_alloc(sizeof(double) * o.nelem * o.g_reg * o.g_reg * 3));
   o.d_Xq_far = static_cast<double*>(dev_alloc(sizeof(double) * o.nelem * o.g_reg_far * o.g_reg_far * 3));
   o.d_N = static_cast<double*>(dev_alloc(sizeof(double) * std::max<int64_t>(nN, 1)));
@@ -404,7 +404,9 @@ void run_assembly_kernels(Op& o) {
     }
   }
   // A6: coupling
-  if (o.nfar > 0) {
+  if (o.nfar > 0 && o.efie) {
+    efie_coupling_assemble(o);
+  } else if (o.nfar > 0) {
     const int64_t n = nK;
     if (o.cplx)
       k_coupling<true><<<grid_for(n, 256), 256, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre,

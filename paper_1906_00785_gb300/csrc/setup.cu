@@ -154,6 +154,67 @@ std::vector<double> extraction_1d(int deg, int nel1) {
   return ex;
 }
 
+// Leaf moments of the S^1 functions for the three EFIE channels (geometry
+// independent): V[ch][i][a], ch 0: int phi_hat^1 L_a, 1: int phi_hat^2 L_a,
+// 2: int div phi_hat L_a over the element, in patch parameters (measure h^2,
+// d/ds = (1/h) d/du), i = (element in leaf, Morton) * nloc + local function.
+void efie_moments(Op& o, const std::vector<double>& gx, const std::vector<double>& gw) {
+  const int p = o.d, q = o.q, q2 = o.q2, m = o.m, nloc = o.nloc, nld = o.nld;
+  auto bern_d = [](int deg, int k, double u) {  // d/du of the Bernstein polynomial
+    if (deg == 0) return 0.0;
+    const double lo = k >= 1 ? bernstein_h(deg - 1, k - 1, u) : 0.0;
+    const double hi = k <= deg - 1 ? bernstein_h(deg - 1, k, u) : 0.0;
+    return deg * (lo - hi);
+  };
+  // 1-D moments per element position me inside the leaf: degree p values,
+  // degree p - 1 values, degree p derivatives
+  std::vector<double> Mp((size_t)m * (p + 1) * q), Mq((size_t)m * p * q), Dp((size_t)m * (p + 1) * q);
+  for (int me = 0; me < m; ++me)
+    for (int a = 0; a < q; ++a) {
+      for (int k = 0; k <= p; ++k) {
+        double v = 0.0, dv = 0.0;
+        for (size_t g = 0; g < gx.size(); ++g) {
+          const double la = lagrange01(q, a, (me + gx[g]) / m);
+          v += gw[g] * bernstein_h(p, k, gx[g]) * la;
+          dv += gw[g] * bern_d(p, k, gx[g]) * la;
+        }
+        Mp[((size_t)me * (p + 1) + k) * q + a] = v;
+        Dp[((size_t)me * (p + 1) + k) * q + a] = dv;
+      }
+      for (int k = 0; k < p; ++k) {
+        double v = 0.0;
+        for (size_t g = 0; g < gx.size(); ++g) v += gw[g] * bernstein_h(p - 1, k, gx[g]) * lagrange01(q, a, (me + gx[g]) / m);
+        Mq[((size_t)me * p + k) * q + a] = v;
+      }
+    }
+  const double h = o.h;
+  std::vector<double> V((size_t)3 * nld * q2, 0.0);
+  for (int pe = 0; pe < m * m; ++pe) {
+    uint32_t e1, e2;
+    morton_decode(pe, e1, e2);
+    for (int k = 0; k < nloc; ++k) {
+      const bool first = k < (p + 1) * p;
+      const int kk = first ? k : k - (p + 1) * p;
+      const int k1 = first ? kk % (p + 1) : kk % p, k2 = first ? kk / (p + 1) : kk / p;
+      const int i = pe * nloc + k;
+      for (int a2 = 0; a2 < q; ++a2)
+        for (int a1 = 0; a1 < q; ++a1) {
+          const int a = a1 + q * a2;
+          if (first) {  // degree p in s, p - 1 in t
+            const double ms = Mp[((size_t)e1 * (p + 1) + k1) * q + a1], mt = Mq[((size_t)e2 * p + k2) * q + a2];
+            V[((size_t)0 * nld + i) * q2 + a] = h * h * ms * mt;
+            V[((size_t)2 * nld + i) * q2 + a] = h * Dp[((size_t)e1 * (p + 1) + k1) * q + a1] * mt;
+          } else {      // degree p - 1 in s, p in t
+            const double ms = Mq[((size_t)e1 * p + k1) * q + a1], mt = Mp[((size_t)e2 * (p + 1) + k2) * q + a2];
+            V[((size_t)1 * nld + i) * q2 + a] = h * h * ms * mt;
+            V[((size_t)2 * nld + i) * q2 + a] = h * ms * Dp[((size_t)e2 * (p + 1) + k2) * q + a2];
+          }
+        }
+    }
+  }
+  o.d_V = upload(V);
+}
+
 // S^1 space of App. E on the six patches: global numbering with the edge glue
 // (normal continuity) and the signed extraction E (element-local Bernstein
 // functions <- global dofs) as CSR, plus its transpose.
@@ -660,6 +721,7 @@ void build_structure(Op& o) {
     const int q = o.q, q2 = o.q2;
     std::vector<double> gx, gw;
     gauss01(d + q, gx, gw);
+    if (o.efie) efie_moments(o, gx, gw);
     // M1[me][k][a] = int_0^1 B_k(u) l_a((me + u)/m) du
     std::vector<double> M1((size_t)o.m * (d + 1) * q, 0.0);
     for (int me = 0; me < o.m; ++me)
@@ -671,7 +733,7 @@ void build_structure(Op& o) {
           M1[((size_t)me * (d + 1) + k) * q + a] = acc;
         }
     std::vector<double> V((size_t)nld * q2);
-    for (int pe = 0; pe < m2; ++pe) {
+    for (int pe = 0; pe < m2 && !o.efie; ++pe) {
       uint32_t e1, e2;
       morton_decode(pe, e1, e2);
       for (int k2 = 0; k2 <= d; ++k2)
@@ -695,7 +757,7 @@ void build_structure(Op& o) {
             for (int a1 = 0; a1 < q; ++a1)
               T[((size_t)c * q2 + ap1 + q * ap2) * q2 + a1 + q * a2] =
                   T1[((c & 1) * q + ap1) * q + a1] * T1[((c >> 1) * q + ap2) * q + a2];
-    o.d_V = upload(V);
+    if (!o.efie) o.d_V = upload(V);
     o.d_T = upload(T);
     std::vector<float> V32(V.begin(), V.end()), T32(T.begin(), T.end());
     o.d_V32 = upload(V32);
@@ -722,6 +784,27 @@ void build_structure(Op& o) {
       }
     });
     o.d_nodes = upload(nodes);
+    if (o.efie) {  // d_s gamma, d_t gamma at the cluster points (EFIE coupling)
+      std::vector<double> jac((size_t)o.nclusters * q2 * 6);
+      parallel_for(o.nclusters, [&](int64_t c0, int64_t c1) {
+        for (int64_t gc = c0; gc < c1; ++gc) {
+          int l = 0;
+          while (gc >= o.lvl_off[l + 1]) ++l;
+          const int64_t nper = int64_t(1) << (2 * l);
+          const int64_t c = gc - o.lvl_off[l];
+          const double H = std::ldexp(1.0, -l);
+          uint32_t j1, j2;
+          morton_decode(uint32_t(c % nper), j1, j2);
+          for (int a2 = 0; a2 < q; ++a2)
+            for (int a1 = 0; a1 < q; ++a1) {
+              double x[3];
+              double* J = &jac[((size_t)gc * q2 + a1 + q * a2) * 6];
+              sphere6_jac(int(c / nper), (j1 + cheb[a1]) * H, (j2 + cheb[a2]) * H, x, J, J + 3);
+            }
+        }
+      });
+      o.d_nodes_jac = upload(jac);
+    }
     std::vector<float> nodes32(nodes.size() / 3 * 4, 0.f);
     for (size_t k = 0; k < nodes.size() / 3; ++k)
       for (int c = 0; c < 3; ++c) nodes32[k * 4 + c] = float(nodes[k * 3 + c]);

@@ -115,9 +115,47 @@ def test_efie_level4_degree2_k4(geom):
     assert err < 1e-2, (err, info)
 
 
+@pytest.mark.parametrize("L,p,q", [(2, 1, 3), (2, 2, 4)])
+def test_efie_h2_parity(geom, L, p, q):
+    """Compressed EFIE: nested channel moments, transfers and the five coupling
+    matrices against the oracle's directly integrated H^2 blocks."""
+    from oracle.efie import EfieH2Oracle
+
+    op = bem.bembel_assemble(geom, MAX, 2.0, L, p, q, g_regular=3, g_singular=4, leaf_level=L - 1, eta=1.6)
+    sp = S1Space(Sphere6(), L, p)
+    h2 = EfieH2Oracle(sp, 2.0, q=q, eta=1.6, leaf_level=L - 1, g_reg=3, g_sing=4)
+    assert bem.bembel_op_info_get(op)["n_far_blocks"] == len(h2.far) > 0
+    ref = h2.dense()
+    A = gpu_matrix(op, sp.ndofs)
+    assert np.max(np.abs(A - ref)) / np.max(np.abs(ref)) < 1e-12
+
+
+def test_efie_h2_solution_matches_dense(geom):
+    """At q = 5 the compressed EFIE's scattered field matches the dense one's Mie error."""
+    k = 2.0
+    rng = np.random.default_rng(4)
+    pts = rng.standard_normal((40, 3))
+    pts *= (3.0 / np.linalg.norm(pts, axis=1))[:, None]
+    ref = scattered_pec(pts, k)
+    errs = []
+    for q in (0, 5):
+        op = bem.bembel_assemble(geom, MAX, k, 3, 2, q)
+        n = bem.bembel_ndofs(op)
+        b = torch.empty(n, dtype=torch.complex128, device="cuda")
+        bem.bembel_rhs(op, bem.BEMBEL_RHS_EFIE_PLANE_WAVE, plane(k), b)
+        x = torch.empty_like(b)
+        info = bem.bembel_solve(op, b, x, 1, tol=1e-6, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI, restart=100,
+                                max_iter=3000)
+        assert info["converged"], info
+        out = torch.empty((1, 40, 3), dtype=torch.complex128, device="cuda")
+        bem.bembel_eval(op, torch.from_numpy(pts).cuda(), x, out, 1, g=6)
+        errs.append(np.linalg.norm(out[0].cpu().numpy() - ref) / np.linalg.norm(ref))
+    assert abs(errs[1] - errs[0]) < 0.1 * errs[0], errs
+
+
 def test_efie_invalid(geom):
     with pytest.raises(bem.BembelError):
-        bem.bembel_assemble(geom, MAX, 2.0, 2, 1, 4)  # compressed EFIE not provided
+        bem.bembel_assemble(geom, MAX, 2.0, 2, 1, 4, precision=bem.BEMBEL_PREC_MIXED)  # compressed EFIE is FP64
     with pytest.raises(bem.BembelError):
         bem.bembel_assemble(geom, MAX, 0.0, 2, 1, 0)  # kappa = 0
     with pytest.raises(bem.BembelError):

@@ -198,3 +198,17 @@ def test_efie_converges_to_mie():
         errs[(L, p)] = np.linalg.norm(efie_field(sp, rho, pts, k) - ref) / np.linalg.norm(ref)
     assert errs[(1, 1)] < 0.1 and errs[(0, 1)] / errs[(1, 1)] > 5.0
     assert errs[(1, 2)] < errs[(1, 1)]
+
+
+def test_compressed_efie_converges_to_dense():
+    """The H^2 EFIE (Jacobian factors interpolated with G) approaches the dense EFIE as q grows."""
+    from oracle.efie import EfieH2Oracle
+
+    sp = S1Space(Sphere6(), 2, 1)
+    A = EfieAssembler(sp, 2.0, 3, 4).dense()
+    errs = []
+    for q in (3, 5):
+        h2 = EfieH2Oracle(sp, 2.0, q=q, eta=1.6, leaf_level=1, g_reg=3, g_sing=4)
+        assert len(h2.far) > 0
+        errs.append(np.abs(h2.dense() - A).max() / np.abs(A).max())
+    assert errs[1] < errs[0] / 20 and errs[1] < 1e-4, errs
