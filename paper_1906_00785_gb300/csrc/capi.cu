@@ -47,7 +47,7 @@ void free_op(Op* o) {
   if (!o) return;
   void* ptrs[] = {o->d_far_ptr, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
-                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_BW_far, o->d_nodes_jac,   o->d_nodes, o->d_scratch, o->d_bj,
+                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_BW_far, o->d_nodes_jac, o->d_dofmajor,   o->d_nodes, o->d_scratch, o->d_bj,
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
                   o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
                   o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val};

@@ -124,9 +124,136 @@ __global__ void k_csr_scatter(const int* __restrict__ ptr, const int* __restrict
   y[((int64_t)r * ndofs + g) * C + comp] = T(acc);
 }
 
+// Wide products: the API vectors (one contiguous vector per column) are first
+// transposed to dof-major (ndofs x ncol, 32 x 32 shared-memory tiles), so the
+// gather and scatter read and write whole rows of columns.
+template <typename T>
+__global__ void k_to_dofmajor(const T* __restrict__ x, T* __restrict__ xt, int64_t ndofs, int ncol, int C) {
+  __shared__ T tile[32][33];
+  const int64_t g0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  // read: consecutive threads along dofs of one column (column c = r * C + comp)
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i;
+    const int64_t g = g0 + threadIdx.x;
+    if (c < ncol && g < ndofs) tile[i][threadIdx.x] = x[((int64_t)(c / C) * ndofs + g) * C + c % C];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t g = g0 + i;
+    const int c = c0 + threadIdx.x;
+    if (c < ncol && g < ndofs) xt[g * ncol + c] = tile[threadIdx.x][i];
+  }
+}
+
+template <typename T>
+__global__ void k_from_dofmajor(const T* __restrict__ yt, T* __restrict__ y, int64_t ndofs, int ncol, int C) {
+  __shared__ T tile[32][33];
+  const int64_t g0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t g = g0 + i;
+    const int c = c0 + threadIdx.x;
+    if (c < ncol && g < ndofs) tile[i][threadIdx.x] = yt[g * ncol + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i;
+    const int64_t g = g0 + threadIdx.x;
+    if (c < ncol && g < ndofs) y[((int64_t)(c / C) * ndofs + g) * C + c % C] = tile[threadIdx.x][i];
+  }
+}
+
+// S^2 gather from dof-major x: warp per local dof, lanes over columns.
+template <typename T>
+__global__ void k_gather_dm(const T* __restrict__ xt, T* __restrict__ xl, const double* __restrict__ ex, int L, int d,
+                            int n1, int64_t nlocal, int ncol) {
+  const int64_t ld = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (ld >= nlocal) return;
+  const int D1 = d + 1, nloc = D1 * D1;
+  const int64_t e = ld / nloc;
+  const int k = int(ld % nloc), k1 = k % D1, k2 = k / D1;
+  const int64_t per = int64_t(1) << (2 * L);
+  const int patch = int(e / per);
+  uint32_t i1, i2;
+  morton_decode(uint32_t(e % per), i1, i2);
+  for (int c = lane; c < ncol; c += 32) {
+    double acc = 0.0;
+    for (int j2 = 0; j2 < D1; ++j2) {
+      const double c2 = ex[((int64_t)i2 * D1 + j2) * D1 + k2];
+      if (c2 == 0.0) continue;
+      for (int j1 = 0; j1 < D1; ++j1) {
+        const double c1 = ex[((int64_t)i1 * D1 + j1) * D1 + k1];
+        if (c1 == 0.0) continue;
+        const int64_t g = (int64_t)patch * n1 * n1 + (int64_t)(i2 + j2) * n1 + (i1 + j1);
+        acc += c1 * c2 * (double)xt[g * ncol + c];
+      }
+    }
+    xl[ld * ncol + c] = T(acc);
+  }
+}
+
+// S^2 scatter to dof-major y: warp per global dof, lanes over columns.
+template <typename T>
+__global__ void k_scatter_dm(const T* __restrict__ yl, T* __restrict__ yt, const double* __restrict__ ex, int L,
+                             int d, int n1, int64_t ndofs, int ncol) {
+  const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= ndofs) return;
+  const int D1 = d + 1, nloc = D1 * D1;
+  const int nel1 = 1 << L;
+  const int patch = int(g / ((int64_t)n1 * n1));
+  const int rem = int(g % ((int64_t)n1 * n1));
+  const int j2 = rem / n1, j1 = rem % n1;
+  const int64_t per = int64_t(1) << (2 * L);
+  for (int c = lane; c < ncol; c += 32) {
+    double acc = 0.0;
+    for (int i2 = max(0, j2 - d); i2 <= min(nel1 - 1, j2); ++i2)
+      for (int i1 = max(0, j1 - d); i1 <= min(nel1 - 1, j1); ++i1) {
+        const int64_t e = (int64_t)patch * per + morton_encode(i1, i2);
+        for (int k2 = 0; k2 < D1; ++k2) {
+          const double c2 = ex[((int64_t)i2 * D1 + (j2 - i2)) * D1 + k2];
+          if (c2 == 0.0) continue;
+          for (int k1 = 0; k1 < D1; ++k1) {
+            const double c1 = ex[((int64_t)i1 * D1 + (j1 - i1)) * D1 + k1];
+            if (c1 == 0.0) continue;
+            acc += c1 * c2 * (double)yl[(e * nloc + k1 + D1 * k2) * ncol + c];
+          }
+        }
+      }
+    yt[g * ncol + c] = T(acc);
+  }
+}
+
 // element-local <-> global for either space
+// matvec_noalloc sets this: nothing may be allocated on its path
+static thread_local bool t_no_alloc = false;
+
+// dof-major staging buffer for wide S^2 products (ndofs x ncol): used when it
+// is already large enough, or grown when allocating is allowed here (not under
+// graph capture, not on the no-allocation path); otherwise the strided kernels run
+template <typename T>
+T* dofmajor_buffer(const Op& o, int ncol) {
+  const size_t bytes = sizeof(T) * (size_t)o.ndofs * ncol;
+  if (o.efie || ncol < 32) return nullptr;
+  if (o.dofmajor_bytes < bytes) {
+    if (capturing() || t_no_alloc) return nullptr;
+    ensure_dofmajor(const_cast<Op&>(o), bytes);
+  }
+  return static_cast<T*>(o.d_dofmajor);
+}
+
 template <typename T>
 void gather_l(const Op& o, const T* x, T* xl, int ncol, int C, cudaStream_t s) {
+  if (T* xt = dofmajor_buffer<T>(o, ncol)) {
+    k_to_dofmajor<T><<<dim3(unsigned((o.ndofs + 31) / 32), unsigned((ncol + 31) / 32)), dim3(32, 8), 0, s>>>(
+        x, xt, o.ndofs, ncol, C);
+    launched("k_to_dofmajor");
+    k_gather_dm<T><<<blocks_for(o.nlocal * 32, 256), 256, 0, s>>>(xt, xl, o.d_ex, o.L, o.d, o.n1, o.nlocal, ncol);
+    launched("k_gather_dm");
+    return;
+  }
   if (o.efie)
     k_csr_gather<T><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(o.d_e_ptr, o.d_e_col, o.d_e_val, x, xl,
                                                                       o.ndofs, o.nlocal, ncol, C);
@@ -138,6 +265,14 @@ void gather_l(const Op& o, const T* x, T* xl, int ncol, int C, cudaStream_t s) {
 
 template <typename T>
 void scatter_l(const Op& o, const T* yl, T* y, int ncol, int C, cudaStream_t s) {
+  if (T* yt = dofmajor_buffer<T>(o, ncol)) {
+    k_scatter_dm<T><<<blocks_for(o.ndofs * 32, 256), 256, 0, s>>>(yl, yt, o.d_ex, o.L, o.d, o.n1, o.ndofs, ncol);
+    launched("k_scatter_dm");
+    k_from_dofmajor<T><<<dim3(unsigned((o.ndofs + 31) / 32), unsigned((ncol + 31) / 32)), dim3(32, 8), 0, s>>>(
+        yt, y, o.ndofs, ncol, C);
+    launched("k_from_dofmajor");
+    return;
+  }
   if (o.efie)
     k_csr_scatter<T><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(o.d_et_ptr, o.d_et_col, o.d_et_val, yl, y,
                                                                       o.ndofs, ncol, C);
@@ -566,6 +701,101 @@ __global__ void k_down_subtree(const T* __restrict__ yh, T* __restrict__ yl, con
   }
 }
 
+// Block-sparse product for many right-hand sides, one CTA per target block
+// row: y[t] += sum_{k in row t} M_k x[col_k].  Each block (bs x bs, row-major)
+// and its source slice (bs x ncol) are staged in shared memory (two buffers),
+// every thread accumulates up to kRowOut outputs (row a, column j; complex
+// pairs for CPLX) in registers and adds them into its own rows: the block
+// matrix is read once per product and no atomics are needed.
+constexpr int kRowOut = 16;
+constexpr int kRowThreads = 256;
+
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(kRowThreads) k_bsr_rows(const long long* __restrict__ ptr,
+                                                          const int* __restrict__ col, int64_t nrows,
+                                                          const T* __restrict__ M, const T* __restrict__ x,
+                                                          T* __restrict__ y, int bs, int nrhs) {
+  constexpr int C = CPLX ? 2 : 1;
+  extern __shared__ unsigned char smem_raw[];
+  const int ncol = nrhs * C;
+  const int mstride = bs * bs * C, xstride = bs * ncol;
+  T* Ms = reinterpret_cast<T*>(smem_raw);  // [2][bs*bs*C]
+  T* Xs = Ms + 2 * mstride;                // [2][bs*ncol]
+  const int64_t t = blockIdx.x;
+  if (t >= nrows) return;
+  T accr[kRowOut], acci[kRowOut];
+#pragma unroll
+  for (int o = 0; o < kRowOut; ++o) accr[o] = acci[o] = T(0);
+  const long long k0 = ptr[t], k1 = ptr[t + 1];
+  auto stage = [&](long long k, int buf) {
+    const T* mk = M + k * (int64_t)mstride;
+    for (int i = threadIdx.x; i < mstride; i += blockDim.x) Ms[buf * mstride + i] = mk[i];
+    const T* xk = x + (int64_t)col[k] * xstride;
+    for (int i = threadIdx.x; i < xstride; i += blockDim.x) Xs[buf * xstride + i] = xk[i];
+  };
+  if (k0 < k1) stage(k0, 0);
+  __syncthreads();
+  for (long long k = k0; k < k1; ++k) {
+    const int buf = int((k - k0) & 1);
+    if (k + 1 < k1) stage(k + 1, buf ^ 1);
+    const T* Mb = Ms + buf * mstride;
+    const T* Xb = Xs + buf * xstride;
+    // thread (row group rg, column j): rows a = rg + ng * o.  One load of x per
+    // b serves every row of the thread; the block entries are warp broadcasts.
+    {
+      const int j = threadIdx.x % nrhs, rg = threadIdx.x / nrhs, ng = kRowThreads / nrhs;
+      if (rg < ng) {
+        for (int b = 0; b < bs; ++b) {
+          const T* xv = Xb + (int64_t)b * ncol + j * C;
+          const T xr = xv[0], xi = CPLX ? xv[1] : T(0);
+#pragma unroll
+          for (int o = 0; o < kRowOut; ++o) {
+            const int a = rg + ng * o;
+            if (a >= bs) break;
+            const T* m = Mb + ((int64_t)a * bs + b) * C;
+            if (CPLX) {
+              accr[o] = fma(m[0], xr, fma(-m[1], xi, accr[o]));
+              acci[o] = fma(m[0], xi, fma(m[1], xr, acci[o]));
+            } else {
+              accr[o] = fma(m[0], xr, accr[o]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int j = threadIdx.x % nrhs, rg = threadIdx.x / nrhs, ng = kRowThreads / nrhs;
+  if (rg >= ng) return;
+#pragma unroll
+  for (int o = 0; o < kRowOut; ++o) {
+    const int a = rg + ng * o;
+    if (a >= bs) break;
+    T* yo = y + (t * bs + a) * (int64_t)ncol + j * C;
+    yo[0] += accr[o];
+    if (CPLX) yo[1] += acci[o];
+  }
+}
+
+// the row kernel applies when the product is wide, nrhs divides the thread
+// count and every thread's rows fit its registers
+bool rows_kernel_fits(int bs, int nrhs, int C, size_t el) {
+  const size_t shm = el * 2 * ((size_t)bs * bs * C + (size_t)bs * nrhs * C);
+  if (nrhs * C < 8 || nrhs > kRowThreads || kRowThreads % nrhs != 0) return false;
+  const int ng = kRowThreads / nrhs;
+  return (bs + ng - 1) / ng <= kRowOut && shm <= 160 * 1024;
+}
+
+template <typename T, bool CPLX>
+void launch_bsr_rows(const long long* ptr, const int* col, int64_t nrows, const T* M, const T* x, T* y, int bs,
+                     int nrhs, cudaStream_t s) {
+  const int C = CPLX ? 2 : 1;
+  const size_t shm = sizeof(T) * 2 * ((size_t)bs * bs * C + (size_t)bs * nrhs * C);
+  set_smem_limit(k_bsr_rows<T, CPLX>, shm);
+  k_bsr_rows<T, CPLX><<<int(nrows), kRowThreads, shm, s>>>(ptr, col, nrows, M, x, y, bs, nrhs);
+  launched("k_bsr_rows");
+}
+
 template <typename T, bool CPLX, bool ONFLY>
 void launch_bsr(const int* tgt, const int* src, int64_t nblk, const T* M, const float* pts, float kre, float kim,
                 const T* x, T* y, int bs, int nrhs, cudaStream_t s, int chunk) {
@@ -670,12 +900,16 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
       if (fp32)
         launch_bsr<T, true, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, float(o.kre),
                                   float(o.kim), xh, yh, q2, nrhs, s, o.bsr_chunk);
+      else if (rows_kernel_fits(q2, nrhs, C, sizeof(T)))
+        launch_bsr_rows<T, true>(o.d_far_ptr, o.d_far_src, o.nclusters, K, xh, yh, q2, nrhs, s);
       else
         launch_bsr<T, true, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s, o.bsr_chunk);
     } else {
       if (fp32)
         launch_bsr<T, false, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, 0.f, 0.f, xh, yh, q2,
                                    nrhs, s, o.bsr_chunk);
+      else if (rows_kernel_fits(q2, nrhs, C, sizeof(T)))
+        launch_bsr_rows<T, false>(o.d_far_ptr, o.d_far_src, o.nclusters, K, xh, yh, q2, nrhs, s);
       else
         launch_bsr<T, false, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s, o.bsr_chunk);
     }
@@ -705,10 +939,17 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
   } else {
     cuda_check(cudaMemsetAsync(yl, 0, sizeof(T) * o.nlocal * ncol, s), "yl clear");
   }
-  if (o.cplx)
+  if (rows_kernel_fits(o.nld, nrhs, C, sizeof(T))) {
+    // many right-hand sides: one CTA per target leaf row
+    if (o.cplx)
+      launch_bsr_rows<T, true>(o.d_near_ptr, o.d_near_col, o.nleaf, N, xl, yl, o.nld, nrhs, s);
+    else
+      launch_bsr_rows<T, false>(o.d_near_ptr, o.d_near_col, o.nleaf, N, xl, yl, o.nld, nrhs, s);
+  } else if (o.cplx) {
     launch_bsr<T, true, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
-  else
+  } else {
     launch_bsr<T, false, false>(o.d_near_tgt, o.d_near_col, o.nnear, N, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
+  }
   scatter_l<T>(o, yl, y, ncol, C, s);
 }
 
@@ -786,6 +1027,10 @@ void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cu
   if (fp32 && !o.d_N32) fail(BEMBEL_EINVAL, "FP32 matvec needs an operator assembled with precision MIXED");
   // every scratch element is written before it is read, so nothing is cleared
   void* scratch = noalloc_scratch_address();
+  struct NoAlloc {
+    NoAlloc() { t_no_alloc = true; }
+    ~NoAlloc() { t_no_alloc = false; }
+  } no_alloc_scope;
   if (fp32)
     matvec_impl<float>(o, static_cast<const float*>(x), static_cast<float*>(y), nrhs, s, o.d_K32, o.d_N32, o.d_V32,
                        o.d_T32, scratch);
@@ -864,6 +1109,17 @@ void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cud
     precond_impl<float>(o, static_cast<const float*>(x), static_cast<float*>(y), nrhs, s, o.d_bj32);
   else
     precond_impl<double>(o, static_cast<const double*>(x), static_cast<double*>(y), nrhs, s, o.d_bj);
+}
+
+void ensure_dofmajor(Op& o, size_t bytes) {
+  if (bytes <= o.dofmajor_bytes) return;
+  if (capturing()) fail(BEMBEL_ECUDA, "dof-major buffer must be reserved before graph capture");
+  if (o.d_dofmajor) {
+    cuda_check(cudaStreamSynchronize(o.stream), "dof-major sync");
+    dev_free(o.d_dofmajor);
+  }
+  o.d_dofmajor = dev_alloc(bytes);
+  o.dofmajor_bytes = bytes;
 }
 
 void ensure_scratch(Op& o, size_t bytes) {

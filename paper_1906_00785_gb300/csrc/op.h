@@ -110,6 +110,8 @@ struct Op {
   int* h_tc_err = nullptr;         // host-mapped flag: set when a bounded MMA wait timed out
   int64_t tc_ngroups = 0, tc_nentries = 0;
   void* d_scratch = nullptr;
+  void* d_dofmajor = nullptr;  // dof-major staging of wide S^2 products (ndofs x ncol)
+  size_t dofmajor_bytes = 0;
   size_t scratch_bytes = 0;
 
   // block-Jacobi preconditioner: inverses of the near-field diagonal blocks
@@ -162,6 +164,7 @@ void efie_field(const Op& o, const double* rl, const double* gx, const double* g
 // h2mv.cu
 void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
 void ensure_scratch(Op& o, size_t bytes);
+void ensure_dofmajor(Op& o, size_t bytes);
 size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32);
 // same product with the fixed file-scope scratch of h2mv.cu; allocates nothing
 void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
