@@ -727,17 +727,42 @@ __global__ void __launch_bounds__(kRowThreads) k_bsr_rows(const long long* __res
 #pragma unroll
   for (int o = 0; o < kRowOut; ++o) accr[o] = acci[o] = T(0);
   const long long k0 = ptr[t], k1 = ptr[t + 1];
+  // staging: asynchronous 16-byte copies (cp.async) when every piece is 16-byte
+  // aligned, so the next block streams in while the current one is used
+  const bool async = ((mstride * sizeof(T)) % 16 == 0) && ((xstride * sizeof(T)) % 16 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(x)) % 16 == 0);
   auto stage = [&](long long k, int buf) {
     const T* mk = M + k * (int64_t)mstride;
-    for (int i = threadIdx.x; i < mstride; i += blockDim.x) Ms[buf * mstride + i] = mk[i];
     const T* xk = x + (int64_t)col[k] * xstride;
-    for (int i = threadIdx.x; i < xstride; i += blockDim.x) Xs[buf * xstride + i] = xk[i];
+    if (async) {
+      const int mchunks = int(mstride * sizeof(T) / 16), xchunks = int(xstride * sizeof(T) / 16);
+      const char* msrc = reinterpret_cast<const char*>(mk);
+      const char* xsrc = reinterpret_cast<const char*>(xk);
+      const uint32_t mdst = static_cast<uint32_t>(__cvta_generic_to_shared(Ms + buf * mstride));
+      const uint32_t xdst = static_cast<uint32_t>(__cvta_generic_to_shared(Xs + buf * xstride));
+      for (int i = threadIdx.x; i < mchunks; i += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(mdst + 16 * i), "l"(msrc + 16 * i)
+                     : "memory");
+      for (int i = threadIdx.x; i < xchunks; i += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(xdst + 16 * i), "l"(xsrc + 16 * i)
+                     : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    } else {
+      for (int i = threadIdx.x; i < mstride; i += blockDim.x) Ms[buf * mstride + i] = mk[i];
+      for (int i = threadIdx.x; i < xstride; i += blockDim.x) Xs[buf * xstride + i] = xk[i];
+    }
   };
   if (k0 < k1) stage(k0, 0);
-  __syncthreads();
   for (long long k = k0; k < k1; ++k) {
     const int buf = int((k - k0) & 1);
-    if (k + 1 < k1) stage(k + 1, buf ^ 1);
+    if (k + 1 < k1) stage(k + 1, buf ^ 1);  // buf ^ 1 was released by the previous iteration's barrier
+    if (async) {
+      if (k + 1 < k1)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // block k has landed (k + 1 may be in flight)
+      else
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
     const T* Mb = Ms + buf * mstride;
     const T* Xb = Xs + buf * xstride;
     // thread (row group rg, column j): rows a = rg + ng * o.  One load of x per
