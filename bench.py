@@ -38,8 +38,25 @@ WORKLOAD = dict(level=6, p=1, q=4, eta=1.6, leaf=5, g_reg=4, g_sing=5, quad_tol=
 # FP64 flops per quadrature point (counted from the formulas):
 # regular pair point (x_p, y_q): difference, squared norm, 1/r, 4 (d=1) weighted products
 FLOPS_REG_POINT = {0: 12, 1: 18, 2: 28}
-# Duffy point: rule map + both patch maps + 1/r + (d+1)^4 basis products
+# identical-pair Duffy point: rule map + both patch maps + 1/r + (d+1)^4 basis products
 FLOPS_SING_POINT = {0: 80, 1: 110, 2: 250}
+# one side point of the factorised edge / vertex rules: patch map + weighted Bernstein values
+FLOPS_SIDE_POINT = {0: 22, 1: 30, 2: 48}
+
+
+def touching_pair_flops(kind, g, p):
+    """FP64 flops of one common-edge / common-vertex pair in the factorised rule sums:
+    every rule point is one kernel evaluation with its (d+1)^2 row update (the regular-point
+    count), every distinct side point one patch map, every outer point one (d+1)^4 outer product."""
+    g0, g1, g2, g3 = g
+    fk, fp, fo = FLOPS_REG_POINT[p], FLOPS_SIDE_POINT[p], 2 * (p + 1) ** 4
+    if kind == "vertex":
+        items, staged, moving = 2 * g0 * g2 * g3 + 2 * g0 * g1 * g2, 2 * g0 * g1 + 2 * g0 * g3, 0
+    else:
+        items = 2 * g0 * g3 * g2 + 4 * g0 * g2 * g3
+        staged, moving = 2 * g0 * g3 * g1, 4 * g0 * g2 * g3 * g1
+    npts = (4 if kind == "vertex" else 6) * g0 * g1 * g2 * g3
+    return npts * fk + items * (fp + fo) + (staged + moving) * fp
 
 
 def parse():
@@ -342,9 +359,12 @@ def main():
     names = ["tabulation", "near_regular", "singular_identical", "singular_edge", "singular_vertex", "coupling",
              "fp32_copies"]
     # rule points actually integrated (identical pairs: half of the 8 sub-domains, by symmetry)
-    def npts4(kind):  # Gauss points of one sub-domain: per-variable orders when tuned so
+    def orders(kind):  # per-variable orders when tuned so
         v = tune[f"g_{kind}_var"]
-        return int(np.prod(v)) if all(v) else tune[f"g_{kind}"] ** 4
+        return tuple(v) if all(v) else (tune[f"g_{kind}"],) * 4
+
+    def npts4(kind):  # Gauss points of one sub-domain
+        return int(np.prod(orders(kind)))
 
     n_far = opinfo["n_pairs_regular_far"]
     pts_phase = {"near_regular": (opinfo["n_pairs_regular"] - n_far) * tune["g_regular"] ** 4
@@ -352,8 +372,11 @@ def main():
                  "singular_identical": opinfo["n_pairs_identical"] * 4 * npts4("identical"),
                  "singular_edge": opinfo["n_pairs_edge"] * 6 * npts4("edge"),
                  "singular_vertex": opinfo["n_pairs_vertex"] * 4 * npts4("vertex")}
-    flops_phase = {k: v * (FLOPS_REG_POINT[w["p"]] if k == "near_regular" else FLOPS_SING_POINT[w["p"]])
-                   for k, v in pts_phase.items()}
+    flops_phase = {"near_regular": pts_phase["near_regular"] * FLOPS_REG_POINT[w["p"]],
+                   "singular_identical": pts_phase["singular_identical"] * FLOPS_SING_POINT[w["p"]],
+                   "singular_edge": opinfo["n_pairs_edge"] * touching_pair_flops("edge", orders("edge"), w["p"]),
+                   "singular_vertex": opinfo["n_pairs_vertex"] * touching_pair_flops("vertex", orders("vertex"),
+                                                                                     w["p"])}
     dom = max(flops_phase, key=lambda k: ph[names.index(k)])
     dom_ms = ph[names.index(dom)]
     achieved = flops_phase[dom] / (dom_ms / 1e3) / 1e12
