@@ -42,6 +42,9 @@ FLOPS_REG_POINT = {0: 12, 1: 18, 2: 28}
 FLOPS_SING_POINT = {0: 80, 1: 110, 2: 250}
 # one side point of the factorised edge / vertex rules: patch map + weighted Bernstein values
 FLOPS_SIDE_POINT = {0: 22, 1: 30, 2: 48}
+# DRAM bytes per separated pair of k_near_regular<1, 0> (pair record + written blocks), from the
+# ncu capture in profiles/quadrature_kernels_laplace_L5_p1.md: 28.31 MB over 254,412 pairs
+REGULAR_DRAM_BYTES_PER_PAIR = 28.31e6 / 254412
 
 
 def touching_pair_flops(kind, g, p):
@@ -383,7 +386,10 @@ def main():
     peak = fp64_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
     roofline = {"kernel": f"k_near_singular ({dom})" if dom != "near_regular" else "k_near_regular",
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                # ncu DRAM bytes of a level-5 launch scaled by the pairs of this launch (traffic grows
+                # with the pair count: records read, blocks written); measured for degree 1 only
+                "traffic": (REGULAR_DRAM_BYTES_PER_PAIR * opinfo["n_pairs_regular"]
+                            if dom == "near_regular" and w["p"] == 1 else None),
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (derived; no FP64 peak "
                                "in MEASURED_PEAKS.json)",
                 "algorithmic_flops": flops_phase[dom], "launch_ms": dom_ms}

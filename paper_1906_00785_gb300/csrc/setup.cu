@@ -521,28 +521,41 @@ void build_structure(Op& o) {
   const long long blk2 = (long long)nld * nld;
 
   // ---- element corner ids (physical matching, App. D) --------------------------
+  // A grid node inside a patch belongs to that patch alone; the nodes on patch
+  // boundaries are matched across patches by rounded position.
   std::vector<long long> cid(o.nelem * 4);
   {
-    // corner positions in parallel, then ids by matching rounded positions
-    std::vector<std::array<long long, 3>> keys(o.nelem * 4);
+    const int64_t nn = int64_t(nel1 + 1) * (nel1 + 1);  // grid nodes per patch
+    std::vector<long long> node(6 * nn, -1);
+    std::unordered_map<std::array<long long, 3>, long long, KeyHash> table;
+    table.reserve(6 * 4 * (size_t)nel1 * 2);
+    long long next = 0;
+    for (int patch = 0; patch < 6; ++patch)
+      for (int i = 0; i <= nel1; ++i) {
+        const int walk[4][2] = {{i, 0}, {i, nel1}, {0, i}, {nel1, i}};
+        for (const auto& w : walk) {
+          long long& id = node[patch * nn + w[0] + int64_t(nel1 + 1) * w[1]];
+          if (id >= 0) continue;
+          double x[3];
+          gamma_eval(o.geom, patch, w[0] * o.h, w[1] * o.h, x);
+          const std::array<long long, 3> key = {llround(x[0] * 1e9), llround(x[1] * 1e9), llround(x[2] * 1e9)};
+          const auto it = table.emplace(key, next);
+          if (it.second) ++next;
+          id = it.first->second;
+        }
+      }
+    for (int patch = 0; patch < 6; ++patch)
+      for (int i2 = 1; i2 < nel1; ++i2)
+        for (int i1 = 1; i1 < nel1; ++i1) node[patch * nn + i1 + int64_t(nel1 + 1) * i2] = next++;
     parallel_for(o.nelem, [&](int64_t e0, int64_t e1) {
       for (int64_t e = e0; e < e1; ++e) {
         const int patch = int(e / per_patch);
         uint32_t i1, i2;
         morton_decode(uint32_t(e % per_patch), i1, i2);
-        for (int c = 0; c < 4; ++c) {
-          double x[3];
-          gamma_eval(o.geom, patch, (i1 + (c & 1)) * o.h, (i2 + (c >> 1)) * o.h, x);
-          for (int k = 0; k < 3; ++k) keys[e * 4 + c][k] = llround(x[k] * 1e9);
-        }
+        for (int c = 0; c < 4; ++c)
+          cid[e * 4 + c] = node[patch * nn + (i1 + (c & 1)) + int64_t(nel1 + 1) * (i2 + (c >> 1))];
       }
     });
-    std::unordered_map<std::array<long long, 3>, long long, KeyHash> table;
-    table.reserve(o.nelem * 2);
-    for (int64_t k = 0; k < o.nelem * 4; ++k) {
-      auto it = table.emplace(keys[k], (long long)table.size()).first;
-      cid[k] = it->second;
-    }
   }
 
   debug_mark("setup: cluster balls on levels 0..leaf");
