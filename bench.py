@@ -35,15 +35,15 @@ sys.path.insert(0, ROOT)
 METRIC = "H² assembly time & matvec GDOF/s; GMRES time-to-1e-8 vs plain FP64 GPU path"
 WORKLOAD = dict(level=6, p=1, q=4, eta=1.6, leaf=5, g_reg=4, g_sing=5, quad_tol=1e-6, x0=(0.0, 0.0, 2.0),
                 n_eval=100)
-# FP64 flops per quadrature point (counted from the formulas):
+# FP64 flops per quadrature point, counted from the formulas:
 # regular pair point (x_p, y_q): difference, squared norm, 1/r, 4 (d=1) weighted products
 FLOPS_REG_POINT = {0: 12, 1: 18, 2: 28}
 # identical-pair Duffy point: rule map + both patch maps + 1/r + (d+1)^4 basis products
 FLOPS_SING_POINT = {0: 80, 1: 110, 2: 250}
 # one side point of the factorised edge / vertex rules: patch map + weighted Bernstein values
 FLOPS_SIDE_POINT = {0: 22, 1: 30, 2: 48}
-# DRAM bytes per separated pair of k_near_regular<1, 0> (pair record + written blocks), from the
-# ncu capture in profiles/quadrature_kernels_laplace_L5_p1.md: 28.31 MB over 254,412 pairs
+# DRAM bytes per separated pair of k_near_regular<1, 0> (pair record + written blocks), from an
+# ncu capture of the level-5 degree-1 launch: 28.31 MB over 254,412 pairs
 REGULAR_DRAM_BYTES_PER_PAIR = 28.31e6 / 254412
 
 
