@@ -62,6 +62,23 @@ def touching_pair_flops(kind, g, p):
     return npts * fk + items * (fp + fo) + (staged + moving) * fp
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """Largest value of x over the ranks of the job (x itself on one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gdofs(dofs_per_rank: int, world: int, ms: float) -> float:
+    """Dofs solved by all replicas per second (GDOF/s) at the slowest rank's step time ms."""
+    return dofs_per_rank * world / (ms / 1e3) / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,13 +311,9 @@ def main():
     barrier()
     sampler.stop()
     launches = bem.bembel_kernel_launches() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
     n1 = ndofs // args.steps
-    value = n1 * world / (ms / 1e3) / 1e9
+    value = whole_job_gdofs(n1, world, ms)
     info, opinfo = state["info"], state["opinfo"]
     exact = 1.0 / np.linalg.norm(pts_host.numpy() - np.array(w["x0"]), axis=1)
     pot_err = float(np.max(np.abs(state["u"].cpu().numpy() - exact) / exact))
@@ -315,12 +328,8 @@ def main():
         step(pts_dev=pts_step, out_host=(rho_host, u_host))
         torch.cuda.synchronize(dev)
     barrier()
-    ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": n1 * world / (ms_e2e / 1e3) / 1e9, "unit": "GDOF/s",
+    ms_e2e = reduce_max((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
+    e2e = {"value": whole_job_gdofs(n1, world, ms_e2e), "unit": "GDOF/s",
            "h2d_bytes_per_step": int(pts_host.numel() * 8 + x0.size * 8),
            "d2h_bytes_per_step": int((n1 + w["n_eval"]) * 8)}
 
