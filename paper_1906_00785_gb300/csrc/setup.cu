@@ -718,10 +718,8 @@ void build_structure(Op& o) {
     }
     o.npairs_regular_far = (int64_t)cnt[4];
     dev_free(d_v2e);
-    unsigned long long bad = 0;
     dev_free(d_cid);
     dev_free(d_cnt);
-    (void)bad;
   }
 
   debug_mark("setup: Bezier extraction");
