@@ -1,6 +1,9 @@
 """Pins of the EFIE oracle: S^1 basis (derivatives, glue, div-conformity),
 Galerkin form (complex symmetry), field evaluation (gradient term), and the
 whole chain against the Mie series of a perfectly conducting sphere."""
+import functools
+import os
+
 import numpy as np
 import pytest
 from scipy.interpolate import BSpline
@@ -184,20 +187,39 @@ def test_mie_helper_pins():
     assert np.abs(tang).max() < 1e-10
 
 
-def test_efie_converges_to_mie():
+@functools.lru_cache(maxsize=None)
+def _mie_error(L, p):
+    """Relative error of the oracle's scattered field (plane wave along z, x-polarised,
+    k = 2) at 20 points on the sphere of radius 3 against the Mie series."""
     k = 2.0
     rng = np.random.default_rng(4)
     pts = rng.standard_normal((20, 3))
     pts *= (3.0 / np.linalg.norm(pts, axis=1))[:, None]
     ref = scattered_pec(pts, k)
     einc = lambda x: np.stack([np.exp(-1j * k * x[:, 2]), 0 * x[:, 0], 0 * x[:, 0]], axis=1)  # noqa: E731
-    errs = {}
-    for L, p in [(0, 1), (1, 1), (1, 2)]:
-        sp = S1Space(Sphere6(), L, p)
-        rho = np.linalg.solve(EfieAssembler(sp, k, 4, 5).dense(), efie_rhs(sp, einc))
-        errs[(L, p)] = np.linalg.norm(efie_field(sp, rho, pts, k) - ref) / np.linalg.norm(ref)
-    assert errs[(1, 1)] < 0.1 and errs[(0, 1)] / errs[(1, 1)] > 5.0
-    assert errs[(1, 2)] < errs[(1, 1)]
+    sp = S1Space(Sphere6(), L, p)
+    rho = np.linalg.solve(EfieAssembler(sp, k, 4, 5).dense(), efie_rhs(sp, einc))
+    return np.linalg.norm(efie_field(sp, rho, pts, k) - ref) / np.linalg.norm(ref)
+
+
+def test_efie_converges_to_mie():
+    assert _mie_error(1, 1) < 0.1 and _mie_error(0, 1) / _mie_error(1, 1) > 5.0
+    assert _mie_error(1, 2) < _mie_error(1, 1)
+
+
+@pytest.mark.slow
+def test_efie_convergence_orders_of_the_paper():
+    """Observed orders of the scattered-field error under uniform refinement against
+    the orders 2P + 1 the paper prints (tests/golden/efie_convergence_orders.txt):
+    P = 1 fitted over levels 0..2 (about 2.9), P = 2 from level 1 to 2 (about 4.7,
+    level 0 is pre-asymptotic)."""
+    table = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "efie_convergence_orders.txt"))
+    order = {int(P): o for P, o in table}
+    e1 = [np.log2(_mie_error(L, 1)) for L in (0, 1, 2)]
+    slope1 = -np.polyfit([0, 1, 2], e1, 1)[0]
+    assert abs(slope1 - order[1]) < 0.5, slope1
+    slope2 = np.log2(_mie_error(1, 2) / _mie_error(2, 2))
+    assert abs(slope2 - order[2]) < 1.0, slope2
 
 
 def test_compressed_efie_converges_to_dense():
