@@ -547,15 +547,13 @@ void build_structure(Op& o) {
     for (int patch = 0; patch < 6; ++patch)
       for (int i2 = 1; i2 < nel1; ++i2)
         for (int i1 = 1; i1 < nel1; ++i1) node[patch * nn + i1 + int64_t(nel1 + 1) * i2] = next++;
-    parallel_for(o.nelem, [&](int64_t e0, int64_t e1) {
-      for (int64_t e = e0; e < e1; ++e) {
-        const int patch = int(e / per_patch);
-        uint32_t i1, i2;
-        morton_decode(uint32_t(e % per_patch), i1, i2);
-        for (int c = 0; c < 4; ++c)
-          cid[e * 4 + c] = node[patch * nn + (i1 + (c & 1)) + int64_t(nel1 + 1) * (i2 + (c >> 1))];
-      }
-    });
+    for (int64_t e = 0; e < o.nelem; ++e) {  // a table lookup per corner: cheaper than starting threads
+      const int patch = int(e / per_patch);
+      uint32_t i1, i2;
+      morton_decode(uint32_t(e % per_patch), i1, i2);
+      for (int c = 0; c < 4; ++c)
+        cid[e * 4 + c] = node[patch * nn + (i1 + (c & 1)) + int64_t(nel1 + 1) * (i2 + (c >> 1))];
+    }
   }
 
   debug_mark("setup: cluster balls on levels 0..leaf");
