@@ -67,3 +67,25 @@ def test_binding_loads_and_reports_errors(built_lib):
         bem.bembel_assemble(g, bem.BEMBEL_LAPLACE_SL, 0.0, 2, 3, 0)
     assert ei.value.code == bem.BEMBEL_EINVAL
     assert L.bembel_ndofs(None, ctypes.byref(ctypes.c_int64())) == bem.BEMBEL_EINVAL
+
+
+@pytest.mark.parametrize("kw", [dict(g_edge_var=(4, 0, 5, 3)),      # partial
+                                dict(g_edge_var=(4, 11, 11, 3)),    # above the largest order
+                                dict(g_edge_var=(4, 4, 5, 3)),      # edge rule not symmetric
+                                dict(g_vertex_var=(5, 4, 4, 3)),    # vertex rule not symmetric
+                                dict(g_regular=11), dict(eta=0.0), dict(leaf_level=7)])
+def test_assemble_rejects_bad_options_before_device_work(built_lib, kw):
+    import paper_1906_00785_gb300 as bem
+
+    g = bem.bembel_geom_create()
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_assemble(g, bem.BEMBEL_LAPLACE_SL, 0.0, 2, 1, 4, **kw)
+    assert ei.value.code == bem.BEMBEL_EINVAL
+
+
+def test_batch_rejects_empty_list(built_lib):
+    import paper_1906_00785_gb300 as bem
+
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_assemble_batch([], bem.BEMBEL_LAPLACE_SL, 1, 4)
+    assert ei.value.code == bem.BEMBEL_EINVAL
