@@ -298,6 +298,18 @@ int bembel_autotune(bembel_geom* g, int op, double k_re, double k_im, int level,
 int bembel_ndofs(const bembel_op* op, int64_t* n);
 /* Fill *info with the operator's counters. */
 int bembel_op_info_get(const bembel_op* op, bembel_op_info* info);
+/* Diagnostic read of one element-pair block of the near field as assembled:
+ * int_e int_f G(gamma(s), gamma(t)) phi_k(s) phi_l(t) dt ds in the parameter
+ * measure (App. B eq. (LS)/(HS) with the Piola lift of App. E), for the
+ * element-local tensor Bernstein polynomials of degree p on e and f, index
+ * k = k1 + (p+1) k2 with k1 along the patch's first parameter.  Elements are
+ * named by (patch, i1, i2), 0 <= i1, i2 < 2^level.  out (host) receives the
+ * (p+1)^2 x (p+1)^2 block row-major (k row, l column), interleaved complex for
+ * Helmholtz.  Synchronises the operator's stream.  S^2 operators only.
+ * Errors: EINVAL (NULL, element out of range, pair not in the near field),
+ * EUNSUPPORTED (EFIE operator), ECUDA. */
+int bembel_near_block(const bembel_op* op, int e_patch, int e_i1, int e_i2, int f_patch, int f_i1, int f_i2,
+                      double* out);
 
 /* y = A x for nrhs columns (Sec. 4.5 "H * x"): gather to element-local
  * coefficients, leaf moments, upward transfer, coupling, downward transfer,
@@ -325,22 +337,33 @@ int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs,
  * this library to a fixed, known memory footprint.  The operator (made by
  * bembel_assemble) and the x and y buffers are still the caller's inputs and
  * outputs, exactly as for bembel_matvec.
- * Scratch: a fixed array of 8 MiB compiled into the library as device memory;
- * every GPU that loads the library holds it until the process exits.  A
+ * Scratch: a fixed array of 8 MiB compiled into the library as device memory.
+ * It is part of the library's matvec module, which the CUDA runtime may load
+ * lazily; bembel_assemble and bembel_assemble_batch look the array's address up
+ * on the current device, which loads the module there, so the memory is taken
+ * at assembly and a later bembel_matvec_noalloc on that device loads and
+ * allocates nothing.  A device keeps the array until the process exits.  A
  * product needs (2 * nlocal + 2 * n_clusters * q^2) * nrhs values (x2 for
  * complex operators, 8 bytes each in FP64, 4 in FP32; counts from
  * bembel_op_info_get); larger requests are rejected with BEMBEL_EINVAL and a
  * message giving the size needed -- use bembel_matvec for them.  The level-6,
  * degree-1, q = 4 Laplace operator needs 3.7 MB per right-hand side.
- * The first call on each device looks up the array's device address (one
- * cudaGetSymbolAddress with that device current) and caches it; make that
- * first call before any stream capture.  Every call uses the same array and
+ * The address lookup (one cudaGetSymbolAddress per device, with that device
+ * current) happens at the first assembly on the device and is cached; call
+ * bembel_assemble before any stream capture.  Every call uses the same array and
  * leaves its contents behind; each call writes every scratch value before
  * reading it, so nothing carries over.  Calls that overlap on the GPU (on
  * different streams, from different threads, or from different operators)
  * race on the array and give wrong results: order them on one stream or
  * synchronise between them.
- * Arguments, layouts and the fp32 flag are those of bembel_matvec.
+ * Arguments, layouts and the fp32 flag are those of bembel_matvec.  The
+ * kernels are those of bembel_matvec with one exception: this call never
+ * builds the sibling groups of the tensor-core coupling (that would allocate),
+ * so a wide FP32 product on a MIXED operator uses the bf16 tensor cores only
+ * after a bembel_matvec or bembel_solve with as many columns has built them;
+ * before that it takes the FP32 CUDA-core coupling (results then differ from
+ * bembel_matvec's tensor-core product by the bf16 rounding, ~1e-3 of the far
+ * field).
  * Errors: EINVAL (NULL, nrhs < 1, aliasing, scratch too small, fp32 on an FP64
  * operator), ECUDA. */
 int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs, int fp32);
@@ -407,6 +430,28 @@ int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, 
  * Errors: EINVAL, ECUDA. */
 int bembel_eval(const bembel_op* op, const double* pts_dev, int64_t npts, const void* rho_dev, int nrhs, int g,
                 void* out_dev);
+
+/* The same potential through the cluster tree (Sec. 4.7 evaluated with the far-field
+ * machinery of Sec. 2) for many points: a source cluster sigma that is admissible
+ * for the point x, 2 r_sigma <= eta max(0, |x - c_sigma| - r_sigma) with the block
+ * tree's bounding balls, contributes sum_b G(x, gamma(x_b)) rhohat_sigma[b] over
+ * its q x q Chebyshev points x_b, rhohat_sigma[b] = sum_j rho_j int phi_hat_j L_b
+ * (the operator's leaf moments and upward transfers); elements of non-admissible
+ * leaf clusters take the g x g Gauss rule of bembel_eval; every other cluster is
+ * split into its children, starting from the six patches.  Work per point grows
+ * like the logarithm of the number of elements instead of linearly.  Arguments and
+ * layouts as bembel_eval; eta > 0 (the operator's eta is a good choice).  Compressed
+ * S^2 operators (q > 0) only.
+ * Errors: EINVAL (NULL, sizes, eta <= 0, a point whose cluster frontier exceeds
+ * 1024 clusters), EUNSUPPORTED (q = 0 or EFIE), ENOMEM, ECUDA. */
+int bembel_eval_h2(const bembel_op* op, const double* pts_dev, int64_t npts, const void* rho_dev, int nrhs, int g,
+                   double eta, void* out_dev);
+
+/* Evaluation points on a sphere about the origin (Sec. 5, Util::makeSphereGrid):
+ * n points on each of n circles of latitude, polar angles pi (i + 1/2) / n and
+ * azimuths 2 pi j / n; point i n + j at out_host[3 (i n + j)].  out_host: host,
+ * 3 n^2 doubles.  Errors: EINVAL (NULL, radius <= 0, n < 1 or n > 46340). */
+int bembel_sphere_grid(double radius, int n, double* out_host);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ EXPORTED = [
     "bembel_matvec", "bembel_rhs", "bembel_solve", "bembel_eval", "bembel_kernel_launches",
     "bembel_matvec_noalloc", "bembel_autotune", "bembel_learned_collect", "bembel_learned_set_destroy",
     "bembel_learned_train", "bembel_learned_attach", "bembel_mlp_eval", "bembel_tc_selftest",
-    "bembel_assemble_batch",
+    "bembel_assemble_batch", "bembel_near_block", "bembel_eval_h2", "bembel_sphere_grid",
 ]
 
 
@@ -127,6 +127,9 @@ def lib():
     L.bembel_rhs.argtypes = [vp, ci, C.POINTER(dbl), ci, ci, vp]
     L.bembel_solve.argtypes = [vp, vp, vp, ci, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]
     L.bembel_eval.argtypes = [vp, vp, i64, vp, ci, ci, vp]
+    L.bembel_near_block.argtypes = [vp, ci, ci, ci, ci, ci, ci, C.POINTER(dbl)]
+    L.bembel_eval_h2.argtypes = [vp, vp, i64, vp, ci, ci, dbl, vp]
+    L.bembel_sphere_grid.argtypes = [dbl, ci, C.POINTER(dbl)]
     for n in EXPORTED:
         if n not in ("bembel_opts_default", "bembel_solve_opts_default", "bembel_last_error",
                      "bembel_kernel_launches"):
@@ -337,6 +340,18 @@ def bembel_op_info_get(op: Operator) -> dict:
     return out
 
 
+def bembel_near_block(op: Operator, e, f) -> np.ndarray:
+    """Stored near-field block of elements e = (patch, i1, i2) and f, in the element-local
+    Bernstein basis: (nloc, nloc) float64, or complex128 for Helmholtz."""
+    info = bembel_op_info_get(op)
+    nloc = (info["degree"] + 1) ** 2
+    c = 2 if op.complex else 1
+    out = np.zeros(nloc * nloc * c)
+    _check(lib().bembel_near_block(op.handle, *[int(v) for v in e], *[int(v) for v in f],
+                                   out.ctypes.data_as(C.POINTER(C.c_double))))
+    return (out.view(np.complex128) if c == 2 else out).reshape(nloc, nloc)
+
+
 def bembel_kernel_launches() -> int:
     return int(lib().bembel_kernel_launches())
 
@@ -369,3 +384,14 @@ def bembel_solve(op: Operator, b, x, nrhs: int = 1, solve_opts: SolveOpts | None
 
 def bembel_eval(op: Operator, pts, rho, out, nrhs: int = 1, g: int = 6) -> None:
     _check(lib().bembel_eval(op.handle, _ptr(pts), pts.shape[0], _ptr(rho), nrhs, g, _ptr(out)))
+
+
+def bembel_eval_h2(op: Operator, pts, rho, out, nrhs: int = 1, g: int = 6, eta: float = 1.6) -> None:
+    _check(lib().bembel_eval_h2(op.handle, _ptr(pts), pts.shape[0], _ptr(rho), nrhs, g, eta, _ptr(out)))
+
+
+def bembel_sphere_grid(radius: float, n: int) -> np.ndarray:
+    """(n * n, 3) host array of points on the sphere of the given radius."""
+    out = np.zeros((n * n, 3))
+    _check(lib().bembel_sphere_grid(radius, n, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out

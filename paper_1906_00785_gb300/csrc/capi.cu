@@ -3,6 +3,7 @@
 // Every entry point catches the library's internal errors and turns them into
 // status codes plus a thread-local message; no exception crosses the ABI.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -45,9 +46,9 @@ int guarded(F&& f) {
 
 void free_op(Op* o) {
   if (!o) return;
-  void* ptrs[] = {o->d_far_ptr, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
+  void* ptrs[] = {o->d_far_ptr, o->d_balls, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
-                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_BW_far, o->d_nodes_jac, o->d_dofmajor,   o->d_nodes, o->d_scratch, o->d_bj,
+                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_Xq_far32, o->d_cen, o->d_BW_far, o->d_nodes_jac, o->d_dofmajor,   o->d_nodes, o->d_scratch, o->d_bj,
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
                   o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
                   o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val};
@@ -348,6 +349,7 @@ int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level,
     cuda_check(cudaEventCreate(&e0), "event");
     cuda_check(cudaEventCreate(&e1), "event");
     setup_op(*res);
+    noalloc_prepare();
     debug_mark("assemble: kernels");
     cuda_check(cudaEventRecord(e0, res->stream), "event record");
     run_assembly_kernels(*res);
@@ -381,6 +383,7 @@ int bembel_assemble_batch(int op, int p, int q, const bembel_batch_item* items, 
       ops.push_back(make_op(items[i].geom, op, items[i].k_re, items[i].k_im, items[i].level, p, q, o));
     }
     for (Op* r : ops) setup_op(*r);
+    noalloc_prepare();
     debug_mark("assemble_batch: kernels");
     cudaEvent_t e0, e1;
     cuda_check(cudaEventCreate(&e0), "event");
@@ -418,6 +421,43 @@ int bembel_ndofs(const bembel_op* op, int64_t* n) {
   return guarded([&] {
     if (!op || !n) fail(BEMBEL_EINVAL, "ndofs: NULL argument");
     *n = reinterpret_cast<const Op*>(op)->ndofs;
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_near_block(const bembel_op* op, int e_patch, int e_i1, int e_i2, int f_patch, int f_i1, int f_i2,
+                      double* out) {
+  return guarded([&] {
+    if (!op || !out) fail(BEMBEL_EINVAL, "near_block: NULL argument");
+    const Op* o = reinterpret_cast<const Op*>(op);
+    if (o->efie) fail(BEMBEL_EUNSUPPORTED, "near_block: S^2 operators only");
+    const int np = 6, nel = 1 << o->L;  // six patches (cube layout)
+    auto elem = [&](int pa, int i1, int i2) -> int64_t {
+      if (pa < 0 || pa >= np || i1 < 0 || i1 >= nel || i2 < 0 || i2 >= nel)
+        fail(BEMBEL_EINVAL, "near_block: element out of range");
+      return (int64_t)pa * nel * nel + morton_encode(uint32_t(i1), uint32_t(i2));
+    };
+    const int64_t ge = elem(e_patch, e_i1, e_i2), gf = elem(f_patch, f_i1, f_i2);
+    const int shift = 2 * (o->L - o->leaf);
+    const int64_t le = ge >> shift, lf = gf >> shift;
+    const int64_t pe = ge - (le << shift), pf = gf - (lf << shift);
+    cuda_check(cudaStreamSynchronize(o->stream), "near_block: sync");
+    long long rng[2];
+    cuda_check(cudaMemcpy(rng, o->d_near_ptr + le, sizeof(rng), cudaMemcpyDeviceToHost), "near_block: row range");
+    std::vector<int> cols(size_t(rng[1] - rng[0]));
+    if (!cols.empty())
+      cuda_check(cudaMemcpy(cols.data(), o->d_near_col + rng[0], sizeof(int) * cols.size(), cudaMemcpyDeviceToHost),
+                 "near_block: columns");
+    const auto it = std::find(cols.begin(), cols.end(), int(lf));
+    if (it == cols.end()) fail(BEMBEL_EINVAL, "near_block: the pair is not in the near field");
+    const int64_t blk = rng[0] + (it - cols.begin());
+    const int C = o->cplx ? 2 : 1;
+    const size_t pitch = sizeof(double) * C * o->nld;
+    const double* src = o->d_N + (size_t)blk * o->nld * o->nld * C + (size_t)(pe * o->nloc) * o->nld * C +
+                        (size_t)(pf * o->nloc) * C;
+    cuda_check(cudaMemcpy2D(out, sizeof(double) * C * o->nloc, src, pitch, sizeof(double) * C * o->nloc, o->nloc,
+                            cudaMemcpyDeviceToHost),
+               "near_block: copy");
     return BEMBEL_OK;
   });
 }
@@ -555,6 +595,37 @@ int bembel_eval(const bembel_op* op, const double* pts_dev, int64_t npts, const 
     if (npts > (1LL << 31) - 1 || nrhs > 65535) fail(BEMBEL_EINVAL, "eval: npts or nrhs too large");
     if (g < 1 || g > kMaxG) fail(BEMBEL_EINVAL, "eval: g must be in [1, 10]");
     eval_device(*reinterpret_cast<const Op*>(op), pts_dev, npts, rho_dev, nrhs, g, out_dev);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_eval_h2(const bembel_op* op, const double* pts_dev, int64_t npts, const void* rho_dev, int nrhs, int g,
+                   double eta, void* out_dev) {
+  return guarded([&] {
+    if (!op || !pts_dev || !rho_dev || !out_dev) fail(BEMBEL_EINVAL, "eval_h2: NULL argument");
+    if (npts < 1 || nrhs < 1) fail(BEMBEL_EINVAL, "eval_h2: npts and nrhs must be >= 1");
+    if (npts > (1LL << 31) - 1 || nrhs > 65535) fail(BEMBEL_EINVAL, "eval_h2: npts or nrhs too large");
+    if (g < 1 || g > kMaxG) fail(BEMBEL_EINVAL, "eval_h2: g must be in [1, 10]");
+    if (!(eta > 0.0)) fail(BEMBEL_EINVAL, "eval_h2: eta must be > 0");
+    eval_h2_device(*reinterpret_cast<const Op*>(op), pts_dev, npts, rho_dev, nrhs, g, eta, out_dev);
+    return BEMBEL_OK;
+  });
+}
+
+int bembel_sphere_grid(double radius, int n, double* out_host) {
+  return guarded([&] {
+    if (!out_host) fail(BEMBEL_EINVAL, "sphere_grid: NULL argument");
+    if (!(radius > 0.0) || n < 1 || n > 46340) fail(BEMBEL_EINVAL, "sphere_grid: radius > 0 and 1 <= n <= 46340");
+    for (int i = 0; i < n; ++i) {
+      const double th = M_PI * (i + 0.5) / n;
+      for (int j = 0; j < n; ++j) {
+        const double ph = 2.0 * M_PI * j / n;
+        double* p = out_host + 3 * ((int64_t)i * n + j);
+        p[0] = radius * std::sin(th) * std::cos(ph);
+        p[1] = radius * std::sin(th) * std::sin(ph);
+        p[2] = radius * std::cos(th);
+      }
+    }
     return BEMBEL_OK;
   });
 }

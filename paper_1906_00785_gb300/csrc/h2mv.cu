@@ -980,6 +980,26 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
 
 }  // namespace
 
+void cluster_moments(const Op& o, const double* x, double* xl, double* xh, int nrhs, cudaStream_t s) {
+  if (o.q2 == 0 || o.efie) fail(BEMBEL_EUNSUPPORTED, "cluster moments: compressed S^2 operators only");
+  const int C = o.cplx ? 2 : 1;
+  const int ncol = nrhs * C;
+  const int q2 = o.q2, tb = 256;
+  gather_l<double>(o, x, xl, ncol, C, s);
+  const int64_t leaf_off = o.lvl_off[o.leaf];
+  k_leaf_up<double><<<blocks_for(o.nleaf * q2 * ncol, tb), tb, sizeof(double) * o.nld * q2, s>>>(
+      xl, xh + leaf_off * q2 * ncol, o.d_V, o.nleaf, o.nld, q2, ncol);
+  launched("k_leaf_up");
+  const size_t tsh = sizeof(double) * 4 * q2 * q2;
+  for (int l = o.leaf - 1; l >= 0; --l) {
+    const int64_t np = o.lvl_off[l + 1] - o.lvl_off[l];
+    k_up<double><<<blocks_for(np * q2 * ncol, tb), tb, tsh, s>>>(xh + o.lvl_off[l] * q2 * ncol,
+                                                                  xh + o.lvl_off[l + 1] * q2 * ncol, o.d_T, np, q2,
+                                                                  ncol);
+    launched("k_up");
+  }
+}
+
 void gather_to_local(const Op& o, const double* x, double* xl, int nrhs, cudaStream_t s) {
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
@@ -1042,6 +1062,11 @@ void* noalloc_scratch_address() {
 }  // namespace
 
 size_t matvec_noalloc_limit() { return kNoAllocScratchBytes; }
+
+// Looking the address up loads this file's module (and so the fixed array) on
+// the current device when lazy module loading deferred it; assembly calls this
+// so that a later matvec_noalloc on the device has nothing left to load.
+void noalloc_prepare() { (void)noalloc_scratch_address(); }
 
 void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s) {
   const size_t need = matvec_scratch_bytes(o, nrhs, fp32);

@@ -44,6 +44,7 @@ struct Op {
   // cluster tree (levels 0..leaf), global cluster id = lvl_off[l] + patch*4^l + morton
   std::vector<int64_t> lvl_off;
   int64_t nclusters = 0;
+  double* d_balls = nullptr;  // compressed operators: (centre, radius) per cluster, 4 doubles
 
   // far field: CSR over target cluster ids
   int64_t nfar = 0;
@@ -80,6 +81,8 @@ struct Op {
   int gauss_off_far = 0;         // its [nodes][weights] in d_gauss
   int64_t npairs_regular_far = 0;
   double* d_Xq_far = nullptr;    // gamma at the far order's points
+  float* d_Xq_far32 = nullptr;   // MIXED: the same as FP32 offsets (x, y, z, 0) from the element centre
+  double* d_cen = nullptr;       // MIXED: element centres (x, y, z, 0) of those points
   double* d_nodes_jac = nullptr; // EFIE: d_s gamma, d_t gamma at the cluster points
   double* d_BW_far = nullptr;
   double* d_Xq = nullptr;  // nelem * g_reg^2 * 3
@@ -169,6 +172,7 @@ size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32);
 // same product with the fixed file-scope scratch of h2mv.cu; allocates nothing
 void matvec_noalloc(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
 size_t matvec_noalloc_limit();
+void noalloc_prepare();
 // y = E^T D^-1 E x (block-Jacobi), uses the matvec scratch
 void precond_apply(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
 // element-local helpers (h2mv.cu): gather E x, scatter E^T y, block-diagonal D^-1 x_loc
@@ -201,6 +205,12 @@ void scatter_to_global(const Op& o, const double* yl, double* y, int nrhs, cudaS
 int solve_gmres(const Op& o, const void* b, void* x, int nrhs, const bembel_solve_opts& so, bembel_solve_info* info);
 void rhs_device(const Op& o, int kind, const double* params, int nrhs, int g, void* b);
 void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, int nrhs, int g, void* out);
+// compressed evaluation (S^2 operators with q > 0): far clusters by their interpolated moments
+void eval_h2_device(const Op& o, const double* pts, int64_t npts, const void* rho, int nrhs, int g, double eta,
+                    void* out);
+// h2mv.cu: cluster moments of a global vector x (FP64): gather + leaf moments + upward
+// transfers; xl (nlocal x ncol) and xh (nclusters x q2 x ncol) are caller-provided
+void cluster_moments(const Op& o, const double* x, double* xl, double* xh, int nrhs, cudaStream_t s);
 
 // error plumbing (capi.cu)
 struct Error {

@@ -101,8 +101,107 @@ __device__ __forceinline__ void regular_pair(const PairRec& pr, const double* __
   __syncwarp();
 }
 
-inline size_t regular_smem(int G2, int G2f, int NL, int C) {
-  return sizeof(double) * ((size_t)G2 * NL + (size_t)G2f * NL + (size_t)kWarps * std::max(G2, G2f) * NL * C);
+// Single-layer kernel in FP32: 1/r and, for Helmholtz, exp(-i kappa r) / r.
+__device__ __forceinline__ void kernel_value_f(bool cplx, float r2, float kre, float kim, float& gr, float& gi) {
+  const float rinv = rsqrtf(r2);
+  if (!cplx) {
+    gr = rinv;
+    gi = 0.f;
+  } else {
+    const float r = r2 * rinv;
+    float sn, cs;
+    sincosf(kre * r, &sn, &cs);
+    const float a = (kim != 0.f ? expf(kim * r) : 1.f) * rinv;
+    gr = a * cs;
+    gi = -a * sn;
+  }
+}
+
+// Separated pair beyond the ring with the kernel in FP32 (MIXED operators):
+// points are stored as FP32 offsets from their element's centre, the centre
+// difference is taken in FP64 once per pair, so each distance is formed from
+// numbers of the size of the distance itself (relative error ~1e-7); the sum
+// over f's points runs in FP32 per point of e and everything after it in FP64,
+// as in regular_pair.  Block error ~3e-7 relative, below the quadrature target.
+template <int D, bool CPLX>
+__device__ __forceinline__ void regular_pair_f32(const PairRec& pr, const float4* __restrict__ Xq32,
+                                                 const double* __restrict__ cen, const float* __restrict__ BW32,
+                                                 const double* __restrict__ BW, double* __restrict__ ubuf, int G2,
+                                                 float kre, float kim, double* __restrict__ N, int nld, int lane) {
+  constexpr int NL = (D + 1) * (D + 1);
+  constexpr int C = CPLX ? 2 : 1;
+  const int S = G2 <= 16 ? 2 : 1;  // lanes per point p
+  const int P = 32 / S;
+  const int half = lane / P;
+  const int qlen = (G2 + S - 1) / S;
+  const float4* xe = Xq32 + (int64_t)pr.e * G2;
+  const float4* xf = Xq32 + (int64_t)pr.f * G2;
+  const float c0 = float(cen[pr.e * 4] - cen[pr.f * 4]);
+  const float c1 = float(cen[pr.e * 4 + 1] - cen[pr.f * 4 + 1]);
+  const float c2 = float(cen[pr.e * 4 + 2] - cen[pr.f * 4 + 2]);
+  for (int p0 = 0; p0 < G2; p0 += P) {
+    const int p = p0 + (lane % P);
+    float ur[NL], ui[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) ur[j] = ui[j] = 0.f;
+    if (p < G2) {
+      const float4 a = xe[p];
+      const float a0 = c0 + a.x, a1 = c1 + a.y, a2 = c2 + a.z;
+      const int qb = half * qlen, qe = min(G2, qb + qlen);
+      for (int qq = qb; qq < qe; ++qq) {
+        const float4 b = xf[qq];
+        const float d0 = a0 - b.x, d1 = a1 - b.y, d2 = a2 - b.z;
+        float gr, gi;
+        kernel_value_f(CPLX, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), kre, kim, gr, gi);
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          ur[j] = fmaf(gr, BW32[qq * NL + j], ur[j]);
+          if (CPLX) ui[j] = fmaf(gi, BW32[qq * NL + j], ui[j]);
+        }
+      }
+    }
+    if (S == 2) {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        ur[j] += __shfl_down_sync(0xffffffffu, ur[j], P);
+        if (CPLX) ui[j] += __shfl_down_sync(0xffffffffu, ui[j], P);
+      }
+    }
+    if (lane < P && p < G2) {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        ubuf[(p * NL + j) * C] = double(ur[j]);
+        if (CPLX) ubuf[(p * NL + j) * C + 1] = double(ui[j]);
+      }
+    }
+  }
+  __syncwarp();
+  for (int ij = lane; ij < NL * NL; ij += 32) {
+    const int i = ij % NL, j = ij / NL;
+    double ar = 0.0, ai = 0.0;
+    for (int p = 0; p < G2; ++p) {
+      ar = fma(BW[p * NL + i], ubuf[(p * NL + j) * C], ar);
+      if (CPLX) ai = fma(BW[p * NL + i], ubuf[(p * NL + j) * C + 1], ai);
+    }
+    ar *= kInv4Pi;
+    ai *= kInv4Pi;
+    const long long o1 = pr.off1 + (long long)i * nld + j;
+    N[o1 * C] = ar;
+    if (CPLX) N[o1 * C + 1] = ai;
+    if (pr.off2 >= 0) {
+      const long long o2 = pr.off2 + (long long)j * nld + i;
+      N[o2 * C] = ar;
+      if (CPLX) N[o2 * C + 1] = ai;
+    }
+  }
+  __syncwarp();
+}
+
+// shared memory of k_near_regular: both FP64 tables, the FP32 copy of the far
+// table (FP32 path only), per-warp inner sums
+inline size_t regular_smem(int G2, int G2f, int NL, int C, bool f32 = false) {
+  return sizeof(double) * ((size_t)G2 * NL + (size_t)G2f * NL + (size_t)kWarps * std::max(G2, G2f) * NL * C) +
+         (f32 ? sizeof(float) * (size_t)G2f * NL : 0);
 }
 
 // Separable Duffy rules.  In the common-vertex and common-edge rules (see

@@ -32,14 +32,17 @@ __global__ void k_tabulate(Geom g, int L, int64_t nelem, int G, const double* __
 }
 
 // Separated pairs: the ring next to the touching pairs (pad 0) at order G2 =
-// g^2 points per element, farther pairs (pad 1) at their own order G2f.
+// g^2 points per element, farther pairs (pad 1) at their own order G2f, with
+// the kernel in FP32 when Xqf32 is given (MIXED operators; regular_pair_f32).
 template <int D, bool CPLX>
 __global__ void __launch_bounds__(32 * kWarps) k_near_regular(const PairRec* __restrict__ pairs, int64_t npairs,
                                                               const double* __restrict__ Xq,
                                                               const double* __restrict__ BWg, int G2,
                                                               const double* __restrict__ Xqf,
                                                               const double* __restrict__ BWfg, int G2f, double kre,
-                                                              double kim, double* __restrict__ N, int nld) {
+                                                              double kim, double* __restrict__ N, int nld,
+                                                              const float4* __restrict__ Xqf32,
+                                                              const double* __restrict__ cen) {
   constexpr int NL = (D + 1) * (D + 1);
   constexpr int C = CPLX ? 2 : 1;
   extern __shared__ double sh[];
@@ -47,17 +50,40 @@ __global__ void __launch_bounds__(32 * kWarps) k_near_regular(const PairRec* __r
   double* BW = sh;                                                      // G2 * NL
   double* BWf = sh + G2 * NL;                                           // G2f * NL
   double* ubuf = BWf + G2f * NL + (threadIdx.x >> 5) * gmax * NL * C;  // per warp
+  float* BWf32 = reinterpret_cast<float*>(BWf + G2f * NL + kWarps * gmax * NL * C);  // G2f * NL (FP32 path)
   for (int i = threadIdx.x; i < G2 * NL; i += blockDim.x) BW[i] = BWg[i];
-  for (int i = threadIdx.x; i < G2f * NL; i += blockDim.x) BWf[i] = BWfg[i];
+  for (int i = threadIdx.x; i < G2f * NL; i += blockDim.x) {
+    BWf[i] = BWfg[i];
+    if (Xqf32) BWf32[i] = float(BWfg[i]);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < npairs; w += (int64_t)gridDim.x * kWarps) {
     const PairRec& pr = pairs[w];
-    if (pr.pad)
+    if (pr.pad && Xqf32)
+      regular_pair_f32<D, CPLX>(pr, Xqf32, cen, BWf32, BWf, ubuf, G2f, float(kre), float(kim), N, nld, lane);
+    else if (pr.pad)
       regular_pair<D, CPLX>(pr, Xqf, BWf, ubuf, G2f, kre, kim, N, nld, lane);
     else
       regular_pair<D, CPLX>(pr, Xq, BW, ubuf, G2, kre, kim, N, nld, lane);
   }
+}
+
+// FP32 copy of the far-order points for regular_pair_f32: per element the mean
+// of its G2 points (FP64) and each point as an FP32 offset from it.
+__global__ void k_points_f32(const double* __restrict__ Xq, int64_t nelem, int G2, float4* __restrict__ X32,
+                             double* __restrict__ cen) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nelem) return;
+  const double* x = Xq + e * G2 * 3;
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int p = 0; p < G2; ++p)
+    for (int k = 0; k < 3; ++k) c[k] += x[p * 3 + k];
+  for (int k = 0; k < 3; ++k) c[k] /= G2;
+  for (int p = 0; p < G2; ++p)
+    X32[e * G2 + p] = make_float4(float(x[p * 3] - c[0]), float(x[p * 3 + 1] - c[1]), float(x[p * 3 + 2] - c[2]), 0.f);
+  for (int k = 0; k < 3; ++k) cen[e * 4 + k] = c[k];
+  cen[e * 4 + 3] = 0.0;
 }
 
 template <int D, bool CPLX, int KIND>
@@ -111,13 +137,14 @@ void launch_pairs(Op& o, cudaEvent_t* ev) {
   const int threads = 32 * kWarps;
   if (o.npairs[kRegular] > 0) {
     const int G2f = o.g_reg_far * o.g_reg_far;
-    const size_t shm = regular_smem(G2, G2f, NL, CPLX ? 2 : 1);
+    const size_t shm = regular_smem(G2, G2f, NL, CPLX ? 2 : 1, o.d_Xq_far32 != nullptr);
     if (shm > 48 * 1024)
       cuda_check(cudaFuncSetAttribute(k_near_regular<D, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm)),
                  "smem attr");
     const int grid = int(std::min<int64_t>((o.npairs[kRegular] + kWarps - 1) / kWarps, 152 * 64));
     k_near_regular<D, CPLX><<<grid, threads, shm, s>>>(o.d_pairs[kRegular], o.npairs[kRegular], o.d_Xq, o.d_BW,
-                                                       G2, o.d_Xq_far, o.d_BW_far, G2f, o.kre, o.kim, o.d_N, o.nld);
+                                                       G2, o.d_Xq_far, o.d_BW_far, G2f, o.kre, o.kim, o.d_N, o.nld,
+                                                       reinterpret_cast<const float4*>(o.d_Xq_far32), o.d_cen);
     launched("k_near_regular");
   }
   cuda_check(cudaEventRecord(ev[2], s), "event");
@@ -152,6 +179,11 @@ void alloc_assembly_outputs(Op& o) {
   if (nK > 0) o.d_K = static_cast<double*>(dev_alloc(sizeof(double) * nK * C));
   if (o.opts.precision == BEMBEL_PREC_MIXED) {
     o.d_N32 = static_cast<float*>(dev_alloc(sizeof(float) * std::max<int64_t>(nN, 1)));
+    // FP32 kernel evaluation for separated pairs beyond the ring (S^2 operators)
+    if (!o.efie && o.npairs_regular_far > 0) {
+      o.d_Xq_far32 = static_cast<float*>(dev_alloc(sizeof(float) * 4 * o.nelem * o.g_reg_far * o.g_reg_far));
+      o.d_cen = static_cast<double*>(dev_alloc(sizeof(double) * 4 * o.nelem));
+    }
   }
 }
 
@@ -175,6 +207,11 @@ void run_assembly_kernels(Op& o) {
     k_tabulate<<<grid_for(nf, 256), 256, 0, s>>>(o.geom, o.L, o.nelem, o.g_reg_far, o.d_gauss + o.gauss_off_far, o.h,
                                                  o.d_Xq_far);
     launched("k_tabulate");
+    if (o.d_Xq_far32) {
+      k_points_f32<<<grid_for(o.nelem, 128), 128, 0, s>>>(o.d_Xq_far, o.nelem, o.g_reg_far * o.g_reg_far,
+                                                          reinterpret_cast<float4*>(o.d_Xq_far32), o.d_cen);
+      launched("k_points_f32");
+    }
   }
   cuda_check(cudaEventRecord(ev[1], s), "event");
   // A4 + A5: near field (S^1 functions for the EFIE)
@@ -266,7 +303,7 @@ void run_sample(Op& o, int kind, const PairRec* d_sample, int64_t ns, const int 
       cuda_check(cudaFuncSetAttribute(k_near_regular<D, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm)),
                  "smem attr");
     k_near_regular<D, CPLX><<<grid, threads, shm, s>>>(d_sample, ns, Xq, d_BW, G2, Xq, d_BW, G2, o.kre, o.kim, out,
-                                                       nloc);
+                                                       nloc, nullptr, nullptr);
     launched("k_near_regular");
     cuda_check(cudaStreamSynchronize(s), "sample sync");
     dev_free(Xq);

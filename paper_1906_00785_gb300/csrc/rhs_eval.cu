@@ -147,6 +147,109 @@ __global__ void k_potential(const double* __restrict__ pts, int64_t npts, const 
   }
 }
 
+// Compressed evaluation, one warp per (evaluation point, rhs column): a level-by-level
+// descent of the cluster tree from the six patch clusters.  A cluster admissible for
+// the point (2 r <= eta max(0, |x - c| - r)) adds sum_b G(x, y_b) xh[b] over its q^2
+// interpolation points y_b and moments xh; a non-admissible leaf adds its elements'
+// Gauss points directly; any other non-admissible cluster passes on its four children.
+// The frontier of one level lives in shared memory; a frontier that would exceed
+// kFront sets *err and the point is left unfinished (the host reports it).
+constexpr int kTreeWarps = 4;
+constexpr int kFront = 1024;
+
+struct TreeLevels {
+  long long off[16];
+};
+
+template <bool CPLX>
+__device__ __forceinline__ void add_kernel_sum(double x0, double x1, double x2, const double* __restrict__ Y,
+                                               const double* __restrict__ w, int64_t wstride, int n, double kre,
+                                               double kim, double& sr, double& si) {
+  for (int k = 0; k < n; ++k) {
+    const double d0 = x0 - Y[k * 3], d1 = x1 - Y[k * 3 + 1], d2 = x2 - Y[k * 3 + 2];
+    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const double rinv = rsqrt(r2);
+    const double wr = w[k * wstride];
+    if (CPLX) {
+      const double wi = w[k * wstride + 1];
+      const double rr = r2 * rinv;
+      double sn, cs;
+      sincos(kre * rr, &sn, &cs);
+      const double am = exp(kim * rr) * rinv;
+      const double gr = am * cs, gi = -am * sn;
+      sr += gr * wr - gi * wi;
+      si += gr * wi + gi * wr;
+    } else {
+      sr += rinv * wr;
+    }
+  }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(32 * kTreeWarps)
+    k_potential_tree(const double* __restrict__ pts, int64_t npts, const double* __restrict__ balls,
+                     const double* __restrict__ nodes, const double* __restrict__ xh, int q2, TreeLevels lv,
+                     int leaf, int L, const double* __restrict__ Y, const double* __restrict__ rq, int G2, int ncol,
+                     double eta, double kre, double kim, int* __restrict__ err, double* __restrict__ out) {
+  __shared__ int front[kTreeWarps][2][kFront];
+  __shared__ int count[kTreeWarps][2];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ip = blockIdx.x * (int64_t)kTreeWarps + wid;
+  if (ip >= npts) return;  // whole warps leave together
+  const int C = CPLX ? 2 : 1;
+  const int col = blockIdx.y * C;  // first real column of this rhs
+  const double x0 = pts[ip * 3], x1 = pts[ip * 3 + 1], x2 = pts[ip * 3 + 2];
+  if (lane < 6) front[wid][0][lane] = int(lv.off[0]) + lane;
+  if (lane == 0) count[wid][0] = 6;
+  __syncwarp();
+  double sr = 0.0, si = 0.0;
+  int cur = 0;
+  bool overflow = false;
+  for (int l = 0; l <= leaf; ++l) {
+    const int n = count[wid][cur];
+    if (lane == 0) count[wid][cur ^ 1] = 0;
+    __syncwarp();
+    for (int idx = lane; idx < n; idx += 32) {
+      const int c = front[wid][cur][idx];
+      const double* b = balls + (int64_t)c * 4;
+      const double e0 = x0 - b[0], e1 = x1 - b[1], e2 = x2 - b[2];
+      const double dist = fmax(0.0, sqrt(e0 * e0 + e1 * e1 + e2 * e2) - b[3]);
+      if (2.0 * b[3] <= eta * dist) {
+        add_kernel_sum<CPLX>(x0, x1, x2, nodes + (int64_t)c * q2 * 3, xh + (int64_t)c * q2 * ncol + col, ncol, q2,
+                             kre, kim, sr, si);
+      } else if (l == leaf) {
+        const int sh = 2 * (L - leaf);
+        const int64_t e0i = (int64_t(c) - lv.off[leaf]) << sh;
+        const int ne = 1 << sh;
+        add_kernel_sum<CPLX>(x0, x1, x2, Y + e0i * G2 * 3, rq + e0i * G2 * ncol + col, ncol, ne * G2, kre, kim, sr,
+                             si);
+      } else {
+        const int k = atomicAdd(&count[wid][cur ^ 1], 4);
+        if (k + 4 <= kFront) {
+          const int first = int(lv.off[l + 1] + 4 * (int64_t(c) - lv.off[l]));
+          for (int j = 0; j < 4; ++j) front[wid][cur ^ 1][k + j] = first + j;
+        } else {
+          overflow = true;
+        }
+      }
+    }
+    __syncwarp();
+    if (__any_sync(0xffffffffu, overflow)) {
+      if (lane == 0) atomicExch(err, 1);
+      return;
+    }
+    cur ^= 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) {
+    out[((int64_t)blockIdx.y * npts + ip) * C] = sr * kInv4Pi;
+    if (CPLX) out[((int64_t)blockIdx.y * npts + ip) * C + 1] = si * kInv4Pi;
+  }
+}
+
 __global__ void k_tab_points(Geom g, int L, int64_t nelem, int G, const double* __restrict__ gx, double h,
                              double* __restrict__ Y) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -286,6 +389,58 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
                                             nrhs, o.kre, o.kim, static_cast<double*>(out));
   launched("eval kernels");
   cuda_check(cudaStreamSynchronize(s), "eval sync");
+}
+
+void eval_h2_device(const Op& o, const double* pts, int64_t npts, const void* rho, int nrhs, int G, double eta,
+                    void* out) {
+  if (o.efie || o.q2 == 0) fail(BEMBEL_EUNSUPPORTED, "eval_h2: compressed S^2 operators only");
+  const cudaStream_t s = o.stream;
+  const int C = o.cplx ? 2 : 1;
+  const int ncol = nrhs * C;
+  const int G2 = G * G;
+  Buf gt(sizeof(double) * 2 * G), rl(sizeof(double) * o.nlocal * ncol), rq(sizeof(double) * o.nelem * G2 * ncol),
+      Y(sizeof(double) * o.nelem * G2 * 3), xh(sizeof(double) * o.nclusters * o.q2 * ncol), err(sizeof(int));
+  gauss_table(G, static_cast<double*>(gt.p), s);
+  const double* gx = static_cast<double*>(gt.p);
+  const double* gw = gx + G;
+  cluster_moments(o, static_cast<const double*>(rho), static_cast<double*>(rl.p), static_cast<double*>(xh.p), nrhs,
+                  s);
+  const int64_t nq = o.nelem * G2;
+  k_tab_points<<<int((nq + 255) / 256), 256, 0, s>>>(o.geom, o.L, o.nelem, G, gx, o.h, static_cast<double*>(Y.p));
+  launched("k_tab_points");
+  const int64_t nd = nq * ncol;
+  switch (o.d) {
+    case 0:
+      k_density_points<0><<<int((nd + 255) / 256), 256, 0, s>>>(static_cast<double*>(rl.p), o.nelem, G, gx, gw, o.h,
+                                                                 ncol, static_cast<double*>(rq.p));
+      break;
+    case 1:
+      k_density_points<1><<<int((nd + 255) / 256), 256, 0, s>>>(static_cast<double*>(rl.p), o.nelem, G, gx, gw, o.h,
+                                                                 ncol, static_cast<double*>(rq.p));
+      break;
+    default:
+      k_density_points<2><<<int((nd + 255) / 256), 256, 0, s>>>(static_cast<double*>(rl.p), o.nelem, G, gx, gw, o.h,
+                                                                 ncol, static_cast<double*>(rq.p));
+      break;
+  }
+  launched("k_density_points");
+  cuda_check(cudaMemsetAsync(err.p, 0, sizeof(int), s), "err clear");
+  TreeLevels lv{};
+  for (int l = 0; l <= o.leaf + 1 && l < 16; ++l) lv.off[l] = o.lvl_off[l];
+  dim3 grid(unsigned((npts + kTreeWarps - 1) / kTreeWarps), unsigned(nrhs));
+  if (o.cplx)
+    k_potential_tree<true><<<grid, 32 * kTreeWarps, 0, s>>>(
+        pts, npts, o.d_balls, o.d_nodes, static_cast<double*>(xh.p), o.q2, lv, o.leaf, o.L, static_cast<double*>(Y.p),
+        static_cast<double*>(rq.p), G2, ncol, eta, o.kre, o.kim, static_cast<int*>(err.p), static_cast<double*>(out));
+  else
+    k_potential_tree<false><<<grid, 32 * kTreeWarps, 0, s>>>(
+        pts, npts, o.d_balls, o.d_nodes, static_cast<double*>(xh.p), o.q2, lv, o.leaf, o.L, static_cast<double*>(Y.p),
+        static_cast<double*>(rq.p), G2, ncol, eta, o.kre, o.kim, static_cast<int*>(err.p), static_cast<double*>(out));
+  launched("k_potential_tree");
+  int h_err = 0;
+  cuda_check(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "err read");
+  cuda_check(cudaStreamSynchronize(s), "eval_h2 sync");
+  if (h_err) fail(BEMBEL_EINVAL, "eval_h2: cluster frontier of a point exceeds its capacity (eta too small?)");
 }
 
 }  // namespace bembel

@@ -567,10 +567,11 @@ void build_structure(Op& o) {
     if (o.leaf > 14) fail(BEMBEL_EINVAL, "assemble: leaf level above 14");
     LevelTable lt{};
     for (int l = 0; l <= o.leaf + 1; ++l) lt.off[l] = o.lvl_off[l];
-    DevBuf db(sizeof(Ball) * o.nclusters);
-    k_cluster_balls<<<int((o.nclusters + 127) / 128), 128>>>(o.geom, lt, o.nclusters, static_cast<double*>(db.p));
+    // kept on the device for the compressed potential evaluation
+    o.d_balls = static_cast<double*>(dev_alloc(sizeof(Ball) * o.nclusters));
+    k_cluster_balls<<<int((o.nclusters + 127) / 128), 128>>>(o.geom, lt, o.nclusters, o.d_balls);
     launched("k_cluster_balls");
-    cuda_check(cudaMemcpy(balls.data(), db.p, sizeof(Ball) * o.nclusters, cudaMemcpyDeviceToHost), "balls");
+    cuda_check(cudaMemcpy(balls.data(), o.d_balls, sizeof(Ball) * o.nclusters, cudaMemcpyDeviceToHost), "balls");
   }
 
   debug_mark("setup: block tree");

@@ -49,6 +49,49 @@ def test_noalloc_matches_matvec_twice(op_kind, k, level, p, q, nrhs, prec):
         assert torch.max(torch.abs(y - y_ref)).item() <= tol * torch.max(torch.abs(y_ref)).item()
 
 
+def test_noalloc_first_product_on_fresh_operator():
+    """The very first product of a freshly assembled operator is the no-allocation one (no
+    bembel_matvec before it), twice; bembel_matvec afterwards must give the same columns."""
+    geom = bem.bembel_geom_create(bem.BEMBEL_GEOM_SPHERE6)
+    op = bem.bembel_assemble(geom, bem.BEMBEL_LAPLACE_SL, 0.0, 4, 1, 4)
+    n = bem.bembel_ndofs(op)
+    xs = [torch.from_numpy(random_vector(n, seed)).cuda() for seed in (31, 32)]
+    ys = []
+    for x in xs:
+        y = torch.full_like(x, float("nan"))
+        assert _noalloc(op, x, y, 1) == bem.BEMBEL_OK, bem.lib().bembel_last_error()
+        ys.append(y)
+    torch.cuda.synchronize()
+    for x, y in zip(xs, ys):
+        y_ref = torch.empty_like(x)
+        bem.bembel_matvec(op, x, y_ref, 1)
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(y - y_ref)).item() <= 1e-13 * torch.max(torch.abs(y_ref)).item()
+
+
+def test_noalloc_compressed_efie_twice():
+    """Compressed EFIE: three moment channels per cluster in the scratch layout."""
+    geom = bem.bembel_geom_create(bem.BEMBEL_GEOM_SPHERE6)
+    op = bem.bembel_assemble(geom, bem.BEMBEL_MAXWELL_SL, 2.0, 3, 2, 4, leaf_level=2)
+    n = bem.bembel_ndofs(op)
+    for seed in (41, 42):
+        x = torch.from_numpy(np.ascontiguousarray(random_vector(n, seed, nrhs=2, complex_=True).T)).cuda()
+        y = torch.full_like(x, float("nan"))
+        assert _noalloc(op, x, y, 2) == bem.BEMBEL_OK, bem.lib().bembel_last_error()
+        y_ref = torch.empty_like(x)
+        bem.bembel_matvec(op, x, y_ref, 2)
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(y - y_ref)).item() <= 1e-13 * torch.max(torch.abs(y_ref)).item()
+    # the three channels count in the size check: a request past the fixed array is refused
+    info = bem.bembel_op_info_get(op)
+    per_rhs = 16 * (2 * info["nlocal"] + 2 * 3 * info["n_clusters"] * 16)
+    nbig = (8 << 20) // per_rhs + 1
+    xb = torch.zeros((nbig, n), dtype=torch.complex128, device="cuda")
+    yb = torch.zeros_like(xb)
+    assert _noalloc(op, xb, yb, nbig) == bem.BEMBEL_EINVAL
+    assert b"fixed buffer" in bem.lib().bembel_last_error()
+
+
 def test_noalloc_rejects_oversized_request():
     geom = bem.bembel_geom_create(bem.BEMBEL_GEOM_SPHERE6)
     op = bem.bembel_assemble(geom, bem.BEMBEL_LAPLACE_SL, 0.0, 5, 1, 4)
