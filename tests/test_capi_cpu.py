@@ -89,3 +89,17 @@ def test_batch_rejects_empty_list(built_lib):
     with pytest.raises(bem.BembelError) as ei:
         bem.bembel_assemble_batch([], bem.BEMBEL_LAPLACE_SL, 1, 4)
     assert ei.value.code == bem.BEMBEL_EINVAL
+
+
+def test_sphere_grid_matches_oracle(built_lib):
+    """bembel_sphere_grid (host code, no GPU) gives the oracle's sphere grid (Sec. 5)."""
+    import numpy as np
+
+    import paper_1906_00785_gb300 as bem
+    from oracle.potential_h2 import sphere_grid
+
+    np.testing.assert_allclose(bem.bembel_sphere_grid(6.0, 10), sphere_grid(6.0, 10), rtol=0, atol=1e-14)
+    for bad in ((0.0, 10), (1.0, 0)):
+        with pytest.raises(bem.BembelError) as ei:
+            bem.bembel_sphere_grid(*bad)
+        assert ei.value.code == bem.BEMBEL_EINVAL
