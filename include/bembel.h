@@ -131,6 +131,17 @@ typedef struct {
    * touching pairs (no element holds a corner of both); g_regular then applies
    * to the ring only.  0 = g_regular (default 0). */
   int g_regular_far;
+  /* Repetition r of every interior knot of the S^2 spline space (Sec. 4.3,
+   * Discretization(geom, pde, P, knotRepetition, L)): smoothness C^(d-r) inside a
+   * patch, d + 1 + (2^level - 1) r functions per direction, r = d + 1 gives
+   * discontinuous piecewise polynomials.  1 <= r <= p + 1; 0 = 1 (default 1).
+   * The EFIE, the learned preconditioner and bembel_assemble_batch take r = 1 only. */
+  int knot_repetition;
+  /* Helmholtz: a cluster pair is admissible only if also |kappa| max(diam) <= kdiam,
+   * so that the oscillation of exp(-i kappa r) over a far block stays within what
+   * q Chebyshev points resolve (diameters of the bounding balls; App. B eq. (HS)).
+   * 0 = no such limit (default 0). */
+  double kdiam;
 } bembel_opts;
 
 /* Counters describing an assembled operator (host struct). */
@@ -219,7 +230,7 @@ int bembel_geom_destroy(bembel_geom* g);
  *   a(j, mu) = int int G(x,y) [ j(y) . mu(x) - kappa^-2 div j(y) div mu(x) ],
  * and the perfect-conductor condition n x (E_inc + E) = 0 of (MP) reads
  * a(j, mu) = -int E_inc . mu (BEMBEL_RHS_EFIE_PLANE_WAVE builds that right-hand
- * side).  Space: S^1 of App. E, p in [1, 2] (degree p across, p-1 along each
+ * side).  Space: S^1 of App. E, p in [1, 3] (degree p across, p-1 along each
  * component), lifted by the div-conforming Piola transform, with the normal
  * component glued across patch edges.  Dofs per patch 2 (2^L+p)(2^L+p-1), minus
  * one per glued edge function: ndofs = 12 (2^L+p)(2^L+p-1) - 12 (2^L+p-1).

@@ -73,21 +73,26 @@ class Clusters:
         return self.cache[c]
 
 
-def admissible(cl: Clusters, t, s, eta: float) -> bool:
+def admissible(cl: Clusters, t, s, eta: float, kdiam: float = 0.0, kabs: float = 0.0) -> bool:
+    """max(diam) <= eta dist; for Helmholtz with kdiam > 0 also |kappa| max(diam) <= kdiam
+    (the kernel's oscillation over the block, App. B eq. (HS))."""
     ct, rt = cl.ball(t)
     cs, rs = cl.ball(s)
     dist = max(0.0, np.linalg.norm(ct - cs) - rt - rs)
-    return 2.0 * max(rt, rs) <= eta * dist
+    diam = 2.0 * max(rt, rs)
+    if kdiam > 0 and kabs * diam > kdiam:
+        return False
+    return diam <= eta * dist
 
 
-def block_tree(geom, leaf_level: int, eta: float):
+def block_tree(geom, leaf_level: int, eta: float, kdiam: float = 0.0, kabs: float = 0.0):
     """(far, near): lists of cluster pairs ((patch, lev, i1, i2), (patch, lev, i1, i2))."""
     cl = Clusters(geom, leaf_level)
     far, near = [], []
     stack = [((p, 0, 0, 0), (r, 0, 0, 0)) for p in range(geom.npatch) for r in range(geom.npatch)]
     while stack:
         t, s = stack.pop()
-        if eta > 0 and admissible(cl, t, s, eta):
+        if eta > 0 and admissible(cl, t, s, eta, kdiam, kabs):
             far.append((t, s))
         elif t[1] == leaf_level:
             near.append((t, s))
@@ -116,14 +121,15 @@ def cluster_of(space, e: int, lev: int):
 class H2Oracle:
     """Block-wise H^2 approximant on an S2Space."""
 
-    def __init__(self, space, op, kappa=0.0, q=4, eta=1.6, leaf_level=None, g_reg=4, g_sing=6):
+    def __init__(self, space, op, kappa=0.0, q=4, eta=1.6, leaf_level=None, g_reg=4, g_sing=6, kdiam=0.0):
         self.space = space
         self.q = q
         self.leaf = max(0, space.level - 1) if leaf_level is None else leaf_level
         if self.leaf > space.level:
             raise ValueError("leaf level above element level")
         self.asm = Assembler(space, op, kappa, g_reg, g_sing)
-        self.far, self.near, self.cl = block_tree(space.geom, self.leaf, eta if q > 0 else 0.0)
+        kabs = abs(kappa) if op == "helmholtz" else 0.0
+        self.far, self.near, self.cl = block_tree(space.geom, self.leaf, eta if q > 0 else 0.0, kdiam, kabs)
         self.nodes = chebyshev_nodes01(q) if q > 0 else None
         self._mom: dict = {}
         self._xhat: dict = {}
@@ -213,9 +219,12 @@ class H2Oracle:
             patch, rem = divmod(int(i), n * n)
             j2, j1 = divmod(rem, n)
             acc = 0.0
+            r_ = sp.r  # element i carries the functions r i .. r i + d
             for k2 in range(sp.d + 1):
                 for k1 in range(sp.d + 1):
-                    i1, i2 = j1 - k1, j2 - k2
+                    if (j1 - k1) % r_ or (j2 - k2) % r_:
+                        continue
+                    i1, i2 = (j1 - k1) // r_, (j2 - k2) // r_
                     if not (0 <= i1 < sp.n_el and 0 <= i2 < sp.n_el):
                         continue
                     e = sp.element_index(patch, i1, i2)

@@ -29,8 +29,10 @@ from .h2 import H2Oracle, cluster_elements
 
 
 def h2_potential(space, rho, pts, op: str, kappa: complex = 0.0, q: int = 4, eta: float = 1.6,
-                 leaf_level: int | None = None, g: int = 6) -> np.ndarray:
-    """u~(x) at every point of pts (n, 3) for the density rho (global S^2 coefficients)."""
+                 leaf_level: int | None = None, g: int = 6, kdiam: float = 0.0) -> np.ndarray:
+    """u~(x) at every point of pts (n, 3) for the density rho (global S^2 coefficients).
+    kdiam > 0 (Helmholtz): a cluster is admissible only if also |kappa| diam <= kdiam, the
+    block tree's limit on the kernel's oscillation."""
     h2 = H2Oracle(space, op, kappa, q=q, eta=eta, leaf_level=leaf_level)
     leaf = h2.leaf
     cl = h2.cl
@@ -72,7 +74,8 @@ def h2_potential(space, rho, pts, op: str, kappa: complex = 0.0, q: int = 4, eta
             c = stack.pop()
             ctr, r = cl.ball(c)
             dist = max(0.0, float(np.linalg.norm(x - ctr)) - r)
-            if 2.0 * r <= eta * dist:
+            osc_ok = not (op == "helmholtz" and kdiam > 0) or abs(kappa) * 2.0 * r <= kdiam
+            if osc_ok and 2.0 * r <= eta * dist:
                 acc = acc + green(op, kappa, x[None, :], nodes_of(c)) @ moment_of(c)
             elif c[1] == leaf:
                 for f in cluster_elements(space, c):

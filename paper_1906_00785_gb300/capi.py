@@ -52,7 +52,8 @@ class Opts(C.Structure):
                 ("g_identical", C.c_int), ("g_edge", C.c_int), ("g_vertex", C.c_int), ("bsr_chunk", C.c_int),
                 ("tensor_cores", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p), ("g_identical_var", C.c_int * 4),
-                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4), ("g_regular_far", C.c_int)]
+                ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4), ("g_regular_far", C.c_int),
+                ("knot_repetition", C.c_int), ("kdiam", C.c_double)]
 
 
 class OpInfo(C.Structure):

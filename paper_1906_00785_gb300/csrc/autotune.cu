@@ -8,7 +8,9 @@
 // * Interpolation: leaf-level far blocks are sampled; the H^2 block V K V^T
 //   (Sec. 2, kernel interpolated at q x q Chebyshev points per cluster) is
 //   compared on the host with a converged tensor-Gauss integration of the same
-//   element pairs; the smallest q with relative error <= far_tol is chosen.
+//   element pairs; far blocks on the coarser levels (larger clusters) are sampled
+//   too, by the pointwise error of the kernel interpolant; the smallest q whose
+//   worst relative error is <= far_tol is chosen.
 // * Chunk size of the block-sparse products: the fastest of a few by timing.
 #include <algorithm>
 #include <chrono>
@@ -132,6 +134,69 @@ double far_error(const Op& o, int q, const std::vector<std::pair<int, int>>& blo
   return worst;
 }
 
+// Largest relative error of the kernel interpolant sum_ab L_a(s) K_ab L_b(t) against
+// G(gamma(s), gamma(t)) over 64 seeded point pairs of each sampled far block (blocks of
+// any level, global cluster ids): the coarse levels hold the largest clusters, where an
+// oscillating Helmholtz kernel is hardest to interpolate.  Relative to the block's
+// largest |G| at the samples.
+double kernel_interp_error(const Op& o, int q, const std::vector<std::pair<int, int>>& blocks) {
+  const int q2 = q * q;
+  double worst = 0.0;
+  unsigned long long state = 0x9E3779B97F4A7C15ull;
+  auto unif = [&]() {  // splitmix64 -> [0, 1)
+    state += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return double((z ^ (z >> 31)) >> 11) * 0x1.0p-53;
+  };
+  for (const auto& bl : blocks) {
+    double pts[2][kMaxQ * kMaxQ * 3];
+    int patch[2], lev[2];
+    uint32_t jj[2][2];
+    for (int side = 0; side < 2; ++side) {
+      const int64_t c = side == 0 ? bl.first : bl.second;
+      int l = 0;
+      while (c >= o.lvl_off[l + 1]) ++l;
+      lev[side] = l;
+      const int64_t nper = int64_t(1) << (2 * l), loc = c - o.lvl_off[l];
+      patch[side] = int(loc / nper);
+      morton_decode(uint32_t(loc % nper), jj[side][0], jj[side][1]);
+      const double H = std::ldexp(1.0, -l);
+      for (int a2 = 0; a2 < q; ++a2)
+        for (int a1 = 0; a1 < q; ++a1)
+          gamma_eval(o.geom, patch[side], (jj[side][0] + chebyshev01(q, a1)) * H,
+                     (jj[side][1] + chebyshev01(q, a2)) * H, &pts[side][(a1 + q * a2) * 3]);
+    }
+    std::vector<cplx> K((size_t)q2 * q2);
+    for (int a = 0; a < q2; ++a)
+      for (int b = 0; b < q2; ++b) K[(size_t)a * q2 + b] = green_h(o, &pts[0][a * 3], &pts[1][b * 3]);
+    double num = 0.0, den = 0.0;
+    for (int smp = 0; smp < 64; ++smp) {
+      double u[2][2], x[2][3];
+      std::vector<double> La[2];
+      for (int side = 0; side < 2; ++side) {
+        u[side][0] = unif();
+        u[side][1] = unif();
+        const double H = std::ldexp(1.0, -lev[side]);
+        gamma_eval(o.geom, patch[side], (jj[side][0] + u[side][0]) * H, (jj[side][1] + u[side][1]) * H, x[side]);
+        La[side].resize(q2);
+        for (int a2 = 0; a2 < q; ++a2)
+          for (int a1 = 0; a1 < q; ++a1)
+            La[side][a1 + q * a2] = lagrange01(q, a1, u[side][0]) * lagrange01(q, a2, u[side][1]);
+      }
+      cplx ap(0.0);
+      for (int a = 0; a < q2; ++a)
+        for (int b = 0; b < q2; ++b) ap += La[0][a] * K[(size_t)a * q2 + b] * La[1][b];
+      const cplx ex = green_h(o, x[0], x[1]);
+      num = std::max(num, std::abs(ap - ex));
+      den = std::max(den, std::abs(ex));
+    }
+    if (den > 0) worst = std::max(worst, num / den);
+  }
+  return worst;
+}
+
 }  // namespace
 
 }  // namespace bembel
@@ -238,9 +303,20 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
         if (n == 0) continue;
         blocks.push_back({int(t), src[ptr[t] + (k * 31) % n]});
       }
-      if (!blocks.empty()) {
+      // far blocks of every level above the leaves: a few targets per level
+      std::vector<std::pair<int, int>> coarse;
+      for (int l = 0; l < opr.leaf; ++l) {
+        const int64_t n_l = opr.lvl_off[l + 1] - opr.lvl_off[l];
+        for (int64_t k = 0; k < 4; ++k) {
+          const int64_t t = opr.lvl_off[l] + (k * 7919) % n_l;
+          const long long n = ptr[t + 1] - ptr[t];
+          if (n > 0) coarse.push_back({int(t), src[ptr[t] + (k * 31) % n]});
+        }
+      }
+      if (!blocks.empty() || !coarse.empty()) {
         for (int qq = 2; qq <= q_max; ++qq) {
-          far_err = far_error(opr, qq, blocks);
+          far_err = std::max(blocks.empty() ? 0.0 : far_error(opr, qq, blocks),
+                             coarse.empty() ? 0.0 : kernel_interp_error(opr, qq, coarse));
           q_best = qq;
           if (far_err <= far_tol) break;
         }

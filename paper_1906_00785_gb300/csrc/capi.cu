@@ -48,7 +48,7 @@ void free_op(Op* o) {
   if (!o) return;
   void* ptrs[] = {o->d_far_ptr, o->d_balls, o->d_far_src, o->d_far_tgt, o->d_K,     o->d_K32,   o->d_near_ptr, o->d_near_col,
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
-                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_Xq_far32, o->d_cen, o->d_BW_far, o->d_nodes_jac, o->d_dofmajor,   o->d_nodes, o->d_scratch, o->d_bj,
+                  o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_Xq_far32, o->d_cen, o->d_BW_far32, o->d_BW_far, o->d_nodes_jac, o->d_dofmajor,   o->d_nodes, o->d_scratch, o->d_bj,
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
                   o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
                   o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val};
@@ -77,20 +77,6 @@ void cuda_check(cudaError_t e, const char* what) {
 }
 
 static std::atomic<long long> g_launches{0};
-// BEMBEL_SYNC_DEBUG=1 synchronises after every launch and logs progress to stderr.
-static const bool g_sync_debug = std::getenv("BEMBEL_SYNC_DEBUG") != nullptr;
-
-void debug_mark(const char* what) {
-  if (g_sync_debug) {
-    // host time since the previous marker (launches are synchronised in this mode)
-    static thread_local auto last = std::chrono::steady_clock::now();
-    const auto now = std::chrono::steady_clock::now();
-    std::fprintf(stderr, "[bembel] +%.3f ms  %s\n", std::chrono::duration<double, std::milli>(now - last).count(), what);
-    std::fflush(stderr);
-    last = now;
-  }
-}
-
 static thread_local bool t_capturing = false;
 static thread_local long long t_captured = 0;
 
@@ -118,10 +104,6 @@ void launched(const char* what) {
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cuda_check(cudaGetLastError(), what);
-  if (g_sync_debug) {
-    debug_mark(what);
-    cuda_check(cudaDeviceSynchronize(), what);
-  }
 }
 
 long long launches_total() { return g_launches.load(); }
@@ -149,6 +131,7 @@ extern "C" {
 
 void bembel_opts_default(bembel_opts* o) {
   if (!o) return;
+  std::memset(o, 0, sizeof(*o));  // every field not named below defaults to 0
   o->eta = 1.6;
   o->leaf_level = -1;
   o->g_regular = 4;
@@ -160,6 +143,7 @@ void bembel_opts_default(bembel_opts* o) {
   o->tensor_cores = 1;
   o->precision = BEMBEL_PREC_FP64;
   o->stream = nullptr;
+  o->knot_repetition = 1;
 }
 
 void bembel_solve_opts_default(bembel_solve_opts* o) {
@@ -255,7 +239,7 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
   if (op != BEMBEL_LAPLACE_SL && op != BEMBEL_HELMHOLTZ_SL && op != BEMBEL_MAXWELL_SL)
     fail(BEMBEL_EINVAL, "assemble: unknown operator");
   if (op == BEMBEL_MAXWELL_SL) {
-    if (p < 1 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: the EFIE needs the S^1 degree p in [1, 2]");
+    if (p < 1 || p > kMaxEfieDeg) fail(BEMBEL_EINVAL, "assemble: the EFIE needs the S^1 degree p in [1, 3]");
     if (q != 0 && o && o->precision == BEMBEL_PREC_MIXED)
       fail(BEMBEL_EUNSUPPORTED, "assemble: the compressed EFIE (q > 0) is FP64 only");
     if (reinterpret_cast<GeomHandle*>(g)->g.kind != BEMBEL_GEOM_SPHERE6)
@@ -263,7 +247,7 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
     if (k_re == 0.0 && k_im == 0.0) fail(BEMBEL_EINVAL, "assemble: the EFIE needs a nonzero wavenumber");
   }
   if (level < 0 || level > 10) fail(BEMBEL_EINVAL, "assemble: level must be in [0, 10]");
-  if (p < 0 || p > kMaxDeg) fail(BEMBEL_EINVAL, "assemble: degree p must be in [0, 2]");
+  if (op != BEMBEL_MAXWELL_SL && (p < 0 || p > kMaxDeg)) fail(BEMBEL_EINVAL, "assemble: degree p must be in [0, 2]");
   if (q < 0 || q > kMaxQ) fail(BEMBEL_EINVAL, "assemble: q must be in [0, 8]");
   bembel_opts opts;
   bembel_opts_default(&opts);
@@ -275,10 +259,15 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
   if (opts.precision != BEMBEL_PREC_FP64 && opts.precision != BEMBEL_PREC_MIXED)
     fail(BEMBEL_EINVAL, "assemble: unknown precision");
   if (q > 0 && !(opts.eta > 0)) fail(BEMBEL_EINVAL, "assemble: eta must be positive");
+  if (!(opts.kdiam >= 0.0)) fail(BEMBEL_EINVAL, "assemble: kdiam must be >= 0");
   if (opts.bsr_chunk < 0 || opts.bsr_chunk > 4096) fail(BEMBEL_EINVAL, "assemble: bsr_chunk must be in [0, 4096]");
   const int leaf = opts.leaf_level < 0 ? (level > 0 ? level - 1 : 0) : opts.leaf_level;
   if (leaf > level) fail(BEMBEL_EINVAL, "assemble: leaf_level above level");
+  const int rep = opts.knot_repetition == 0 ? 1 : opts.knot_repetition;
+  if (rep < 1 || rep > p + 1) fail(BEMBEL_EINVAL, "assemble: knot_repetition must be in [1, p + 1]");
+  if (rep > 1 && op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE takes knot_repetition 1");
   Op* res = new Op();
+  res->rep = rep;
   res->geom = reinterpret_cast<GeomHandle*>(g)->g;
   res->op = op;
   res->efie = op == BEMBEL_MAXWELL_SL;
@@ -330,7 +319,6 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
 
 // host set-up of one operator, timed into info.setup_ms
 void setup_op(Op& o) {
-  debug_mark("assemble: build_structure");
   const auto th0 = std::chrono::steady_clock::now();
   build_structure(o);
   o.info.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
@@ -350,7 +338,6 @@ int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level,
     cuda_check(cudaEventCreate(&e1), "event");
     setup_op(*res);
     noalloc_prepare();
-    debug_mark("assemble: kernels");
     cuda_check(cudaEventRecord(e0, res->stream), "event record");
     run_assembly_kernels(*res);
     cuda_check(cudaEventRecord(e1, res->stream), "event record");
@@ -378,13 +365,13 @@ int bembel_assemble_batch(int op, int p, int q, const bembel_batch_item* items, 
     if (n < 1 || n > kMaxBatch) fail(BEMBEL_EINVAL, "assemble_batch: n must be in [1, 64]");
     for (int i = 0; i < n; ++i) out[i] = nullptr;
     if (op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble_batch: single-layer scalar operators only");
+    if (o && o->knot_repetition > 1) fail(BEMBEL_EUNSUPPORTED, "assemble_batch: knot_repetition 1 only");
     for (int i = 0; i < n; ++i) {
       if (!items[i].geom) fail(BEMBEL_EINVAL, "assemble_batch: NULL geometry in an item");
       ops.push_back(make_op(items[i].geom, op, items[i].k_re, items[i].k_im, items[i].level, p, q, o));
     }
     for (Op* r : ops) setup_op(*r);
     noalloc_prepare();
-    debug_mark("assemble_batch: kernels");
     cudaEvent_t e0, e1;
     cuda_check(cudaEventCreate(&e0), "event");
     cuda_check(cudaEventCreate(&e1), "event");

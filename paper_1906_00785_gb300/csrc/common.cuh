@@ -18,6 +18,7 @@ namespace bembel {
 
 constexpr double kInv4Pi = 0.079577471545947667884441881686257181;  // 1/(4 pi)
 constexpr int kMaxDeg = 2;                                           // ansatz degree d <= 2
+constexpr int kMaxEfieDeg = 3;                                       // S^1 degree p <= 3 (EFIE)
 constexpr int kMaxQ = 8;                                             // interpolation points per direction
 constexpr int kMaxG = 10;                                            // Gauss points per variable
 constexpr int kMaxBatch = 64;                                        // meshes per batched assembly

@@ -44,13 +44,28 @@ __device__ __forceinline__ void bern_d(double u, double b[D + 1], double db[D + 
     b[1] = u;
     db[0] = -1.0;
     db[1] = 1.0;
-  } else {
+  } else if (D == 2) {
     b[0] = v * v;
     b[1] = 2.0 * u * v;
     b[2] = u * u;
     db[0] = -2.0 * v;
     db[1] = 2.0 * (v - u);
     db[2] = 2.0 * u;
+  } else {
+    // degree D from degree D - 1 (de Casteljau's recursion b_k = u b'_{k-1} + v b'_k of the
+    // degree-(D-1) values b'); derivative D (b'_{k-1} - b'_k)
+    double lo[D + 1];
+    lo[0] = 1.0;
+    for (int r = 1; r < D; ++r) {
+      lo[r] = u * lo[r - 1];
+      for (int k = r - 1; k >= 1; --k) lo[k] = u * lo[k - 1] + v * lo[k];
+      lo[0] = v * lo[0];
+    }
+    for (int k = 0; k <= D; ++k) {
+      const double left = k >= 1 ? lo[k - 1] : 0.0, right = k <= D - 1 ? lo[k] : 0.0;
+      b[k] = u * left + v * right;
+      db[k] = D * (left - right);
+    }
   }
 }
 
@@ -133,11 +148,15 @@ __global__ void __launch_bounds__(32 * kEfieWarps) k_efie_pairs(const PairRec* _
     morton_decode(uint32_t(pr.e % per), e1, e2);
     morton_decode(uint32_t(pr.f % per), f1, f2);
     const int ce = (pr.code >> 2) & 7, cf = (pr.code >> 5) & 7;
-    for (int quad = 0; quad < 4; ++quad) {
+    // rows of the (NH x NH) quadrant block in passes of IB rows: the accumulators
+    // stay in registers for P = 3 (NH = 12) at the price of re-evaluating the kernel
+    constexpr int IB = P <= 2 ? NH : 4;
+    for (int pass = 0; pass < 4 * (NH / IB); ++pass) {
+      const int quad = pass % 4, ib0 = (pass / 4) * IB;
       const int al = quad & 1, be = quad >> 1;
-      double ar[NH * NH], ai[NH * NH];
+      double ar[IB * NH], ai[IB * NH];
 #pragma unroll
-      for (int k = 0; k < NH * NH; ++k) ar[k] = ai[k] = 0.0;
+      for (int k = 0; k < IB * NH; ++k) ar[k] = ai[k] = 0.0;
       for (int idx = lane; idx < npts; idx += 32) {
         int sub, i0, i1, i2, i3;
         rule_index(idx, G, sub, i0, i1, i2, i3);
@@ -175,21 +194,21 @@ __global__ void __launch_bounds__(32 * kEfieWarps) k_efie_pairs(const PairRec* _
         comp_factors<P>(al, ls1, ls2, fs);
         comp_factors<P>(be, lt1, lt2, ft);
 #pragma unroll
-        for (int i = 0; i < NH; ++i) {
+        for (int ii = 0; ii < IB; ++ii) {
           double bi, di;
-          comp_fun<P>(al, i, fs, bi, di);
+          comp_fun<P>(al, ib0 + ii, fs, bi, di);
 #pragma unroll
           for (int j = 0; j < NH; ++j) {
             double bj, dj;
             comp_fun<P>(be, j, ft, bj, dj);
             const double bb = bi * bj, dd = di * dj;
-            ar[i * NH + j] = fma(Pr, bb, fma(Qr, dd, ar[i * NH + j]));
-            ai[i * NH + j] = fma(Pi, bb, fma(Qi, dd, ai[i * NH + j]));
+            ar[ii * NH + j] = fma(Pr, bb, fma(Qr, dd, ar[ii * NH + j]));
+            ai[ii * NH + j] = fma(Pi, bb, fma(Qi, dd, ai[ii * NH + j]));
           }
         }
       }
 #pragma unroll
-      for (int k = 0; k < NH * NH; ++k) {
+      for (int k = 0; k < IB * NH; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
@@ -197,9 +216,9 @@ __global__ void __launch_bounds__(32 * kEfieWarps) k_efie_pairs(const PairRec* _
         }
       }
       const double sc = kInv4Pi * h * h * h * h;
-      const int io = al * NH, jo = be * NH;
+      const int io = al * NH + ib0, jo = be * NH;
 #pragma unroll
-      for (int k = 0; k < NH * NH; ++k) {
+      for (int k = 0; k < IB * NH; ++k) {
         if ((k & 31) != lane) continue;
         const int i = io + k / NH, j = jo + k % NH;
         const long long o1 = pr.off1 + (long long)i * nld + j;
@@ -488,8 +507,10 @@ void launch_efie_pairs(Op& o, cudaEvent_t* ev) {
 void efie_pair_kernels(Op& o, cudaEvent_t* ev) {
   if (o.d == 1)
     launch_efie_pairs<1>(o, ev);
-  else
+  else if (o.d == 2)
     launch_efie_pairs<2>(o, ev);
+  else
+    launch_efie_pairs<3>(o, ev);
 }
 
 void efie_coupling_assemble(Op& o) {
@@ -513,8 +534,10 @@ void efie_rhs_local(const Op& o, const double* gx, const double* gw, int G, cons
   const int grid = int((n + 127) / 128);
   if (o.d == 1)
     k_efie_rhs_local<1><<<grid, 128, 0, s>>>(o.L, o.nelem, G, gx, gw, prm_dev, nrhs, o.kre, o.kim, bl);
-  else
+  else if (o.d == 2)
     k_efie_rhs_local<2><<<grid, 128, 0, s>>>(o.L, o.nelem, G, gx, gw, prm_dev, nrhs, o.kre, o.kim, bl);
+  else
+    k_efie_rhs_local<3><<<grid, 128, 0, s>>>(o.L, o.nelem, G, gx, gw, prm_dev, nrhs, o.kre, o.kim, bl);
   launched("k_efie_rhs_local");
 }
 
@@ -526,8 +549,11 @@ void efie_field(const Op& o, const double* rl, const double* gx, const double* g
   if (o.d == 1)
     k_efie_density<1><<<grid, 128, 0, s>>>(rl, o.L, o.nelem, G, gx, gw, nrhs, static_cast<double*>(Y.p),
                                            static_cast<double*>(J.p));
-  else
+  else if (o.d == 2)
     k_efie_density<2><<<grid, 128, 0, s>>>(rl, o.L, o.nelem, G, gx, gw, nrhs, static_cast<double*>(Y.p),
+                                           static_cast<double*>(J.p));
+  else
+    k_efie_density<3><<<grid, 128, 0, s>>>(rl, o.L, o.nelem, G, gx, gw, nrhs, static_cast<double*>(Y.p),
                                            static_cast<double*>(J.p));
   launched("k_efie_density");
   if (npts > 0) {

@@ -236,7 +236,7 @@ static thread_local bool t_no_alloc = false;
 template <typename T>
 T* dofmajor_buffer(const Op& o, int ncol) {
   const size_t bytes = sizeof(T) * (size_t)o.ndofs * ncol;
-  if (o.efie || ncol < 32) return nullptr;
+  if (o.d_e_ptr || ncol < 32) return nullptr;  // CSR extraction: no dof-major path
   if (o.dofmajor_bytes < bytes) {
     if (capturing() || t_no_alloc) return nullptr;
     ensure_dofmajor(const_cast<Op&>(o), bytes);
@@ -254,7 +254,7 @@ void gather_l(const Op& o, const T* x, T* xl, int ncol, int C, cudaStream_t s) {
     launched("k_gather_dm");
     return;
   }
-  if (o.efie)
+  if (o.d_e_ptr)
     k_csr_gather<T><<<blocks_for(o.nlocal * ncol, 256), 256, 0, s>>>(o.d_e_ptr, o.d_e_col, o.d_e_val, x, xl,
                                                                       o.ndofs, o.nlocal, ncol, C);
   else
@@ -273,7 +273,7 @@ void scatter_l(const Op& o, const T* yl, T* y, int ncol, int C, cudaStream_t s) 
     launched("k_from_dofmajor");
     return;
   }
-  if (o.efie)
+  if (o.d_e_ptr)
     k_csr_scatter<T><<<blocks_for(o.ndofs * ncol, 256), 256, 0, s>>>(o.d_et_ptr, o.d_et_col, o.d_et_val, yl, y,
                                                                       o.ndofs, ncol, C);
   else
@@ -862,6 +862,8 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     T* yhe = xh + o.nclusters * q2 * nch;
     const int64_t leaf_off = o.lvl_off[o.leaf];
     const size_t tsh = sizeof(T) * 4 * q2 * q2;
+    set_smem_limit(k_up<T>, tsh);  // q >= 7: the four transfer matrices exceed 48 KiB
+    set_smem_limit(k_down<T>, tsh);
     k_leaf_up_ch<<<blocks_for(o.nleaf * q2 * nch, tb), tb, 0, s>>>(
         reinterpret_cast<const double*>(xl), reinterpret_cast<double*>(xhe + leaf_off * q2 * nch),
         reinterpret_cast<const double*>(V), o.nleaf, o.nld, q2, ncol);
@@ -889,6 +891,8 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     const int nsub = 1 << (2 * (o.leaf - ls));
     const size_t sub_shm = sizeof(T) * ((size_t)o.nld * q2 + 4 * q2 * q2 + 2 * (size_t)nsub * q2 * ncol);
     const size_t tsh = sizeof(T) * 4 * q2 * q2;
+    set_smem_limit(k_up<T>, tsh);  // q >= 7: the four transfer matrices exceed 48 KiB
+    set_smem_limit(k_down<T>, tsh);
     const bool fused = sub_shm <= 96 * 1024 && o.leaf < 15;
     LevelOffsets lo{};
     for (int l = 0; l <= std::min(o.leaf, 14); ++l) lo.off[l] = o.lvl_off[l];
@@ -991,6 +995,7 @@ void cluster_moments(const Op& o, const double* x, double* xl, double* xh, int n
       xl, xh + leaf_off * q2 * ncol, o.d_V, o.nleaf, o.nld, q2, ncol);
   launched("k_leaf_up");
   const size_t tsh = sizeof(double) * 4 * q2 * q2;
+  set_smem_limit(k_up<double>, tsh);
   for (int l = o.leaf - 1; l >= 0; --l) {
     const int64_t np = o.lvl_off[l + 1] - o.lvl_off[l];
     k_up<double><<<blocks_for(np * q2 * ncol, tb), tb, tsh, s>>>(xh + o.lvl_off[l] * q2 * ncol,

@@ -259,6 +259,7 @@ void mlp_backward(const float* P_dev, const float* F, const float* gw, int64_t n
 }
 
 LearnedSet* learned_collect(Op& src, int ns, unsigned long long seed) {
+  if (src.rep != 1) fail(BEMBEL_EUNSUPPORTED, "learned preconditioner: knot_repetition 1 only");
   precond_setup(src);
   auto* S = new LearnedSet();
   Op& o = S->o;

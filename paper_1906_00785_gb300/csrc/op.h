@@ -33,6 +33,7 @@ struct Op {
   bool cplx = false;   // Helmholtz
   double kre = 0, kim = 0;
   int L = 0, d = 0, q = 0, leaf = 0;
+  int rep = 1;         // knot repetition of the S^2 space; > 1: CSR extraction (d_e_*)
   int nloc = 1, n1 = 1, nel1 = 1, q2 = 0;
   int m = 1;           // elements per leaf side
   int nld = 1;         // local dofs per leaf cluster (m*m*nloc)
@@ -83,6 +84,7 @@ struct Op {
   double* d_Xq_far = nullptr;    // gamma at the far order's points
   float* d_Xq_far32 = nullptr;   // MIXED: the same as FP32 offsets (x, y, z, 0) from the element centre
   double* d_cen = nullptr;       // MIXED: element centres (x, y, z, 0) of those points
+  float* d_BW_far32 = nullptr;   // MIXED: FP32 copy of d_BW_far
   double* d_nodes_jac = nullptr; // EFIE: d_s gamma, d_t gamma at the cluster points
   double* d_BW_far = nullptr;
   double* d_Xq = nullptr;  // nelem * g_reg^2 * 3
@@ -92,7 +94,8 @@ struct Op {
   double* d_nodes = nullptr;  // nclusters * q2 * 3 cluster interpolation points
   float* d_nodes32 = nullptr; // FP32 copy (x, y, z, 0) per point for the on-the-fly FP32 coupling
 
-  // EFIE on the S^1 space: signed extraction E (element-local <- global) as CSR and its transpose
+  // EFIE on the S^1 space, or S^2 with knot repetition > 1: extraction E (element-local
+  // <- global, signed for S^1) as CSR and its transpose; set means "CSR mode"
   bool efie = false;
   int* d_e_ptr = nullptr;
   int* d_e_col = nullptr;
@@ -152,6 +155,8 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
 // quad.cu
 void run_assembly_kernels(Op& o);       // tabulation, near field, coupling
 void alloc_assembly_outputs(Op& o);     // Xq, near field, coupling, FP32 near copy
+// MIXED: FP32 points (offsets from element centres) and weights of the far separated order
+void points_f32(Op& o, cudaStream_t s);
 // several operators sharing (op, degree, q, options): tabulation, one
 // persistent launch for all near-field pairs and coupling blocks, FP32 copies
 void run_assembly_batch(const std::vector<Op*>& ops);
@@ -221,8 +226,6 @@ struct Error {
 void cuda_check(cudaError_t e, const char* what);
 // check the launch that was just issued and count it
 void launched(const char* what);
-// progress marker on stderr when BEMBEL_SYNC_DEBUG is set
-void debug_mark(const char* what);
 // stream capture of a CUDA graph on this thread; capture_end returns the
 // number of kernels captured (launch accounting adds them per replay)
 void capture_begin(cudaStream_t s);

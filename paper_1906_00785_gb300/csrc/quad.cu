@@ -169,6 +169,16 @@ void launch_pairs(Op& o, cudaEvent_t* ev) {
 
 }  // namespace
 
+void points_f32(Op& o, cudaStream_t s) {
+  if (!o.d_Xq_far32) return;
+  const int G2f = o.g_reg_far * o.g_reg_far;
+  k_points_f32<<<grid_for(o.nelem, 128), 128, 0, s>>>(o.d_Xq_far, o.nelem, G2f,
+                                                      reinterpret_cast<float4*>(o.d_Xq_far32), o.d_cen);
+  launched("k_points_f32");
+  k_to_f32<float><<<1, 256, 0, s>>>(o.d_BW_far, o.d_BW_far32, int64_t(G2f) * o.nloc);
+  launched("k_to_f32");
+}
+
 void alloc_assembly_outputs(Op& o) {
   const int C = o.cplx ? 2 : 1;
   const int64_t nN = o.nnear * (int64_t)o.nld * o.nld * C;
@@ -181,8 +191,10 @@ void alloc_assembly_outputs(Op& o) {
     o.d_N32 = static_cast<float*>(dev_alloc(sizeof(float) * std::max<int64_t>(nN, 1)));
     // FP32 kernel evaluation for separated pairs beyond the ring (S^2 operators)
     if (!o.efie && o.npairs_regular_far > 0) {
-      o.d_Xq_far32 = static_cast<float*>(dev_alloc(sizeof(float) * 4 * o.nelem * o.g_reg_far * o.g_reg_far));
+      const int64_t G2f = int64_t(o.g_reg_far) * o.g_reg_far;
+      o.d_Xq_far32 = static_cast<float*>(dev_alloc(sizeof(float) * 4 * o.nelem * G2f));
       o.d_cen = static_cast<double*>(dev_alloc(sizeof(double) * 4 * o.nelem));
+      o.d_BW_far32 = static_cast<float*>(dev_alloc(sizeof(float) * G2f * o.nloc));
     }
   }
 }
@@ -207,11 +219,7 @@ void run_assembly_kernels(Op& o) {
     k_tabulate<<<grid_for(nf, 256), 256, 0, s>>>(o.geom, o.L, o.nelem, o.g_reg_far, o.d_gauss + o.gauss_off_far, o.h,
                                                  o.d_Xq_far);
     launched("k_tabulate");
-    if (o.d_Xq_far32) {
-      k_points_f32<<<grid_for(o.nelem, 128), 128, 0, s>>>(o.d_Xq_far, o.nelem, o.g_reg_far * o.g_reg_far,
-                                                          reinterpret_cast<float4*>(o.d_Xq_far32), o.d_cen);
-      launched("k_points_f32");
-    }
+    points_f32(o, s);
   }
   cuda_check(cudaEventRecord(ev[1], s), "event");
   // A4 + A5: near field (S^1 functions for the EFIE)

@@ -1,4 +1,5 @@
-// quad_batch.cu - assembly of several meshes in one persistent launch (FP64).
+// quad_batch.cu - assembly of several meshes in one persistent launch (FP64; for MIXED
+// operators the separated pairs beyond the ring in FP32, as in quad.cu).
 #include <algorithm>
 #include <vector>
 
@@ -28,6 +29,9 @@ struct MeshWork {
   const double* BW;  // regular basis x weight table (holds h^2: per level)
   const double* BWf; // the same for the far separated order
   double* Xqf;
+  const float4* Xqf32;  // MIXED: FP32 far-order points (regular_pair_f32), else null
+  const double* cen;
+  const float* BWf32;
   double kre, kim, h;
   int64_t nelem;
   double* Xq;
@@ -98,7 +102,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_assemble_multi(const MeshWork* 
     switch (sg.phase) {
       case kRegular:
         for (long long w = first; w < last; ++w)
-          if (m.pairs[kRegular][w].pad)
+          if (m.pairs[kRegular][w].pad && m.Xqf32)
+            regular_pair_f32<D, CPLX>(m.pairs[kRegular][w], m.Xqf32, m.cen, m.BWf32, m.BWf, ubuf, G2f, float(m.kre),
+                                      float(m.kim), m.N, m.nld, lane);
+          else if (m.pairs[kRegular][w].pad)
             regular_pair<D, CPLX>(m.pairs[kRegular][w], m.Xqf, m.BWf, ubuf, G2f, m.kre, m.kim, m.N, m.nld, lane);
           else
             regular_pair<D, CPLX>(m.pairs[kRegular][w], m.Xq, m.BW, ubuf, G2, m.kre, m.kim, m.N, m.nld, lane);
@@ -178,6 +185,9 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
     w.BW = o.d_BW;
     w.BWf = o.d_BW_far;
     w.Xqf = o.d_Xq_far;
+    w.Xqf32 = reinterpret_cast<const float4*>(o.d_Xq_far32);
+    w.cen = o.d_cen;
+    w.BWf32 = o.d_BW_far32;
     w.kre = o.kre;
     w.kim = o.kim;
     w.h = o.h;
@@ -239,6 +249,7 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
                                                                    nmesh, o0.g_reg_far, o0.d_gauss + o0.gauss_off_far,
                                                                    true);
   launched("k_tabulate_multi");
+  for (Op* o : ops) points_f32(*o, s);
   cuda_check(cudaEventRecord(ev[1], s), "event");
   if (nitems > 0) {
     const Segment* d_seg = static_cast<const Segment*>(dseg.p);

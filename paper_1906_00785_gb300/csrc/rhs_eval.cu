@@ -149,7 +149,8 @@ __global__ void k_potential(const double* __restrict__ pts, int64_t npts, const 
 
 // Compressed evaluation, one warp per (evaluation point, rhs column): a level-by-level
 // descent of the cluster tree from the six patch clusters.  A cluster admissible for
-// the point (2 r <= eta max(0, |x - c| - r)) adds sum_b G(x, y_b) xh[b] over its q^2
+// the point (2 r <= eta max(0, |x - c| - r), and |kappa| 2 r <= kdiam when the
+// operator sets that Helmholtz limit) adds sum_b G(x, y_b) xh[b] over its q^2
 // interpolation points y_b and moments xh; a non-admissible leaf adds its elements'
 // Gauss points directly; any other non-admissible cluster passes on its four children.
 // The frontier of one level lives in shared memory; a frontier that would exceed
@@ -190,7 +191,8 @@ __global__ void __launch_bounds__(32 * kTreeWarps)
     k_potential_tree(const double* __restrict__ pts, int64_t npts, const double* __restrict__ balls,
                      const double* __restrict__ nodes, const double* __restrict__ xh, int q2, TreeLevels lv,
                      int leaf, int L, const double* __restrict__ Y, const double* __restrict__ rq, int G2, int ncol,
-                     double eta, double kre, double kim, int* __restrict__ err, double* __restrict__ out) {
+                     double eta, double kdiam, double kre, double kim, int* __restrict__ err,
+                     double* __restrict__ out) {
   __shared__ int front[kTreeWarps][2][kFront];
   __shared__ int count[kTreeWarps][2];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -214,7 +216,8 @@ __global__ void __launch_bounds__(32 * kTreeWarps)
       const double* b = balls + (int64_t)c * 4;
       const double e0 = x0 - b[0], e1 = x1 - b[1], e2 = x2 - b[2];
       const double dist = fmax(0.0, sqrt(e0 * e0 + e1 * e1 + e2 * e2) - b[3]);
-      if (2.0 * b[3] <= eta * dist) {
+      const bool osc_ok = !(CPLX && kdiam > 0.0) || hypot(kre, kim) * 2.0 * b[3] <= kdiam;
+      if (osc_ok && 2.0 * b[3] <= eta * dist) {
         add_kernel_sum<CPLX>(x0, x1, x2, nodes + (int64_t)c * q2 * 3, xh + (int64_t)c * q2 * ncol + col, ncol, q2,
                              kre, kim, sr, si);
       } else if (l == leaf) {
@@ -431,11 +434,13 @@ void eval_h2_device(const Op& o, const double* pts, int64_t npts, const void* rh
   if (o.cplx)
     k_potential_tree<true><<<grid, 32 * kTreeWarps, 0, s>>>(
         pts, npts, o.d_balls, o.d_nodes, static_cast<double*>(xh.p), o.q2, lv, o.leaf, o.L, static_cast<double*>(Y.p),
-        static_cast<double*>(rq.p), G2, ncol, eta, o.kre, o.kim, static_cast<int*>(err.p), static_cast<double*>(out));
+        static_cast<double*>(rq.p), G2, ncol, eta, o.opts.kdiam, o.kre, o.kim, static_cast<int*>(err.p),
+        static_cast<double*>(out));
   else
     k_potential_tree<false><<<grid, 32 * kTreeWarps, 0, s>>>(
         pts, npts, o.d_balls, o.d_nodes, static_cast<double*>(xh.p), o.q2, lv, o.leaf, o.L, static_cast<double*>(Y.p),
-        static_cast<double*>(rq.p), G2, ncol, eta, o.kre, o.kim, static_cast<int*>(err.p), static_cast<double*>(out));
+        static_cast<double*>(rq.p), G2, ncol, eta, o.opts.kdiam, o.kre, o.kim, static_cast<int*>(err.p),
+        static_cast<double*>(out));
   launched("k_potential_tree");
   int h_err = 0;
   cuda_check(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "err read");

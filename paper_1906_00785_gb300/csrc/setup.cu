@@ -80,14 +80,15 @@ double bernstein_h(int d, int k, double u) {
 
 namespace {
 
-// Cox-de Boor on the open knot vector of degree d with n_el uniform elements;
-// value of B-spline j at x in [0,1] (x = 1 belongs to the last interval).
-double bspline_h(int d, int n_el, int j, double x) {
-  const int nk = n_el + 2 * d + 1;
+// Cox-de Boor on the open knot vector of degree d with n_el uniform elements and
+// every interior knot repeated rep times; value of B-spline j at x in [0,1]
+// (x = 1 belongs to the last interval).
+double bspline_h(int d, int n_el, int j, double x, int rep = 1) {
+  const int nk = 2 * (d + 1) + (n_el - 1) * rep;
   std::vector<double> kn(nk);
   for (int i = 0; i < nk; ++i) {
-    const int t = i - d;
-    kn[i] = t <= 0 ? 0.0 : (t >= n_el ? 1.0 : double(t) / n_el);
+    const int t = i - (d + 1);  // interior knot number t / rep + 1
+    kn[i] = t < 0 ? 0.0 : (t >= (n_el - 1) * rep ? 1.0 : double(t / rep + 1) / n_el);
   }
   std::vector<double> b(nk - 1, 0.0);
   int last = 0;
@@ -134,10 +135,11 @@ T* upload(const std::vector<T>& v) {
 }
 
 // 1-D Bezier extraction of the open-knot B-splines of degree deg with nel1
-// uniform elements: B-spline (i + j) restricted to element i equals
-// sum_k ex[(i (deg+1) + j) (deg+1) + k] Bern_k((x - x_i) nel1), found by
-// interpolation at deg + 1 interior points of the element.
-std::vector<double> extraction_1d(int deg, int nel1) {
+// uniform elements and interior knots repeated rep times: B-spline (rep i + j)
+// restricted to element i equals sum_k ex[(i (deg+1) + j) (deg+1) + k]
+// Bern_k((x - x_i) nel1), found by interpolation at deg + 1 interior points of
+// the element.
+std::vector<double> extraction_1d(int deg, int nel1, int rep = 1) {
   const int n = deg + 1;
   std::vector<double> ex((size_t)nel1 * n * n);
   std::vector<double> A(n * (n + 1)), sol;
@@ -146,7 +148,7 @@ std::vector<double> extraction_1d(int deg, int nel1) {
       for (int r = 0; r < n; ++r) {
         const double u = (r + 0.5) / n;
         for (int k = 0; k < n; ++k) A[r * (n + 1) + k] = bernstein_h(deg, k, u);
-        A[r * (n + 1) + n] = bspline_h(deg, nel1, i + j, (i + u) / nel1);
+        A[r * (n + 1) + n] = bspline_h(deg, nel1, rep * i + j, (i + u) / nel1, rep);
       }
       solve_small(n, A, sol);
       for (int k = 0; k < n; ++k) ex[((size_t)i * n + j) * n + k] = sol[k];
@@ -497,6 +499,54 @@ __global__ void k_build_pairs(const long long* __restrict__ nptr, const int* __r
   out[slot_out] = pr;
 }
 
+// S^2 with knot repetition r > 1: the tensor extraction as CSR, element-local
+// function (e, k1 + (d+1) k2) <- global (patch, r i1 + j1, r i2 + j2) with
+// coefficient ex[i1][j1][k1] ex[i2][j2][k2], and its transpose.
+void build_s2_csr(Op& o) {
+  const int d = o.d, D1 = d + 1, nel1 = 1 << o.L, n1 = o.n1, r = o.rep;
+  const std::vector<double> ex = extraction_1d(d, nel1, r);
+  const int64_t per = int64_t(nel1) * nel1;
+  std::vector<int> rptr(o.nlocal + 1, 0), rcol;
+  std::vector<double> rval;
+  for (int64_t e = 0; e < o.nelem; ++e) {
+    const int P = int(e / per);
+    uint32_t i1, i2;
+    morton_decode(uint32_t(e % per), i1, i2);
+    for (int k = 0; k < o.nloc; ++k) {
+      const int k1 = k % D1, k2 = k / D1;
+      for (int j2 = 0; j2 < D1; ++j2) {
+        const double c2 = ex[((size_t)i2 * D1 + j2) * D1 + k2];
+        if (c2 == 0.0) continue;
+        for (int j1 = 0; j1 < D1; ++j1) {
+          const double c1 = ex[((size_t)i1 * D1 + j1) * D1 + k1];
+          if (c1 == 0.0) continue;
+          rcol.push_back(int((int64_t)P * n1 * n1 + (int64_t)(r * i2 + j2) * n1 + (r * i1 + j1)));
+          rval.push_back(c1 * c2);
+        }
+      }
+      rptr[e * o.nloc + k + 1] = int(rcol.size());
+    }
+  }
+  const int64_t n = o.ndofs;
+  std::vector<int> tptr(n + 1, 0), tcol(rcol.size());
+  std::vector<double> tval(rcol.size());
+  for (int c : rcol) ++tptr[c + 1];
+  for (int64_t g = 0; g < n; ++g) tptr[g + 1] += tptr[g];
+  std::vector<int> fill(tptr.begin(), tptr.end() - 1);
+  for (int64_t row = 0; row < o.nlocal; ++row)
+    for (int k = rptr[row]; k < rptr[row + 1]; ++k) {
+      const int at = fill[rcol[k]]++;
+      tcol[at] = int(row);
+      tval[at] = rval[k];
+    }
+  o.d_e_ptr = upload(rptr);
+  o.d_e_col = upload(rcol);
+  o.d_e_val = upload(rval);
+  o.d_et_ptr = upload(tptr);
+  o.d_et_col = upload(tcol);
+  o.d_et_val = upload(tval);
+}
+
 }  // namespace
 
 void build_structure(Op& o) {
@@ -507,11 +557,12 @@ void build_structure(Op& o) {
   o.h = 1.0 / nel1;
   // S^2: (d+1)^2 Bernstein functions per element; S^1 (EFIE): 2 p (p+1)
   o.nloc = o.efie ? 2 * d * (d + 1) : (d + 1) * (d + 1);
-  o.n1 = nel1 + d;
+  o.n1 = d + 1 + (nel1 - 1) * o.rep;
   o.nelem = 6 * per_patch;
   o.ndofs = 6 * int64_t(o.n1) * o.n1;
   o.nlocal = o.nelem * o.nloc;
   if (o.efie) build_s1_space(o);  // sets ndofs (glued S^1 dofs) and the CSR extraction
+  if (!o.efie && o.rep > 1) build_s2_csr(o);
   o.m = 1 << (L - o.leaf);
   o.nld = o.m * o.m * o.nloc;
   o.q2 = o.q * o.q;
@@ -556,7 +607,6 @@ void build_structure(Op& o) {
     }
   }
 
-  debug_mark("setup: cluster balls on levels 0..leaf");
   // ---- cluster balls on levels 0..leaf -----------------------------------------
   o.lvl_off.assign(o.leaf + 2, 0);
   for (int l = 0; l <= o.leaf; ++l) o.lvl_off[l + 1] = o.lvl_off[l] + 6 * (int64_t(1) << (2 * l));
@@ -574,7 +624,6 @@ void build_structure(Op& o) {
     cuda_check(cudaMemcpy(balls.data(), o.d_balls, sizeof(Ball) * o.nclusters, cudaMemcpyDeviceToHost), "balls");
   }
 
-  debug_mark("setup: block tree");
   // ---- block tree, level by level ------------------------------------------------
   // The candidate sources of a target are the children of the non-admissible
   // sources of its parent (all patches on level 0), visited in increasing order,
@@ -585,7 +634,11 @@ void build_structure(Op& o) {
     const Ball &bt = balls[t], &bs = balls[sc];
     const double dx = bt.c[0] - bs.c[0], dy = bt.c[1] - bs.c[1], dz = bt.c[2] - bs.c[2];
     const double dist = std::max(0.0, std::sqrt(dx * dx + dy * dy + dz * dz) - bt.r - bs.r);
-    return 2.0 * std::max(bt.r, bs.r) <= o.opts.eta * dist;
+    const double diam = 2.0 * std::max(bt.r, bs.r);
+    // Helmholtz: the interpolated kernel oscillates like exp(-i kappa r); a limit on
+    // |kappa| diam keeps the phase variation over a far block within reach of q points
+    if (o.cplx && o.opts.kdiam > 0.0 && std::hypot(o.kre, o.kim) * diam > o.opts.kdiam) return false;
+    return diam <= o.opts.eta * dist;
   };
   std::vector<long long> fptr(o.nclusters + 1, 0);
   std::vector<int> fsrc;
@@ -674,7 +727,6 @@ void build_structure(Op& o) {
     o.d_near_tgt = upload(ntgt);
   }
 
-  debug_mark("setup: element pairs of the near field");
   // ---- element pairs of the near field (classified on the device) -----------------
   {
     std::vector<int> cid32(cid.begin(), cid.end());
@@ -721,11 +773,9 @@ void build_structure(Op& o) {
     dev_free(d_cnt);
   }
 
-  debug_mark("setup: Bezier extraction");
   // ---- Bezier extraction (1-D, per element index); S^1: signed CSR with glue ------
-  if (!o.efie) o.d_ex = upload(extraction_1d(d, nel1));
+  if (!o.efie) o.d_ex = upload(extraction_1d(d, nel1, o.rep));
 
-  debug_mark("setup: moments and transfers");
   // ---- moments and transfers (geometry independent) --------------------------------
   if (o.q > 0) {
     const int q = o.q, q2 = o.q2;
@@ -821,7 +871,6 @@ void build_structure(Op& o) {
     o.d_nodes32 = upload(nodes32);
   }
 
-  debug_mark("setup: quadrature tables");
   // ---- quadrature tables -------------------------------------------------------------
   {
     std::vector<double> gx, gw;
@@ -867,7 +916,6 @@ void build_structure(Op& o) {
     o.d_gauss = upload(rg);
   }
 
-  debug_mark("setup: report");
   // ---- report -------------------------------------------------------------------------
   bembel_op_info& in = o.info;
   in.ndofs = o.ndofs;

@@ -418,7 +418,7 @@ int gmres_run(const Op& o, const double* b, double* x, int nrhs, double tol, int
   ensure_scratch(const_cast<Op&>(o), matvec_scratch_bytes(o, nrhs, false));
   if (fp32) tc_prepare(const_cast<Op&>(o), nrhs);  // tensor-core groups, if used, before capture
   // dof-major staging for wide products (the FP64 restart residuals need the larger size)
-  if (!o.efie && nrhs * C >= 32) ensure_dofmajor(const_cast<Op&>(o), sizeof(double) * (size_t)n * nrhs * C);
+  if (!o.d_e_ptr && nrhs * C >= 32) ensure_dofmajor(const_cast<Op&>(o), sizeof(double) * (size_t)n * nrhs * C);
   DevBuf Vbuf(sizeof(T) * vstride * (m + 1)), wbuf(sizeof(T) * vstride), zbuf(sizeof(T) * vstride),
       rbuf(sizeof(double) * vstride), ubuf(sizeof(double) * vstride);
   T* V = static_cast<T*>(Vbuf.p);

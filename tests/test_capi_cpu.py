@@ -73,7 +73,8 @@ def test_binding_loads_and_reports_errors(built_lib):
                                 dict(g_edge_var=(4, 11, 11, 3)),    # above the largest order
                                 dict(g_edge_var=(4, 4, 5, 3)),      # edge rule not symmetric
                                 dict(g_vertex_var=(5, 4, 4, 3)),    # vertex rule not symmetric
-                                dict(g_regular=11), dict(eta=0.0), dict(leaf_level=7)])
+                                dict(g_regular=11), dict(eta=0.0), dict(leaf_level=7),
+                                dict(knot_repetition=3), dict(knot_repetition=-1)])  # degree 1: r <= 2
 def test_assemble_rejects_bad_options_before_device_work(built_lib, kw):
     import paper_1906_00785_gb300 as bem
 

@@ -1,0 +1,81 @@
+"""Convergence orders on the GPU: the analogue of the paper's Fig. 1 (Sec. 5).
+
+The paper reports, for its EFIE example, pointwise errors of the scattered field that
+fall like h^(2P+1) (fitted orders 3, 5, 7 for P = 1, 2, 3).  Here the same experiment
+runs on a perfectly conducting unit sphere (the quarter-pipe geometry of the paper is not
+available): plane wave along +z polarised in x, kappa = 3, scattered field at the 100
+points of the sphere grid of radius 6 (Sec. 5, Util::makeSphereGrid(6, 10)) against the
+Mie series, dense operators (q = 0) at high quadrature orders so that quadrature stays
+below the discretisation error.  The S^2 analogue is the Laplace point-charge problem of
+the interior ball (config 1): potential at 100 points in the ball of radius 0.5 against
+1/|x - x0|, expected order 2d + 3 for ansatz degree d.
+
+Fitted orders come from the last two levels and must reach the expected order minus 0.8
+(pre-asymptotic levels give slightly lower slopes; the oracle's own EFIE orders at levels
+0-2 are 2.9 and 4.7, tests/golden/efie_convergence_orders.txt)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1906_00785_gb300 as bem
+from inputs import ball_points
+from mie import scattered_pec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def geom():
+    return bem.bembel_geom_create()
+
+
+def efie_errors(geom, P, levels, k=3.0):
+    pts = bem.bembel_sphere_grid(6.0, 10)
+    ref = scattered_pec(pts, k)  # E_inc = x_hat exp(-i k z)
+    errs = []
+    for L in levels:
+        op = bem.bembel_assemble(geom, bem.BEMBEL_MAXWELL_SL, k, L, P, 0, g_regular=8, g_singular=7)
+        n = bem.bembel_ndofs(op)
+        b = torch.empty(n, dtype=torch.complex128, device="cuda")
+        bem.bembel_rhs(op, bem.BEMBEL_RHS_EFIE_PLANE_WAVE, np.array([[0.0, 0.0, 1.0, 1.0, 0.0, 0.0]]), b, g=8)
+        j = torch.empty_like(b)
+        info = bem.bembel_solve(op, b, j, 1, tol=1e-12, restart=200, max_iter=20000)
+        assert info["rel_residual"] < 1e-10, (P, L, info)
+        E = torch.empty((100, 3), dtype=torch.complex128, device="cuda")
+        bem.bembel_eval(op, torch.from_numpy(pts).cuda(), j, E, 1, g=8)
+        errs.append(float(np.max(np.linalg.norm(E.cpu().numpy() - ref, axis=1)) / np.max(np.linalg.norm(ref, axis=1))))
+        del op
+        torch.cuda.empty_cache()
+    return errs
+
+
+@pytest.mark.parametrize("P,levels", [(1, [1, 2, 3, 4]), (2, [1, 2, 3, 4]), (3, [0, 1, 2, 3])])
+def test_efie_orders(geom, P, levels):
+    errs = efie_errors(geom, P, levels)
+    orders = [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+    print(f"EFIE P={P} levels {levels}: errors", ["%.2e" % e for e in errs], "orders", ["%.2f" % o for o in orders])
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert orders[-1] >= 2 * P + 1 - 0.8, orders
+
+
+@pytest.mark.parametrize("d,levels", [(0, [1, 2, 3, 4]), (1, [1, 2, 3, 4]), (2, [1, 2, 3, 4])])
+def test_s2_point_charge_orders(geom, d, levels):
+    x0 = np.array([0.0, 0.0, 2.0])
+    pts = ball_points(100, 0.5, 1)
+    exact = 1.0 / np.linalg.norm(pts - x0, axis=1)
+    errs = []
+    for L in levels:
+        op = bem.bembel_assemble(geom, bem.BEMBEL_LAPLACE_SL, 0.0, L, d, 0, g_regular=8, g_singular=8)
+        n = bem.bembel_ndofs(op)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        bem.bembel_rhs(op, bem.BEMBEL_RHS_POINT_SOURCE, x0[None, :], b, g=8)
+        rho = torch.empty_like(b)
+        info = bem.bembel_solve(op, b, rho, 1, tol=1e-13, restart=100, max_iter=5000)
+        assert info["converged"]
+        u = torch.empty(100, dtype=torch.float64, device="cuda")
+        bem.bembel_eval(op, torch.from_numpy(pts).cuda(), rho, u, 1, g=8)
+        errs.append(float(np.max(np.abs(u.cpu().numpy() - exact) / exact)))
+        del op
+    orders = [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+    print(f"S2 d={d} levels {levels}: errors", ["%.2e" % e for e in errs], "orders", ["%.2f" % o for o in orders])
+    assert orders[-1] >= 2 * d + 3 - 0.8, orders

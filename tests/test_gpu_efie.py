@@ -42,7 +42,8 @@ def einc_fun(k, d=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0)):
 
 
 @pytest.mark.parametrize("L,p,k,var", [(0, 1, 2.0, None), (1, 1, 2.0, None), (1, 2, 1.5 + 0.2j, None),
-                                       (0, 2, 3.0, None), (1, 2, 2.0, ((4, 5, 3, 3), (4, 5, 5, 3), (5, 4, 4, 4)))])
+                                       (0, 2, 3.0, None), (1, 2, 2.0, ((4, 5, 3, 3), (4, 5, 5, 3), (5, 4, 4, 4))),
+                                       (0, 3, 2.0, None), (1, 3, 2.5, None)])
 def test_efie_matrix_parity(geom, L, p, k, var):
     kw = {} if var is None else dict(g_identical_var=var[0], g_edge_var=var[1], g_vertex_var=var[2])
     op = bem.bembel_assemble(geom, MAX, k, L, p, 0, g_regular=4, g_singular=5, **kw)
