@@ -77,7 +77,10 @@ enum bembel_rhs_kind {
 enum bembel_precond_kind {
   BEMBEL_PRECOND_NONE = 0,
   BEMBEL_PRECOND_BLOCK_JACOBI = 1, /* M^-1 = E^T D^-1 E, D = near-field diagonal leaf blocks */
-  BEMBEL_PRECOND_LEARNED = 2       /* M^-1 = E^T W D^-1 W E, W from bembel_learned_attach   */
+  BEMBEL_PRECOND_LEARNED = 2,      /* M^-1 = E^T W D^-1 W E + P A_c^-1 P^T, W from
+                                      bembel_learned_attach (W = I: TWO_LEVEL)              */
+  BEMBEL_PRECOND_TWO_LEVEL = 3     /* M^-1 = E^T D^-1 E + P A_c^-1 P^T: block-Jacobi plus the
+                                      coarse-space correction (opts.coarse_level)           */
 };
 #define BEMBEL_LEARNED_NPARAM 433  /* parameters of the learned preconditioner's network */
 
@@ -142,6 +145,14 @@ typedef struct {
    * q Chebyshev points resolve (diameters of the bounding balls; App. B eq. (HS)).
    * 0 = no such limit (default 0). */
   double kdiam;
+  /* Coarse space of the two-level and learned preconditioners (not in the paper): the
+   * S^2 space of the same degree on level coarse_level, nested in the operator's space
+   * (App. E), with P its refinement (knot insertion) into the fine space and A_c its
+   * Galerkin matrix, assembled densely on that level with the operator's quadrature
+   * orders and inverted once on the device (6 (p + 2^coarse_level)^2 <= 8192 dofs,
+   * EINVAL above).  1 <= coarse_level <= level; 0 = max(0, level - 3) (default 0).
+   * S^2 operators with knot_repetition 1 only (EUNSUPPORTED otherwise). */
+  int coarse_level;
 } bembel_opts;
 
 /* Counters describing an assembled operator (host struct). */
@@ -239,10 +250,12 @@ int bembel_geom_destroy(bembel_geom* g);
  * np (np-1) + j1 + (np-1) i2; a function glued to one numbered earlier shares
  * its number, with sign -s_own s_partner (s = +1 on the sides s = 1, t = 1,
  * -1 on s = 0, t = 0).  The EFIE is available on the cube-face sphere, dense
- * (q = 0) or H^2-compressed (q > 0, FP64: the kernel times the Jacobian dot
+ * (q = 0) or H^2-compressed (q > 0: the kernel times the Jacobian dot
  * products and G itself are interpolated per far block, the three moment
  * channels int phi^1 L_a, int phi^2 L_a, int div phi L_a run through the same
- * nested transfers); bembel_eval returns the scattered field (MS) at the points,
+ * nested transfers; MIXED operators keep FP32 copies of the near field and of
+ * the five coupling matrices for the inner solves, FP64 for the refinement);
+ * bembel_eval returns the scattered field (MS) at the points,
  * 3 complex values per point (out: [rhs][point][3] interleaved complex).
  * bembel_autotune, bembel_assemble_batch and the learned preconditioner are
  * for the scalar operators only (EUNSUPPORTED). */
@@ -369,10 +382,11 @@ int bembel_matvec(const bembel_op* op, const void* x_dev, void* y_dev, int nrhs,
  * synchronise between them.
  * Arguments, layouts and the fp32 flag are those of bembel_matvec.  The
  * kernels are those of bembel_matvec with one exception: this call never
- * builds the sibling groups of the tensor-core coupling (that would allocate),
- * so a wide FP32 product on a MIXED operator uses the bf16 tensor cores only
- * after a bembel_matvec or bembel_solve with as many columns has built them;
- * before that it takes the FP32 CUDA-core coupling (results then differ from
+ * builds what wide FP32 products allocate on first use (the tensor-core
+ * groups and tiles, the FP32 copy of the stored coupling), so a wide FP32
+ * product on a MIXED operator uses them only after a bembel_matvec or
+ * bembel_solve with as many columns has made them; before that it evaluates
+ * the FP32 coupling on the fly on the CUDA cores (results then differ from
  * bembel_matvec's tensor-core product by the bf16 rounding, ~1e-3 of the far
  * field).
  * Errors: EINVAL (NULL, nrhs < 1, aliasing, scratch too small, fp32 on an FP64
@@ -383,8 +397,12 @@ int bembel_matvec_noalloc(const bembel_op* op, const void* x_dev, void* y_dev, i
  * canonical K-major shared-memory layout used by the tensor-core coupling, FP32
  * accumulation in TMEM) on exactly representable data, compared with a host
  * product; *max_abs_err receives the largest difference (0 when the layout and
- * descriptors are right).  n: multiple of 16 in [16, 256].  The paper has no
- * counterpart.  Errors: EINVAL, ETIMEOUT (bounded wait expired), ECUDA. */
+ * descriptors are right).  n: multiple of 16 in [16, 256].  n = 0 exercises the
+ * time-out path of the bounded waits instead: one thread waits, with a short
+ * poll limit, on an mbarrier that nothing signals; the call then returns
+ * BEMBEL_ETIMEOUT (the expected outcome) with the device still usable.  The
+ * paper has no counterpart.  Errors: EINVAL, ETIMEOUT (bounded wait expired),
+ * ECUDA. */
 int bembel_tc_selftest(int n, double* max_abs_err);
 
 /* ---- learned preconditioner (not in the paper: the solver's own extension) ----
@@ -393,12 +411,16 @@ int bembel_tc_selftest(int n, double* max_abs_err);
  * leaf, patch/leaf boundary flags, log element distortion, |kappa| * element
  * size); MLP 8 -> 16 -> 16 -> 1 with tanh, parameters packed [W1 (16x8, row-
  * major), b1, W2 (16x16), b2, w3 (16), b3] (BEMBEL_LEARNED_NPARAM floats).
- * Zero w3, b3 gives W = I, i.e. block-Jacobi.  Trained with the unsupervised
+ * The coarse-space correction P A_c^-1 P^T of the two-level preconditioner is added
+ * to it: M_W^-1 = E^T W D^-1 W E + P A_c^-1 P^T (opts.coarse_level).  Zero w3, b3
+ * gives W = I, i.e. the two-level preconditioner.  Trained with the unsupervised
  * loss sum_s |M_W^-1 A z_s - z_s|^2 / |z_s|^2 on systems the solver generates. */
 
-/* Training data of one operator: builds the block-Jacobi inverses, the dof
- * features and nsamples pairs (z ~ N(0,1) seeded, A z by the FP64 product), and
- * keeps only those (the operator may be destroyed afterwards).  1 <= nsamples <= 64. */
+/* Training data of one operator: builds the block-Jacobi inverses and the coarse
+ * correction, the dof features and nsamples pairs (z ~ N(0,1) seeded, y = A z by the
+ * FP64 product, and the part z - P A_c^-1 P^T y that the weighted block-Jacobi term
+ * is trained to reproduce), and keeps only those (the operator may be destroyed
+ * afterwards).  1 <= nsamples <= 64. */
 int bembel_learned_collect(bembel_op* op, int nsamples, uint64_t seed, bembel_learned_set** out);
 int bembel_learned_set_destroy(bembel_learned_set* s);
 /* Adam on the loss over all sets, one step per epoch (full batch); params (host,
@@ -430,6 +452,16 @@ int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, in
  * Errors: EINVAL, ENOMEM, ECUDA, ENOTCONV (x holds the last iterate). */
 int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, const bembel_solve_opts* so,
                  bembel_solve_info* info);
+
+/* Apply the preconditioner M^-1 of kind precond (enum bembel_precond_kind; NONE
+ * copies) to nrhs columns: y = M^-1 x, as the solver applies it.  x_dev, y_dev:
+ * device, column-major ndofs x nrhs, FP64 (fp32 = 0) or FP32 (complex for
+ * Helmholtz), not overlapping.  Builds the block-Jacobi inverses and the coarse
+ * correction on first use (allocates); LEARNED needs bembel_learned_attach first.
+ * Not in the paper (which solves without a preconditioner).  Synchronous on the
+ * operator's stream.  Errors: EINVAL, EUNSUPPORTED (EFIE; coarse space with
+ * knot_repetition > 1), ENOMEM, ECUDA. */
+int bembel_precond_apply(const bembel_op* op, int precond, const void* x_dev, void* y_dev, int nrhs, int fp32);
 
 /* Potential u(x) = sum_j rho_j int G(x, gamma(t)) phi_hat_j(t) dt (Sec. 4.7;
  * (LS)/(HS)) at npts points.  pts_dev: device, npts x 3 row-major FP64;

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbembel.so")
-SOURCES = ["capi.cu", "setup.cu", "quad.cu", "quad_batch.cu", "h2mv.cu", "solve.cu", "rhs_eval.cu", "precond.cu", "autotune.cu", "learned.cu", "tc_coupling.cu", "efie.cu"]
+SOURCES = ["capi.cu", "setup.cu", "quad.cu", "quad_batch.cu", "h2mv.cu", "solve.cu", "rhs_eval.cu", "precond.cu", "autotune.cu", "learned.cu", "tc_coupling.cu", "efie.cu", "coarse.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

@@ -21,7 +21,7 @@ BEMBEL_GEOM_SPHERE6, BEMBEL_GEOM_PERTURBED_SPHERE, BEMBEL_GEOM_NURBS = 0, 1, 2
 BEMBEL_LAPLACE_SL, BEMBEL_HELMHOLTZ_SL, BEMBEL_MAXWELL_SL = 0, 1, 2
 BEMBEL_PREC_FP64, BEMBEL_PREC_MIXED = 0, 1
 BEMBEL_RHS_POINT_SOURCE, BEMBEL_RHS_PLANE_WAVE, BEMBEL_RHS_EFIE_PLANE_WAVE = 0, 1, 2
-BEMBEL_PRECOND_NONE, BEMBEL_PRECOND_BLOCK_JACOBI, BEMBEL_PRECOND_LEARNED = 0, 1, 2
+BEMBEL_PRECOND_NONE, BEMBEL_PRECOND_BLOCK_JACOBI, BEMBEL_PRECOND_LEARNED, BEMBEL_PRECOND_TWO_LEVEL = 0, 1, 2, 3
 BEMBEL_LEARNED_NPARAM = 433
 
 EXPORTED = [
@@ -31,6 +31,7 @@ EXPORTED = [
     "bembel_matvec_noalloc", "bembel_autotune", "bembel_learned_collect", "bembel_learned_set_destroy",
     "bembel_learned_train", "bembel_learned_attach", "bembel_mlp_eval", "bembel_tc_selftest",
     "bembel_assemble_batch", "bembel_near_block", "bembel_eval_h2", "bembel_sphere_grid",
+    "bembel_precond_apply",
 ]
 
 
@@ -53,7 +54,7 @@ class Opts(C.Structure):
                 ("tensor_cores", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p), ("g_identical_var", C.c_int * 4),
                 ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4), ("g_regular_far", C.c_int),
-                ("knot_repetition", C.c_int), ("kdiam", C.c_double)]
+                ("knot_repetition", C.c_int), ("kdiam", C.c_double), ("coarse_level", C.c_int)]
 
 
 class OpInfo(C.Structure):
@@ -381,6 +382,11 @@ def bembel_solve(op: Operator, b, x, nrhs: int = 1, solve_opts: SolveOpts | None
     out = {f: getattr(info, f) for f, _ in SolveInfo._fields_}
     out["converged"] = rc == BEMBEL_OK
     return out
+
+
+def bembel_precond_apply(op: Operator, precond: int, x, y, nrhs: int = 1, fp32: bool = False) -> None:
+    """y = M^-1 x for the preconditioner kind precond (as the solver applies it)."""
+    _check(lib().bembel_precond_apply(op.handle, precond, _ptr(x), _ptr(y), nrhs, int(bool(fp32))))
 
 
 def bembel_eval(op: Operator, pts, rho, out, nrhs: int = 1, g: int = 6) -> None:

@@ -50,8 +50,9 @@ void free_op(Op* o) {
                   o->d_N,       o->d_N32,     o->d_V,       o->d_T,     o->d_V32,   o->d_T32,      o->d_ex,
                   o->d_Xq,      o->d_BW,      o->d_gauss,   o->d_Xq_far, o->d_Xq_far32, o->d_cen, o->d_BW_far32, o->d_BW_far, o->d_nodes_jac, o->d_dofmajor,   o->d_nodes, o->d_scratch, o->d_bj,
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
-                  o->d_tc_gptr, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
-                  o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val};
+                  o->d_tc_gptr, o->d_tc_A, o->d_tc_B, o->d_tc_items, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
+                  o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val,
+                  o->d_R, o->d_rcol, o->d_rrow, o->d_cinv, o->d_cinv32, o->d_cbuf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* p : o->d_pairs)
@@ -240,8 +241,6 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
     fail(BEMBEL_EINVAL, "assemble: unknown operator");
   if (op == BEMBEL_MAXWELL_SL) {
     if (p < 1 || p > kMaxEfieDeg) fail(BEMBEL_EINVAL, "assemble: the EFIE needs the S^1 degree p in [1, 3]");
-    if (q != 0 && o && o->precision == BEMBEL_PREC_MIXED)
-      fail(BEMBEL_EUNSUPPORTED, "assemble: the compressed EFIE (q > 0) is FP64 only");
     if (reinterpret_cast<GeomHandle*>(g)->g.kind != BEMBEL_GEOM_SPHERE6)
       fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE is available on the cube-face sphere");
     if (k_re == 0.0 && k_im == 0.0) fail(BEMBEL_EINVAL, "assemble: the EFIE needs a nonzero wavenumber");
@@ -266,6 +265,8 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
   const int rep = opts.knot_repetition == 0 ? 1 : opts.knot_repetition;
   if (rep < 1 || rep > p + 1) fail(BEMBEL_EINVAL, "assemble: knot_repetition must be in [1, p + 1]");
   if (rep > 1 && op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE takes knot_repetition 1");
+  if (opts.coarse_level < 0 || opts.coarse_level > level)
+    fail(BEMBEL_EINVAL, "assemble: coarse_level must be in [0, level]");
   Op* res = new Op();
   res->rep = rep;
   res->geom = reinterpret_cast<GeomHandle*>(g)->g;
@@ -324,6 +325,33 @@ void setup_op(Op& o) {
   o.info.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
 }
 }  // namespace
+
+extern "C++" {
+namespace bembel {
+void destroy_op(Op* o) { free_op(o); }
+
+// The dense operator (q = 0, FP64) of o's kernel, wavenumber, degree and quadrature
+// orders on another level of the same geometry: the coarse Galerkin matrix of the
+// two-level preconditioner.
+Op* assemble_level(const Op& o, int level) {
+  GeomHandle gh;
+  gh.g = o.geom;  // shares the geometry's buffers; gh owns nothing
+  bembel_opts opts = o.opts;
+  opts.leaf_level = -1;
+  opts.precision = BEMBEL_PREC_FP64;
+  opts.coarse_level = 0;
+  Op* c = make_op(reinterpret_cast<bembel_geom*>(&gh), o.op, o.kre, o.kim, level, o.d, 0, &opts);
+  try {
+    setup_op(*c);
+    run_assembly_kernels(*c);
+  } catch (...) {
+    free_op(c);
+    throw;
+  }
+  return c;
+}
+}  // namespace bembel
+}
 
 int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q, const bembel_opts* o,
                     bembel_op** out) {
@@ -534,6 +562,11 @@ int bembel_mlp_eval(const float* params, const float* feat_dev, int64_t n, const
 int bembel_tc_selftest(int n, double* max_abs_err) {
   return guarded([&] {
     if (!max_abs_err) fail(BEMBEL_EINVAL, "tc_selftest: NULL argument");
+    if (n == 0) {  // the bounded-wait time-out path
+      *max_abs_err = 0.0;
+      if (tc_timeout_probe()) fail(BEMBEL_ETIMEOUT, "tc_selftest: the bounded wait on an unsignalled barrier ran out");
+      return BEMBEL_OK;
+    }
     *max_abs_err = tc_selftest(n);
     return BEMBEL_OK;
   });
@@ -564,13 +597,47 @@ int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, 
     if (o.restart < 1 || o.restart > 200 || o.max_iter < 1 || !(o.tol > 0))
       fail(BEMBEL_EINVAL, "solve: restart in [1, 200], max_iter >= 1, tol > 0 required");
     if (o.precond != BEMBEL_PRECOND_NONE && o.precond != BEMBEL_PRECOND_BLOCK_JACOBI &&
-        o.precond != BEMBEL_PRECOND_LEARNED)
+        o.precond != BEMBEL_PRECOND_LEARNED && o.precond != BEMBEL_PRECOND_TWO_LEVEL)
       fail(BEMBEL_EINVAL, "solve: unknown preconditioner");
     tc_check(*reinterpret_cast<const Op*>(op));
     const int rc = solve_gmres(*reinterpret_cast<const Op*>(op), b_dev, x_dev, nrhs, o, info);
     tc_check(*reinterpret_cast<const Op*>(op));  // solve_gmres synchronised its stream
     if (rc == BEMBEL_ENOTCONV) g_last_error = "solve: GMRES reached max_iter before the tolerance";
     return rc;
+  });
+}
+
+int bembel_precond_apply(const bembel_op* op, int precond, const void* x_dev, void* y_dev, int nrhs, int fp32) {
+  return guarded([&] {
+    if (!op || !x_dev || !y_dev) fail(BEMBEL_EINVAL, "precond_apply: NULL argument");
+    if (nrhs < 1) fail(BEMBEL_EINVAL, "precond_apply: nrhs must be >= 1");
+    if (x_dev == y_dev) fail(BEMBEL_EINVAL, "precond_apply: x and y must not overlap");
+    if (precond < BEMBEL_PRECOND_NONE || precond > BEMBEL_PRECOND_TWO_LEVEL)
+      fail(BEMBEL_EINVAL, "precond_apply: unknown preconditioner");
+    Op& o = *const_cast<Op*>(reinterpret_cast<const Op*>(op));
+    if (o.efie && precond != BEMBEL_PRECOND_NONE)
+      fail(BEMBEL_EUNSUPPORTED, "precond_apply: S^2 operators only");
+    const size_t el = fp32 ? sizeof(float) : sizeof(double);
+    const size_t bytes = el * size_t(o.ndofs) * nrhs * (o.cplx ? 2 : 1);
+    if (precond == BEMBEL_PRECOND_NONE) {
+      cuda_check(cudaMemcpyAsync(y_dev, x_dev, bytes, cudaMemcpyDeviceToDevice, o.stream), "precond copy");
+    } else {
+      if (precond == BEMBEL_PRECOND_LEARNED && !o.d_lw)
+        fail(BEMBEL_EINVAL, "precond_apply: the learned preconditioner needs bembel_learned_attach first");
+      precond_setup(o);
+      if (precond != BEMBEL_PRECOND_BLOCK_JACOBI) coarse_setup(o, nrhs);
+      const int saved = o.active_precond;
+      o.active_precond = precond;
+      try {
+        precond_apply(o, x_dev, y_dev, nrhs, fp32 != 0, o.stream);
+      } catch (...) {
+        o.active_precond = saved;
+        throw;
+      }
+      o.active_precond = saved;
+    }
+    cuda_check(cudaStreamSynchronize(o.stream), "precond_apply sync");
+    return BEMBEL_OK;
   });
 }
 

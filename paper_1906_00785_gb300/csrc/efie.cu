@@ -393,9 +393,10 @@ int4 orders(const Op& o, int kind) {
 }
 
 // Far-field coupling of the compressed EFIE, per far block and cluster points
-// (a, b): K[blk][c][a][b] = G(x_a, y_b) d_alpha gamma(x_a) . d_beta gamma(y_b)
-// for c = 2 alpha + beta (alpha, beta: 0 = d_s, 1 = d_t) and K[blk][4] =
-// -kappa^-2 G(x_a, y_b); complex interleaved, G with its 1/(4 pi).
+// (a, b): K[blk][c][b][a] = G(x_a, y_b) d_alpha gamma(x_a) . d_beta gamma(y_b)
+// for c = 2 alpha + beta (alpha, beta: 0 = d_s, 1 = d_t) and K[blk][4][b][a] =
+// -kappa^-2 G(x_a, y_b); complex interleaved, G with its 1/(4 pi).  Stored with the
+// target point a fastest, so the product's threads (one per a) read consecutive words.
 __global__ void k_efie_coupling(const int* __restrict__ tgt, const int* __restrict__ src, int64_t nfar,
                                 const double* __restrict__ nodes, const double* __restrict__ jac, int q2, double kre,
                                 double kim, double* __restrict__ K) {
@@ -403,7 +404,7 @@ __global__ void k_efie_coupling(const int* __restrict__ tgt, const int* __restri
   const int64_t per = (int64_t)q2 * q2;
   if (id >= nfar * per) return;
   const int64_t blk = id / per;
-  const int a = int(id % per) / q2, b = int(id % per) % q2;
+  const int b = int(id % per) / q2, a = int(id % per) % q2;
   const int64_t pa = (int64_t)tgt[blk] * q2 + a, pb = (int64_t)src[blk] * q2 + b;
   const double* xa = nodes + pa * 3;
   const double* xb = nodes + pb * 3;
@@ -416,7 +417,7 @@ __global__ void k_efie_coupling(const int* __restrict__ tgt, const int* __restri
   gi *= kInv4Pi;
   const double kk_r = kre * kre - kim * kim, kk_i = 2.0 * kre * kim, kk_n = kk_r * kk_r + kk_i * kk_i;
   const double cr = -kk_r / kk_n, ci = kk_i / kk_n;  // -kappa^-2
-  double* out = K + ((blk * 5) * per + (int64_t)a * q2 + b) * 2;
+  double* out = K + ((blk * 5) * per + (int64_t)b * q2 + a) * 2;
   for (int al = 0; al < 2; ++al)
     for (int be = 0; be < 2; ++be) {
       const double g = Ja[3 * al] * Jb[3 * be] + Ja[3 * al + 1] * Jb[3 * be + 1] + Ja[3 * al + 2] * Jb[3 * be + 2];
@@ -427,45 +428,65 @@ __global__ void k_efie_coupling(const int* __restrict__ tgt, const int* __restri
   out[4 * per * 2 + 1] = gr * ci + gi * cr;
 }
 
-// yh[t][a][co ncol + 2r] = sum over far sources s of t, points b and input channels:
-// channels 0, 1 (the two components) couple through K[0..3], channel 2 (the
-// divergence) through K[4].  One thread per (target cluster, a, output channel, rhs).
-__global__ void k_efie_coupling_mv(const long long* __restrict__ fptr, const int* __restrict__ fsrc,
-                                   int64_t nclusters, const double* __restrict__ K, int q2,
-                                   const double* __restrict__ xh, double* __restrict__ yh, int nrhs) {
+// yh[t][a][co ncol + 2r] += sum over far blocks (t, s), points b and input channels:
+// output channels 0, 1 (the two components) couple with input channels 0, 1 through
+// K[0..3], channel 2 (the divergence) with channel 2 through K[4].  One thread per
+// (chunk of kEfieChunk consecutive far blocks, rhs, a), a fastest: the coupling words of
+// consecutive threads are consecutive (K[blk][c][b][a]) and the source moments are the
+// same for the whole group.  The far list is ordered by target: partial sums are flushed
+// with atomics when the target changes inside a chunk and at its end (yh cleared before).
+constexpr int kEfieChunk = 8;
+
+template <typename T>
+__global__ void k_efie_coupling_mv(const int* __restrict__ ftgt, const int* __restrict__ fsrc, int64_t nfar,
+                                   const T* __restrict__ K, int q2, const T* __restrict__ xh, T* __restrict__ yh,
+                                   int nrhs) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= nclusters * q2 * 3 * nrhs) return;
-  const int r = int(id % nrhs);
-  const int co = int((id / nrhs) % 3);
-  const int a = int((id / (3 * nrhs)) % q2);
-  const int64_t t = id / ((int64_t)3 * nrhs * q2);
+  const int64_t nchunk = (nfar + kEfieChunk - 1) / kEfieChunk;
+  if (id >= nchunk * q2 * nrhs) return;
+  const int a = int(id % q2);
+  const int r = int((id / q2) % nrhs);
+  const int64_t c = id / ((int64_t)q2 * nrhs);
   const int ncol = 2 * nrhs, ncolh = 3 * ncol;
   const int64_t per = (int64_t)q2 * q2;
-  double ar = 0.0, ai = 0.0;
-  for (long long k = fptr[t]; k < fptr[t + 1]; ++k) {
+  T acc[6] = {0, 0, 0, 0, 0, 0};  // (re, im) of the three output channels
+  int cur = -1;
+  auto flush = [&]() {
+    T* y = yh + ((int64_t)cur * q2 + a) * ncolh + 2 * r;
+#pragma unroll
+    for (int co = 0; co < 3; ++co) {
+      atomicAdd(y + co * ncol, acc[2 * co]);
+      atomicAdd(y + co * ncol + 1, acc[2 * co + 1]);
+      acc[2 * co] = acc[2 * co + 1] = 0;
+    }
+  };
+  const int64_t k1 = min(nfar, (c + 1) * kEfieChunk);
+  for (int64_t k = c * kEfieChunk; k < k1; ++k) {
+    const int t = ftgt[k];
+    if (t != cur) {
+      if (cur >= 0) flush();
+      cur = t;
+    }
     const int64_t sc = fsrc[k];
-    const double* Kb = K + (int64_t)k * 5 * per * 2;
-    const double* xs = xh + sc * q2 * ncolh + 2 * r;
+    const T* Kb = K + k * 5 * per * 2 + (int64_t)a * 2;
+    const T* xs = xh + sc * q2 * ncolh + 2 * r;
     for (int b = 0; b < q2; ++b) {
-      const double* xb = xs + (int64_t)b * ncolh;
-      if (co < 2) {
-        for (int ci = 0; ci < 2; ++ci) {
-          const double* kc = Kb + ((int64_t)(2 * co + ci) * per + (int64_t)a * q2 + b) * 2;
-          const double xr = xb[ci * ncol], xi = xb[ci * ncol + 1];
-          ar += kc[0] * xr - kc[1] * xi;
-          ai += kc[0] * xi + kc[1] * xr;
-        }
-      } else {
-        const double* kc = Kb + ((int64_t)4 * per + (int64_t)a * q2 + b) * 2;
-        const double xr = xb[2 * ncol], xi = xb[2 * ncol + 1];
-        ar += kc[0] * xr - kc[1] * xi;
-        ai += kc[0] * xi + kc[1] * xr;
+      const T* xb = xs + (int64_t)b * ncolh;
+      const T x0r = xb[0], x0i = xb[1], x1r = xb[ncol], x1i = xb[ncol + 1], x2r = xb[2 * ncol], x2i = xb[2 * ncol + 1];
+      const T* kb = Kb + (int64_t)b * q2 * 2;
+#pragma unroll
+      for (int co = 0; co < 2; ++co) {
+        const T* k0 = kb + (int64_t)(2 * co) * per * 2;
+        const T* k1p = kb + (int64_t)(2 * co + 1) * per * 2;
+        acc[2 * co] += k0[0] * x0r - k0[1] * x0i + k1p[0] * x1r - k1p[1] * x1i;
+        acc[2 * co + 1] += k0[0] * x0i + k0[1] * x0r + k1p[0] * x1i + k1p[1] * x1r;
       }
+      const T* k4 = kb + (int64_t)4 * per * 2;
+      acc[4] += k4[0] * x2r - k4[1] * x2i;
+      acc[5] += k4[0] * x2i + k4[1] * x2r;
     }
   }
-  double* y = yh + (t * q2 + a) * ncolh + co * ncol + 2 * r;
-  y[0] = ar;
-  y[1] = ai;
+  if (cur >= 0) flush();
 }
 
 template <int P>
@@ -522,9 +543,21 @@ void efie_coupling_assemble(Op& o) {
 }
 
 void efie_coupling_apply(const Op& o, const double* xh, double* yh, int nrhs, cudaStream_t s) {
-  const int64_t n = o.nclusters * (int64_t)o.q2 * 3 * nrhs;
-  k_efie_coupling_mv<<<int((n + 127) / 128), 128, 0, s>>>(o.d_far_ptr, o.d_far_src, o.nclusters, o.d_K, o.q2, xh, yh,
-                                                          nrhs);
+  cuda_check(cudaMemsetAsync(yh, 0, sizeof(double) * o.nclusters * o.q2 * 6 * nrhs, s), "efie yh clear");
+  const int64_t n = (o.nfar + kEfieChunk - 1) / kEfieChunk * o.q2 * nrhs;
+  if (n == 0) return;
+  k_efie_coupling_mv<double><<<int((n + 127) / 128), 128, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_K, o.q2, xh,
+                                                                  yh, nrhs);
+  launched("k_efie_coupling_mv");
+}
+
+void efie_coupling_apply(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s) {
+  if (!o.d_K32) fail(BEMBEL_EINVAL, "compressed EFIE: the FP32 product needs an operator assembled MIXED");
+  cuda_check(cudaMemsetAsync(yh, 0, sizeof(float) * o.nclusters * o.q2 * 6 * nrhs, s), "efie yh clear");
+  const int64_t n = (o.nfar + kEfieChunk - 1) / kEfieChunk * o.q2 * nrhs;
+  if (n == 0) return;
+  k_efie_coupling_mv<float><<<int((n + 127) / 128), 128, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_K32, o.q2, xh,
+                                                                 yh, nrhs);
   launched("k_efie_coupling_mv");
 }
 

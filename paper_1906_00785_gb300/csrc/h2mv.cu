@@ -283,33 +283,35 @@ void scatter_l(const Op& o, const T* yl, T* y, int ncol, int C, cudaStream_t s) 
 
 // Compressed EFIE, three moment channels stored as extra columns of the
 // cluster vectors: xh[leaf][a][ch ncol + col] = sum_i V[ch][i][a] xl[leaf nld + i][col]
-__global__ void k_leaf_up_ch(const double* __restrict__ xl, double* __restrict__ xh, const double* __restrict__ V,
-                             int64_t nleaf, int nld, int q2, int ncol) {
+template <typename T>
+__global__ void k_leaf_up_ch(const T* __restrict__ xl, T* __restrict__ xh, const T* __restrict__ V, int64_t nleaf,
+                             int nld, int q2, int ncol) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= nleaf * q2 * 3 * ncol) return;
   const int col = int(id % ncol);
   const int ch = int((id / ncol) % 3);
   const int a = int((id / (3 * ncol)) % q2);
   const int64_t lf = id / ((int64_t)3 * ncol * q2);
-  const double* Vc = V + (int64_t)ch * nld * q2;
-  const double* x = xl + lf * nld * ncol + col;
-  double acc = 0.0;
+  const T* Vc = V + (int64_t)ch * nld * q2;
+  const T* x = xl + lf * nld * ncol + col;
+  T acc = 0;
   for (int i = 0; i < nld; ++i) acc += Vc[(int64_t)i * q2 + a] * x[(int64_t)i * ncol];
   xh[(lf * q2 + a) * 3 * ncol + ch * ncol + col] = acc;
 }
 
 // yl[leaf nld + i][col] = sum_ch sum_a V[ch][i][a] yh[leaf][a][ch ncol + col]
-__global__ void k_leaf_down_ch(const double* __restrict__ yh, const double* __restrict__ V, double* __restrict__ yl,
-                               int64_t nleaf, int nld, int q2, int ncol) {
+template <typename T>
+__global__ void k_leaf_down_ch(const T* __restrict__ yh, const T* __restrict__ V, T* __restrict__ yl, int64_t nleaf,
+                               int nld, int q2, int ncol) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= nleaf * nld * ncol) return;
   const int col = int(id % ncol);
   const int i = int((id / ncol) % nld);
   const int64_t lf = id / ((int64_t)ncol * nld);
-  double acc = 0.0;
+  T acc = 0;
   for (int ch = 0; ch < 3; ++ch) {
-    const double* Vc = V + (int64_t)ch * nld * q2 + (int64_t)i * q2;
-    const double* y = yh + lf * q2 * 3 * ncol + ch * ncol + col;
+    const T* Vc = V + (int64_t)ch * nld * q2 + (int64_t)i * q2;
+    const T* y = yh + lf * q2 * 3 * ncol + ch * ncol + col;
     for (int a = 0; a < q2; ++a) acc += Vc[a] * y[(int64_t)a * 3 * ncol];
   }
   yl[id] = acc;
@@ -574,6 +576,73 @@ __global__ void __launch_bounds__(256) k_bsr_mv1(const int* __restrict__ tgt, co
   }
 }
 
+// FP32 far-field coupling evaluated on the fly for one right-hand side and q = 4 (16
+// interpolation points per cluster): four lanes per far block, each with four target
+// points in registers and all 16 source points, eight blocks of a warp's chunk at a time.
+// A source point is loaded once per four kernel evaluations (the generic kernel above
+// loads one per evaluation) and a target's points once per run of blocks with that
+// target (the far list is ordered by target); row sums are flushed with atomics when the
+// target changes.  y must be cleared by the caller.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_onfly_q4(const int* __restrict__ tgt, const int* __restrict__ src,
+                                                  int64_t nblk, const float4* __restrict__ pts, float kre, float kim,
+                                                  const float* __restrict__ x, float* __restrict__ y, int chunk) {
+  constexpr int C = CPLX ? 2 : 1;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane >> 2, sl = lane & 3;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t b0 = warp * chunk;
+  if (b0 >= nblk) return;
+  const int64_t b1 = min(nblk, b0 + chunk);
+  float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+  float4 pa[4];
+  int cur = -1;
+  auto flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t row = (int64_t)cur * 16 + sl + 4 * k;
+      atomicAdd(y + row * C, ar[k] * float(kInv4Pi));
+      if (CPLX) atomicAdd(y + row * C + 1, ai[k] * float(kInv4Pi));
+      ar[k] = ai[k] = 0.f;
+    }
+  };
+  for (int64_t blk = b0 + grp; blk < b1; blk += 8) {
+    const int t = tgt[blk];
+    if (t != cur) {
+      if (cur >= 0) flush();
+      cur = t;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pa[k] = pts[(int64_t)t * 16 + sl + 4 * k];
+    }
+    const int sidx = src[blk];
+    const float4* pb = pts + (int64_t)sidx * 16;
+    const float* xs = x + (int64_t)sidx * 16 * C;
+#pragma unroll 4
+    for (int b = 0; b < 16; ++b) {
+      const float4 p = pb[b];
+      const float xr = xs[b * C], xi = CPLX ? xs[b * C + 1] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float d0 = pa[k].x - p.x, d1 = pa[k].y - p.y, d2 = pa[k].z - p.z;
+        const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+        const float rinv = rsqrtf(r2);
+        if (CPLX) {
+          const float rr = r2 * rinv;
+          float sn, cs;
+          sincosf(kre * rr, &sn, &cs);
+          const float am = (kim != 0.f ? expf(kim * rr) : 1.f) * rinv;
+          const float mr = am * cs, mi = -am * sn;
+          ar[k] = fmaf(mr, xr, fmaf(-mi, xi, ar[k]));
+          ai[k] = fmaf(mr, xi, fmaf(mi, xr, ai[k]));
+        } else {
+          ar[k] = fmaf(rinv, xr, ar[k]);
+        }
+      }
+    }
+  }
+  if (cur >= 0) flush();
+}
+
 // y_loc[t*nld + i][col] = sum_a V[i][a] yh_leaf[t][a][col]  (real V, any columns)
 template <typename T>
 __global__ void k_leaf_down(const T* __restrict__ yh, const T* __restrict__ V, T* __restrict__ yl, int64_t nleaf,
@@ -830,6 +899,17 @@ void launch_bsr(const int* tgt, const int* src, int64_t nblk, const T* M, const 
   const int grid = int((warps * 32 + threads - 1) / threads);
   const int C = CPLX ? 2 : 1;
   const bool vec_ok = (bs * C * sizeof(T)) % 16 == 0 && bs >= 4 && bs <= 64;
+  if constexpr (ONFLY && sizeof(T) == 4) {
+    if (nrhs == 1 && bs == 16) {  // q = 4: register-blocked on-the-fly coupling
+      constexpr int kChunk = 64;
+      const int64_t w4 = (nblk + kChunk - 1) / kChunk;
+      k_onfly_q4<CPLX><<<int((w4 * 32 + threads - 1) / threads), threads, 0, s>>>(
+          tgt, src, nblk, reinterpret_cast<const float4*>(pts), kre, kim, reinterpret_cast<const float*>(x),
+          reinterpret_cast<float*>(y), kChunk);
+      launched("k_onfly_q4");
+      return;
+    }
+  }
   if (nrhs == 1 && vec_ok)
     k_bsr_mv1<T, CPLX, ONFLY><<<grid, threads, 0, s>>>(tgt, src, nblk, M, reinterpret_cast<const float4*>(pts), kre,
                                                         kim, x, y, bs, chunk);
@@ -855,8 +935,7 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
   const int tb = 256;
   gather_l<T>(o, x, xl, ncol, C, s);
   if (q2 > 0 && o.efie) {
-    // compressed EFIE (FP64): channel moments, transfers on 3 ncol columns, coupling, back
-    if (sizeof(T) != sizeof(double)) fail(BEMBEL_EUNSUPPORTED, "compressed EFIE: FP64 products only");
+    // compressed EFIE: channel moments, transfers on 3 ncol columns, coupling, back
     const int nch = 3 * ncol;
     T* xhe = xh;
     T* yhe = xh + o.nclusters * q2 * nch;
@@ -864,9 +943,8 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     const size_t tsh = sizeof(T) * 4 * q2 * q2;
     set_smem_limit(k_up<T>, tsh);  // q >= 7: the four transfer matrices exceed 48 KiB
     set_smem_limit(k_down<T>, tsh);
-    k_leaf_up_ch<<<blocks_for(o.nleaf * q2 * nch, tb), tb, 0, s>>>(
-        reinterpret_cast<const double*>(xl), reinterpret_cast<double*>(xhe + leaf_off * q2 * nch),
-        reinterpret_cast<const double*>(V), o.nleaf, o.nld, q2, ncol);
+    k_leaf_up_ch<T><<<blocks_for(o.nleaf * q2 * nch, tb), tb, 0, s>>>(xl, xhe + leaf_off * q2 * nch, V, o.nleaf,
+                                                                       o.nld, q2, ncol);
     launched("k_leaf_up_ch");
     for (int l = o.leaf - 1; l >= 0; --l) {
       const int64_t np = o.lvl_off[l + 1] - o.lvl_off[l];
@@ -874,16 +952,15 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
                                                              xhe + o.lvl_off[l + 1] * q2 * nch, Tm, np, q2, nch);
       launched("k_up");
     }
-    efie_coupling_apply(o, reinterpret_cast<const double*>(xhe), reinterpret_cast<double*>(yhe), nrhs, s);
+    efie_coupling_apply(o, xhe, yhe, nrhs, s);
     for (int l = 1; l <= o.leaf; ++l) {
       const int64_t nc = o.lvl_off[l + 1] - o.lvl_off[l];
       k_down<T><<<blocks_for(nc * q2 * nch, tb), tb, tsh, s>>>(yhe + o.lvl_off[l] * q2 * nch,
                                                                yhe + o.lvl_off[l - 1] * q2 * nch, Tm, nc, q2, nch);
       launched("k_down");
     }
-    k_leaf_down_ch<<<blocks_for(o.nleaf * o.nld * ncol, tb), tb, 0, s>>>(
-        reinterpret_cast<const double*>(yhe + leaf_off * q2 * nch), reinterpret_cast<const double*>(V),
-        reinterpret_cast<double*>(yl), o.nleaf, o.nld, q2, ncol);
+    k_leaf_down_ch<T><<<blocks_for(o.nleaf * o.nld * ncol, tb), tb, 0, s>>>(yhe + leaf_off * q2 * nch, V, yl,
+                                                                             o.nleaf, o.nld, q2, ncol);
     launched("k_leaf_down_ch");
   } else if (q2 > 0) {
     const int64_t leaf_off = o.lvl_off[o.leaf];
@@ -925,6 +1002,12 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
     if (fp32 && tc_coupling_usable(o, nrhs)) {
       // many right-hand sides: sibling-grouped coupling on the tensor cores
       tc_coupling(o, reinterpret_cast<const float*>(xh), reinterpret_cast<float*>(yh), nrhs, s);
+    } else if (fp32 && K && ncol >= 8 && rows_kernel_fits(q2, nrhs, C, sizeof(T))) {
+      // many right-hand sides on the CUDA cores: stream the stored FP32 coupling
+      if (o.cplx)
+        launch_bsr_rows<T, true>(o.d_far_ptr, o.d_far_src, o.nclusters, K, xh, yh, q2, nrhs, s);
+      else
+        launch_bsr_rows<T, false>(o.d_far_ptr, o.d_far_src, o.nclusters, K, xh, yh, q2, nrhs, s);
     } else if (o.cplx) {
       if (fp32)
         launch_bsr<T, true, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, float(o.kre),
@@ -1027,6 +1110,7 @@ size_t matvec_scratch_bytes(const Op& o, int nrhs, bool fp32) {
 void matvec_device(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s) {
   ensure_scratch(const_cast<Op&>(o), matvec_scratch_bytes(o, nrhs, fp32));
   if (fp32) tc_prepare(const_cast<Op&>(o), nrhs);
+  if (fp32) coupling_f32_prepare(const_cast<Op&>(o), nrhs);
   if (fp32) {
     if (!o.d_N32) fail(BEMBEL_EINVAL, "FP32 matvec needs an operator assembled with precision MIXED");
     matvec_impl<float>(o, static_cast<const float*>(x), static_cast<float*>(y), nrhs, s, o.d_K32, o.d_N32, o.d_V32,
@@ -1111,6 +1195,8 @@ void precond_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const
     launch_bsr<T, false, false>(o.d_leaf_ids, o.d_leaf_ids, o.nleaf, Dinv, nullptr, 0.f, 0.f, xl, yl, o.nld, nrhs, s, o.bsr_chunk);
   if (learned) learned_scale_local(o, yl, nrhs, sizeof(T) == 4, s);
   scatter_l<T>(o, yl, y, ncol, C, s);
+  if (o.active_precond == BEMBEL_PRECOND_TWO_LEVEL || o.active_precond == BEMBEL_PRECOND_LEARNED)
+    coarse_apply_add(o, x, y, nrhs, sizeof(T) == 4, s);
 }
 }  // namespace
 

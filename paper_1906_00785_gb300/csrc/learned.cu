@@ -3,14 +3,16 @@
 // The block-Jacobi preconditioner M^-1 = E^T D^-1 E (precond.cu) sums, for a
 // global dof shared by several elements or leaves, the contributions of every
 // element-local copy.  The learned form
-//   M_W^-1 = E^T W D^-1 W E,   W = diag(w_i),  w_i = exp(MLP(f_i)) > 0,
+//   M_W^-1 = E^T W D^-1 W E + P A_c^-1 P^T,   W = diag(w_i),  w_i = exp(MLP(f_i)) > 0,
 // weights every element-local dof by a small network of local features f_i
 // (position of the basis function in its element and of the element in its
 // leaf, patch and leaf boundary flags, element distortion, |kappa| h).  W = I
-// (zero output layer) is exactly block-Jacobi.  The network is trained on
-// systems the solver generates, with the unsupervised loss
+// (zero output layer) is exactly the two-level preconditioner (block-Jacobi plus the
+// coarse-space correction P A_c^-1 P^T of coarse.cu, which does not depend on W).  The
+// network is trained on systems the solver generates, with the unsupervised loss
 //   L = sum_s |M_W^-1 A z_s - z_s|^2 / |z_s|^2,
-// whose gradient in W is (y = A z, u = E y, p = D^-1 W u, r = E^T W p - z,
+// whose gradient in W is (y = A z, t = z - P A_c^-1 P^T y, u = E y, p = D^-1 W u,
+// r = E^T W p - t,
 // g = E r, D^-1 complex symmetric)
 //   dL/dw_i = 2 Re[ conj(g_i) p_i + (D^-1 W conj(g))_i u_i ],
 // and back-propagated through the network by this file's own kernels.  Not in
@@ -305,12 +307,25 @@ LearnedSet* learned_collect(Op& src, int ns, unsigned long long seed) {
   double* yd = static_cast<double*>(dev_alloc(sizeof(double) * nv * ns));
   cuda_check(cudaMemcpy(zd, zh.data(), sizeof(double) * nv * ns, cudaMemcpyHostToDevice), "z");
   matvec_device(src, zd, yd, ns, false, src.stream);
-  std::vector<double> yh((size_t)nv * ns);
+  // the coarse correction C y is fixed (independent of W): the weighted block-Jacobi term
+  // is trained to reproduce t = z - C y, so that the loss is |M_W^-1 A z - z|^2 with
+  // M_W^-1 = E^T W D^-1 W E + C
+  coarse_setup(src, ns);
+  double* cd = static_cast<double*>(dev_alloc(sizeof(double) * nv * ns));
+  cuda_check(cudaMemsetAsync(cd, 0, sizeof(double) * nv * ns, src.stream), "cy clear");
+  const int saved = src.active_precond;
+  src.active_precond = BEMBEL_PRECOND_TWO_LEVEL;
+  coarse_apply_add(src, yd, cd, ns, false, src.stream);
+  src.active_precond = saved;
+  std::vector<double> yh((size_t)nv * ns), ch((size_t)nv * ns);
   cuda_check(cudaMemcpyAsync(yh.data(), yd, sizeof(double) * nv * ns, cudaMemcpyDeviceToHost, src.stream), "y");
+  cuda_check(cudaMemcpyAsync(ch.data(), cd, sizeof(double) * nv * ns, cudaMemcpyDeviceToHost, src.stream), "cy");
   cuda_check(cudaStreamSynchronize(src.stream), "collect sync");
   dev_free(zd);
   dev_free(yd);
-  std::vector<float> zf(zh.begin(), zh.end()), yf(yh.begin(), yh.end());
+  dev_free(cd);
+  std::vector<float> zf(zh.size()), yf(yh.begin(), yh.end());
+  for (size_t i = 0; i < zh.size(); ++i) zf[i] = float(zh[i] - ch[i]);
   S->Z = static_cast<float*>(dev_alloc(sizeof(float) * nv * ns));
   S->Y = static_cast<float*>(dev_alloc(sizeof(float) * nv * ns));
   cuda_check(cudaMemcpy(S->Z, zf.data(), sizeof(float) * nv * ns, cudaMemcpyHostToDevice), "z32");

@@ -115,6 +115,10 @@ struct Op {
   int* d_tc_err = nullptr;         // device alias of h_tc_err
   int* h_tc_err = nullptr;         // host-mapped flag: set when a bounded MMA wait timed out
   int64_t tc_ngroups = 0, tc_nentries = 0;
+  unsigned char* d_tc_A = nullptr;  // stored A tiles, 4 KB per group entry (bf16, canonical layout)
+  unsigned char* d_tc_B = nullptr;  // packed source moments, nclusters x 256 columns x 32 B
+  int* d_tc_items = nullptr;        // (group, first entry, end) runs of at most 128 entries
+  int64_t tc_nitems = 0;
   void* d_scratch = nullptr;
   void* d_dofmajor = nullptr;  // dof-major staging of wide S^2 products (ndofs x ncol)
   size_t dofmajor_bytes = 0;
@@ -127,6 +131,17 @@ struct Op {
   int* d_leaf_ids = nullptr;      // 0 .. nleaf-1 (target = source list of the block diagonal)
   float* d_lw = nullptr;          // learned weights per element-local dof (learned.cu)
   int active_precond = 0;         // preconditioner of the running solve (enum bembel_precond_kind)
+  // two-level preconditioner: coarse S^2 space of level coarse_level (coarse.cu)
+  int coarse_level = -1;          // level of the built coarse space (-1: not built)
+  int n1c = 0;                    // coarse functions per direction
+  int64_t ncoarse = 0;            // coarse dofs (6 n1c^2)
+  double* d_R = nullptr;          // 1-D refinement matrix, n1 x n1c row-major
+  int* d_rcol = nullptr;          // per fine row i: first and end nonzero column (2 n1)
+  int* d_rrow = nullptr;          // per coarse column a: first and end nonzero row (2 n1c)
+  double* d_cinv = nullptr;       // A_c^-1, ncoarse x ncoarse row-major (x2 complex)
+  float* d_cinv32 = nullptr;
+  void* d_cbuf = nullptr;         // coarse vectors: restriction and correction (2 x ncoarse x ncol)
+  size_t cbuf_bytes = 0;
 
   bembel_op_info info{};
 };
@@ -157,6 +172,10 @@ void run_assembly_kernels(Op& o);       // tabulation, near field, coupling
 void alloc_assembly_outputs(Op& o);     // Xq, near field, coupling, FP32 near copy
 // MIXED: FP32 points (offsets from element centres) and weights of the far separated order
 void points_f32(Op& o, cudaStream_t s);
+void coupling_f32(Op& o, cudaStream_t s);  // MIXED: d_K32 = float(d_K)
+// MIXED S^2: the FP32 coupling copy that wide FP32 products stream, made on first use
+// (never under graph capture)
+void coupling_f32_prepare(Op& o, int nrhs);
 // several operators sharing (op, degree, q, options): tabulation, one
 // persistent launch for all near-field pairs and coupling blocks, FP32 copies
 void run_assembly_batch(const std::vector<Op*>& ops);
@@ -165,6 +184,7 @@ void run_assembly_batch(const std::vector<Op*>& ops);
 void efie_pair_kernels(Op& o, cudaEvent_t* ev);
 void efie_coupling_assemble(Op& o);  // compressed EFIE: 5 coupling matrices per far block
 void efie_coupling_apply(const Op& o, const double* xh, double* yh, int nrhs, cudaStream_t s);
+void efie_coupling_apply(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s);  // MIXED
 void efie_rhs_local(const Op& o, const double* gx, const double* gw, int G, const double* prm_dev, int nrhs,
                     double* bl, cudaStream_t s);
 void efie_field(const Op& o, const double* rl, const double* gx, const double* gw, int G, const double* pts,
@@ -191,10 +211,17 @@ void tc_prepare(Op& o, int nrhs);                // build the groups if wanted (
 void tc_coupling(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s);
 void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vector<int>& fsrc);
 double tc_selftest(int N);
+bool tc_timeout_probe();  // true when the bounded wait on an unsignalled mbarrier ran out
 // fails with BEMBEL_ETIMEOUT if an earlier tensor-core product on o timed out
 void tc_check(const Op& o);
 // precond.cu
 void precond_setup(Op& o);
+// coarse.cu: coarse correction P A_c^-1 P^T of the two-level and learned preconditioners
+void coarse_setup(Op& o, int nrhs);
+void coarse_apply_add(const Op& o, const void* x, void* y, int nrhs, bool fp32, cudaStream_t s);
+// capi.cu: the dense operator of the same kernel, degree and quadrature on another level
+Op* assemble_level(const Op& o, int level);
+void destroy_op(Op* o);
 // learned.cu
 struct LearnedSet;
 LearnedSet* learned_collect(Op& src, int ns, unsigned long long seed);

@@ -422,43 +422,67 @@ __device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geo
 #pragma unroll
   for (int k = 0; k < NL * NL; ++k) ar[k] = ai[k] = 0.0;
   if constexpr (KIND == kIdentical) {
-    // the rule is symmetric under s <-> t (quadrant sigma maps to -sigma with
-    // the same weight), so half the sub-domains are integrated and the block
-    // is symmetrised at the end: A = M + M^T.
-    const int npts = 4 * G.x * G.y * G.z * G.w;
-    for (int idx = lane; idx < npts; idx += 32) {
-      int sub0, i0, i1, i2, i3;
-      rule_index(idx, G, sub0, i0, i1, i2, i3);
-      // sub-domains with sigma_1 = +1 only (sub & 1 == 0 -> quadrants (+,+), (+,-))
-      const int sub = ((sub0 & 1) << 1) | ((sub0 >> 1) << 2);
-      double s1, s2, t1, t2;
-      const double jac = duffy_point<KIND>(sub, gx[0][i0], gx[1][i1], gx[2][i2], gx[3][i3], s1, s2, t1, t2);
-      const double wt = jac * gw[0][i0] * gw[1][i1] * gw[2][i2] * gw[3][i3];
-      double ls1, ls2, lt1, lt2;
-      apply_cmap(ce, s1, s2, ls1, ls2);
-      apply_cmap(cf, t1, t2, lt1, lt2);
-      double x[3], y[3];
-      gamma_eval(geom, pe, (e1 + ls1) * h, (e2 + ls2) * h, x);
-      gamma_eval(geom, pf, (f1 + lt1) * h, (f2 + lt2) * h, y);
-      const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
-      double gr, gi;
-      kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
-      gr *= wt;
-      gi *= wt;
-      double bs1[D1], bs2[D1], bt1[D1], bt2[D1];
-      bernstein<D>(ls1, bs1);
-      bernstein<D>(ls2, bs2);
-      bernstein<D>(lt1, bt1);
-      bernstein<D>(lt2, bt2);
+    // The rule is symmetric under s <-> t (quadrant sigma maps to -sigma with the same
+    // weight), so half the sub-domains are integrated and the block is symmetrised at the
+    // end: A = M + M^T.  Identical pairs use the identity map (pair code 0), and for fixed
+    // (sub, xi, eta, u1) only the second coordinates s2, t2 move with u2 (s1, t1 and the
+    // Jacobian are fixed), so the sum factorises along these u lines:
+    //   M[i1 i2][j1 j2] += w B_i1(s1) B_j1(t1) sum_u2 w2 G(gamma(s), gamma(t)) B_i2(s2) B_j2(t2)
+    // with (d+1)^2 products per rule point and (d+1)^4 per line instead of (d+1)^4 per point.
+    (void)ce;
+    (void)cf;
+    const int nline = 4 * G.x * G.y * G.z;
+    for (int idx = lane; idx < nline; idx += 32) {
+      int r = idx;
+      const int i0 = r % G.x;
+      r /= G.x;
+      const int i1 = r % G.y;
+      r /= G.y;
+      const int i2 = r % G.z;
+      r /= G.z;
+      // sub-domains with sigma_1 = +1 only (quadrants (+,+), (+,-)), both triangles
+      const int sub = ((r & 1) << 1) | ((r >> 1) << 2);
+      double Sr[D1 * D1], Si[D1 * D1];
+#pragma unroll
+      for (int k = 0; k < D1 * D1; ++k) Sr[k] = Si[k] = 0.0;
+      double s1 = 0.0, t1 = 0.0, jac = 0.0;
+      for (int i3 = 0; i3 < G.w; ++i3) {
+        double s2, t2;
+        jac = duffy_point<KIND>(sub, gx[0][i0], gx[1][i1], gx[2][i2], gx[3][i3], s1, s2, t1, t2);
+        double x[3], y[3];
+        gamma_eval(geom, pe, (e1 + s1) * h, (e2 + s2) * h, x);
+        gamma_eval(geom, pf, (f1 + t1) * h, (f2 + t2) * h, y);
+        const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+        double gr, gi;
+        kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+        gr *= gw[3][i3];
+        gi *= gw[3][i3];
+        double bs2[D1], bt2[D1];
+        bernstein<D>(s2, bs2);
+        bernstein<D>(t2, bt2);
+#pragma unroll
+        for (int a = 0; a < D1; ++a) {
+          const double wr = gr * bs2[a], wi = gi * bs2[a];
+#pragma unroll
+          for (int c = 0; c < D1; ++c) {
+            Sr[a * D1 + c] = fma(wr, bt2[c], Sr[a * D1 + c]);
+            if (CPLX) Si[a * D1 + c] = fma(wi, bt2[c], Si[a * D1 + c]);
+          }
+        }
+      }
+      const double wl = jac * gw[0][i0] * gw[1][i1] * gw[2][i2];
+      double bs1[D1], bt1[D1];
+      bernstein<D>(s1, bs1);
+      bernstein<D>(t1, bt1);
 #pragma unroll
       for (int i = 0; i < NL; ++i) {
-        const double bi = bs1[i % D1] * bs2[i / D1];
-        const double wr = gr * bi, wi = gi * bi;
+        const double wi1 = wl * bs1[i % D1];
 #pragma unroll
         for (int j = 0; j < NL; ++j) {
-          const double bj = bt1[j % D1] * bt2[j / D1];
-          ar[i * NL + j] = fma(wr, bj, ar[i * NL + j]);
-          if (CPLX) ai[i * NL + j] = fma(wi, bj, ai[i * NL + j]);
+          const double f = wi1 * bt1[j % D1];
+          const int k = (i / D1) * D1 + j / D1;
+          ar[i * NL + j] = fma(f, Sr[k], ar[i * NL + j]);
+          if (CPLX) ai[i * NL + j] = fma(f, Si[k], ai[i * NL + j]);
         }
       }
     }

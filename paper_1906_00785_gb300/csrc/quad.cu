@@ -179,6 +179,22 @@ void points_f32(Op& o, cudaStream_t s) {
   launched("k_to_f32");
 }
 
+void coupling_f32(Op& o, cudaStream_t s) {
+  if (!o.d_K32) return;
+  const int C = o.cplx ? 2 : 1;
+  k_to_f32<float><<<1024, 256, 0, s>>>(o.d_K, o.d_K32, o.nfar * (int64_t)o.q2 * o.q2 * (o.efie ? 5 : 1) * C);
+  launched("k_to_f32");
+}
+
+void coupling_f32_prepare(Op& o, int nrhs) {
+  const int C = o.cplx ? 2 : 1;
+  if (o.d_K32 || o.efie || o.nfar == 0 || !o.d_K || o.opts.precision != BEMBEL_PREC_MIXED || nrhs * C < 8 ||
+      capturing())
+    return;
+  o.d_K32 = static_cast<float*>(dev_alloc(sizeof(float) * o.nfar * (int64_t)o.q2 * o.q2 * C));
+  coupling_f32(o, o.stream);
+}
+
 void alloc_assembly_outputs(Op& o) {
   const int C = o.cplx ? 2 : 1;
   const int64_t nN = o.nnear * (int64_t)o.nld * o.nld * C;
@@ -189,6 +205,9 @@ void alloc_assembly_outputs(Op& o) {
   if (nK > 0) o.d_K = static_cast<double*>(dev_alloc(sizeof(double) * nK * C));
   if (o.opts.precision == BEMBEL_PREC_MIXED) {
     o.d_N32 = static_cast<float*>(dev_alloc(sizeof(float) * std::max<int64_t>(nN, 1)));
+    // FP32 copy of the compressed EFIE's stored coupling (it has no on-the-fly form); S^2
+    // operators make theirs at the first wide product (coupling_f32_prepare)
+    if (o.efie && nK > 0) o.d_K32 = static_cast<float*>(dev_alloc(sizeof(float) * nK * C));
     // FP32 kernel evaluation for separated pairs beyond the ring (S^2 operators)
     if (!o.efie && o.npairs_regular_far > 0) {
       const int64_t G2f = int64_t(o.g_reg_far) * o.g_reg_far;
@@ -253,6 +272,7 @@ void run_assembly_kernels(Op& o) {
   if (o.opts.precision == BEMBEL_PREC_MIXED) {
     k_to_f32<float><<<1024, 256, 0, s>>>(o.d_N, o.d_N32, nN);
     launched("k_to_f32");
+    coupling_f32(o, s);
   }
   cuda_check(cudaEventRecord(ev[7], s), "event");
   cuda_check(cudaEventSynchronize(ev[7]), "assembly sync");

@@ -269,6 +269,7 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
     k_to_f32_multi<<<1024, 256, 0, s>>>(d_ms, static_cast<const long long*>(dcpy.p), nmesh);
     launched("k_to_f32_multi");
   }
+  for (Op* o : ops) coupling_f32(*o, s);
   cuda_check(cudaEventRecord(ev[3], s), "event");
   cuda_check(cudaEventSynchronize(ev[3]), "batch sync");
   float t[3] = {0.f, 0.f, 0.f};

@@ -16,6 +16,9 @@
 #include <array>
 #include <map>
 #include <cstring>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <unordered_map>
 
@@ -215,6 +218,7 @@ void efie_moments(Op& o, const std::vector<double>& gx, const std::vector<double
     }
   }
   o.d_V = upload(V);
+  o.d_V32 = upload(std::vector<float>(V.begin(), V.end()));
 }
 
 // S^1 space of App. E on the six patches: global numbering with the edge glue
@@ -393,6 +397,81 @@ int num_threads(int64_t n) {
   return int(std::max<int64_t>(1, std::min<int64_t>({(int64_t)hw, (int64_t)16, (n + 255) / 256})));
 }
 
+// Persistent host workers for the set-up loops (created on first use, kept for the process):
+// creating a team of threads per loop cost more than the loops themselves.  One caller at a
+// time uses the pool; a concurrent caller runs its ranges on its own thread.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool pool;
+    return pool;
+  }
+  // fn(t) for every t in [0, nth), taken one at a time by the workers and the caller
+  void run(int nth, const std::function<void(int)>& fn) {
+    std::unique_lock<std::mutex> busy(use_, std::try_to_lock);
+    if (!busy.owns_lock() || nth <= 1 || workers_.empty()) {
+      for (int t = 0; t < nth; ++t) fn(t);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      job_ = &fn;
+      njob_ = nth;
+      next_ = 0;
+      left_ = nth;
+    }
+    cv_.notify_all();
+    for (;;) {
+      int t;
+      {
+        std::lock_guard<std::mutex> lk(m_);
+        if (next_ >= njob_) break;
+        t = next_++;
+      }
+      fn(t);
+      std::lock_guard<std::mutex> lk(m_);
+      if (--left_ == 0) done_.notify_all();
+    }
+    std::unique_lock<std::mutex> lk(m_);
+    done_.wait(lk, [&] { return left_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  HostPool() {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int n = int(std::min(15u, hw > 1 ? hw - 1 : 0u));
+    for (int i = 0; i < n; ++i) workers_.emplace_back([this] { loop(); });
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& w : workers_) w.join();
+  }
+  void loop() {
+    for (;;) {
+      std::unique_lock<std::mutex> lk(m_);
+      cv_.wait(lk, [&] { return stop_ || next_ < njob_; });
+      if (stop_) return;
+      const int t = next_++;
+      const std::function<void(int)>* f = job_;
+      lk.unlock();
+      (*f)(t);
+      lk.lock();
+      if (--left_ == 0) done_.notify_all();
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex use_, m_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* job_ = nullptr;
+  int njob_ = 0, next_ = 0, left_ = 0;
+  bool stop_ = false;
+};
+
 // Run fn(thread, begin, end) on nth contiguous ranges of [0, n).
 template <typename F>
 void parallel_for_t(int64_t n, int nth, F fn) {
@@ -400,12 +479,8 @@ void parallel_for_t(int64_t n, int nth, F fn) {
     fn(0, 0, n);
     return;
   }
-  std::vector<std::thread> ths;
-  for (int t = 0; t < nth; ++t) {
-    const int64_t a = n * t / nth, b = n * (t + 1) / nth;
-    ths.emplace_back([&fn, t, a, b] { fn(t, a, b); });
-  }
-  for (auto& th : ths) th.join();
+  const std::function<void(int)> task = [&](int t) { fn(t, n * t / nth, n * (t + 1) / nth); };
+  HostPool::get().run(nth, task);
 }
 
 template <typename F>
@@ -820,7 +895,7 @@ void build_structure(Op& o) {
     if (!o.efie) o.d_V = upload(V);
     o.d_T = upload(T);
     std::vector<float> V32(V.begin(), V.end()), T32(T.begin(), T.end());
-    o.d_V32 = upload(V32);
+    if (!o.efie) o.d_V32 = upload(V32);  // the EFIE's three channels are copied in efie_moments
     o.d_T32 = upload(T32);
 
     // cluster interpolation points in R^3

@@ -417,6 +417,7 @@ int gmres_run(const Op& o, const double* b, double* x, int nrhs, double tol, int
   // FP64 bytes cover the FP32 products too; reserved before the graphs capture the address
   ensure_scratch(const_cast<Op&>(o), matvec_scratch_bytes(o, nrhs, false));
   if (fp32) tc_prepare(const_cast<Op&>(o), nrhs);  // tensor-core groups, if used, before capture
+  if (fp32) coupling_f32_prepare(const_cast<Op&>(o), nrhs);
   // dof-major staging for wide products (the FP64 restart residuals need the larger size)
   if (!o.d_e_ptr && nrhs * C >= 32) ensure_dofmajor(const_cast<Op&>(o), sizeof(double) * (size_t)n * nrhs * C);
   DevBuf Vbuf(sizeof(T) * vstride * (m + 1)), wbuf(sizeof(T) * vstride), zbuf(sizeof(T) * vstride),
@@ -600,8 +601,11 @@ int solve_gmres(const Op& o, const void* bv, void* xv, int nrhs, const bembel_so
     cuda_check(cudaStreamWaitEvent(s, e, 0), "wait");
     cudaEventDestroy(e);
   }
-  const bool prec = so.precond == BEMBEL_PRECOND_BLOCK_JACOBI || so.precond == BEMBEL_PRECOND_LEARNED;
+  const bool prec = so.precond == BEMBEL_PRECOND_BLOCK_JACOBI || so.precond == BEMBEL_PRECOND_LEARNED ||
+                    so.precond == BEMBEL_PRECOND_TWO_LEVEL;
   if (prec) precond_setup(const_cast<Op&>(o));
+  if (so.precond == BEMBEL_PRECOND_TWO_LEVEL || so.precond == BEMBEL_PRECOND_LEARNED)
+    coarse_setup(const_cast<Op&>(o), nrhs);
   if (so.precond == BEMBEL_PRECOND_LEARNED && !o.d_lw)
     fail(BEMBEL_EINVAL, "solve: the learned preconditioner needs bembel_learned_attach first");
   const_cast<Op&>(o).active_precond = so.precond;

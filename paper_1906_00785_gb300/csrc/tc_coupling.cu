@@ -199,8 +199,36 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_selftest(const float* __restr
   if (warp == 0) tmem_dealloc(d, ncols);
 }
 
+// One row of a coupling tile: G(pa, pb[b]) / (4 pi) for the 16 source points (real part,
+// or for complex kernels the real (part 0) or imaginary (part 1) part), zero when the
+// row's target does not interact with the source.
+template <bool CPLX>
+__device__ __forceinline__ void tile_row(bool on, float4 pa, const float4* __restrict__ pb, int part, float kre,
+                                         float kim, float (&v)[16]) {
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    float val = 0.f;
+    if (on) {
+      const float4 p = pb[b];
+      const float d0 = pa.x - p.x, d1 = pa.y - p.y, d2 = pa.z - p.z;
+      const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+      const float rinv = rsqrtf(r2) * float(kInv4Pi);
+      if (CPLX) {
+        const float rr = r2 * rsqrtf(r2);
+        float sn, cs;
+        sincosf(kre * rr, &sn, &cs);
+        const float am = (kim != 0.f ? expf(kim * rr) : 1.f) * rinv;
+        val = part == 0 ? am * cs : -am * sn;
+      } else {
+        val = rinv;
+      }
+    }
+    v[b] = val;
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Production kernel.
+// Production kernel, tiles evaluated on the fly.
 // ---------------------------------------------------------------------------
 template <bool CPLX>
 __global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restrict__ gptr, const int* __restrict__ gsrc,
@@ -262,28 +290,7 @@ __global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restric
       {
         float v[16];
         const bool on = tslot < nt && ((mask >> tslot) & 1u);
-        const float4 pa = tpt[tslot * 16 + arow];
-        const float4* pb = pts + (int64_t)sc * 16;
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-          float val = 0.f;
-          if (on) {
-            const float4 p = pb[b];
-            const float d0 = pa.x - p.x, d1 = pa.y - p.y, d2 = pa.z - p.z;
-            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            const float rinv = rsqrtf(r2) * float(kInv4Pi);
-            if (CPLX) {
-              const float rr = r2 * rsqrtf(r2);
-              float sn, cs;
-              sincosf(kre * rr, &sn, &cs);
-              const float am = (kim != 0.f ? expf(kim * rr) : 1.f) * rinv;
-              val = part == 0 ? am * cs : -am * sn;
-            } else {
-              val = rinv;
-            }
-          }
-          v[b] = val;
-        }
+        tile_row<CPLX>(on, tpt[tslot * 16 + arow], pts + (int64_t)sc * 16, part, kre, kim, v);
         store_row16(tA[stage], row, v);
       }
       // B rows: source moments, column n, k = b
@@ -362,6 +369,218 @@ __global__ void __launch_bounds__(kTcThreads) k_coupling_tc(const int* __restric
   if (warp == 0) tmem_dealloc(d, ncols);
 }
 
+// ---------------------------------------------------------------------------
+// Stored tiles.  The A tile of every group entry depends only on the geometry and the
+// wavenumber, so it is evaluated once (tile_row, the same FP32 arithmetic as above) and
+// kept in the canonical layout (4 KB per entry); per product the source moments are
+// packed once per cluster into B tiles (ncol x 16 bf16).  The product kernel then only
+// moves tiles and multiplies: one thread per CTA keeps a ring of kStages stages filled with
+// bulk copies (cp.async.bulk, completion counted in bytes on the stage's "full" mbarrier),
+// issues one tcgen05.mma per entry and commits it to the stage's "empty" mbarrier, which
+// guards the stage's next fill.  Fills run a third of the ring ahead of the MMAs; the other
+// stages hold MMAs in flight (the completion of one MMA is what a fill waits for).  Every wait is bounded: on time-out the CTA records the error, drains and returns.
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 16;  // ring depth: chosen per launch from the shared memory per CTA
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes)
+               : "memory");
+}
+
+// bytes (multiple of 16, 16-byte aligned addresses) global -> shared, counted on m
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(m))
+               : "memory");
+}
+
+// A tiles: block per group, thread per tile row, entries of the group in order.
+template <bool CPLX>
+__global__ void __launch_bounds__(kTcThreads) k_tc_build_a(const int* __restrict__ gptr, const int* __restrict__ gsrc,
+                                                           const unsigned* __restrict__ gmask,
+                                                           const int* __restrict__ gfirst,
+                                                           const int* __restrict__ gcnt, int ngroups,
+                                                           const float4* __restrict__ pts, float kre, float kim,
+                                                           unsigned char* __restrict__ A) {
+  const int row = threadIdx.x;
+  const int tslot = CPLX ? (row >> 1) / 16 : row / 16;
+  const int arow = CPLX ? (row >> 1) % 16 : row % 16;
+  const int part = CPLX ? (row & 1) : 0;
+  for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
+    const int t0 = gfirst[gi], nt = gcnt[gi];
+    const float4 pa = tslot < nt ? pts[(int64_t)(t0 + tslot) * 16 + arow] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = gptr[gi]; e < gptr[gi + 1]; ++e) {
+      float v[16];
+      const bool on = tslot < nt && ((gmask[e] >> tslot) & 1u);
+      tile_row<CPLX>(on, pa, pts + (int64_t)gsrc[e] * 16, part, kre, kim, v);
+      store_row16(A + (int64_t)e * 4096, row, v);
+    }
+  }
+}
+
+// B tiles: B[s] row n (column n of the product), k = b: xh[s][b][n] in bf16.
+__global__ void k_tc_pack_b(const float* __restrict__ xh, int64_t nclusters, int ncol, unsigned char* __restrict__ B) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= nclusters * ncol) return;
+  const int64_t sc = id / ncol;
+  const int n = int(id % ncol);
+  const float* xs = xh + sc * 16 * ncol + n;
+  float v[16];
+#pragma unroll
+  for (int b = 0; b < 16; ++b) v[b] = xs[(int64_t)b * ncol];
+  store_row16(B + sc * (int64_t)ncol * 32, n, v);
+}
+
+// Work items: a run of at most kItemEntries consecutive entries of one group (int3: group,
+// first entry, end), so that the long source lists of a few groups spread over many CTAs;
+// each item's partial product is added to yh (cleared beforehand) with atomics.
+constexpr int kItemEntries = 128;
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kTcThreads)
+    k_coupling_tc_stored(const int3* __restrict__ items, int nitems, const int* __restrict__ gsrc,
+                         const int* __restrict__ gfirst, const int* __restrict__ gcnt,
+                         const unsigned char* __restrict__ A, const unsigned char* __restrict__ B,
+                         float* __restrict__ yh, int ncol, int kStages, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sbytes = 4096u + uint32_t(ncol) * 32u;  // one stage: A tile then B tile
+  const uint32_t ncols = tmem_cols_for(ncol);
+  if (warp == 0) tmem_alloc(&tbase, ncols);
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t d = tbase;
+  const uint32_t idesc = make_idesc(128, ncol);
+  // thread 0's pipeline state, kept across groups
+  uint32_t ph_full[kMaxStages], ph_empty[kMaxStages];
+  bool pending[kMaxStages];  // an MMA committed to empty[st] that nobody has waited for
+  bool filled[kMaxStages];   // a fill of stage st issued and not yet consumed
+  for (int st = 0; st < kStages; ++st) {
+    ph_full[st] = ph_empty[st] = 0u;
+    pending[st] = filled[st] = false;
+  }
+  const int row = tid;
+  const int tslot = CPLX ? (row >> 1) / 16 : row / 16;
+  const int arow = CPLX ? (row >> 1) % 16 : row % 16;
+  const int part = CPLX ? (row & 1) : 0;
+  for (int it = blockIdx.x; it < nitems && !abort_flag; it += gridDim.x) {
+    const int3 item = items[it];
+    const int gi = item.x;
+    const int t0 = gfirst[gi], nt = gcnt[gi];
+    const int e0 = item.y, n = item.z - item.y;
+    if (tid == 0) {
+      bool ok = true;
+      // fill stage j % kStages with entry j once the MMA that last read the stage is done
+      auto load = [&](int j) {
+        const int st = j % kStages;
+        if (pending[st]) {
+          ok = ok && mbar_wait(&empty[st], ph_empty[st]);
+          ph_empty[st] ^= 1u;
+          pending[st] = false;
+        }
+        if (!ok) return;
+        unsigned char* sa = sm + st * sbytes;
+        mbar_expect_tx(&full[st], sbytes);
+        bulk_copy(sa, A + (int64_t)(e0 + j) * 4096, 4096u, &full[st]);
+        bulk_copy(sa + 4096, B + (int64_t)gsrc[e0 + j] * ncol * 32, uint32_t(ncol) * 32u, &full[st]);
+        filled[st] = true;
+      };
+      // fills run `ahead` entries in front; the other kStages - ahead stages hold MMAs in flight
+      const int ahead = max(2, kStages / 3);
+      for (int j = 0; j < ahead && j < n; ++j) load(j);
+      for (int i = 0; i < n && ok; ++i) {
+        if (i + ahead < n) load(i + ahead);
+        const int st = i % kStages;
+        ok = ok && mbar_wait(&full[st], ph_full[st]);
+        ph_full[st] ^= 1u;
+        filled[st] = false;
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t sa = smem_addr(sm + st * sbytes);
+        mma_bf16(d, make_desc(sa, 128, 256), make_desc(sa + 4096, 128, 256), idesc, i > 0 ? 1 : 0);
+        mma_commit(&empty[st]);
+        pending[st] = true;
+      }
+      // the accumulator is read below: wait for every MMA still in flight
+      for (int st = 0; st < kStages; ++st)
+        if (pending[st]) {
+          ok = mbar_wait(&empty[st], ph_empty[st]) && ok;
+          ph_empty[st] ^= 1u;
+          pending[st] = false;
+        }
+      if (!ok) {
+        // copies still in flight land in this CTA's shared memory: wait for them (bounded)
+        for (int st = 0; st < kStages; ++st)
+          if (filled[st]) {
+            mbar_wait(&full[st], ph_full[st]);
+            filled[st] = false;
+          }
+        *reinterpret_cast<volatile int*>(err) = 1;
+        abort_flag = 1;
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (abort_flag) break;
+    for (int c0 = 0; c0 < ncol && n > 0; c0 += 8) {
+      float v[8];
+      tmem_ld8(d + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (!CPLX) {
+        if (tslot < nt) {
+          float* y = yh + ((int64_t)(t0 + tslot) * 16 + arow) * ncol + c0;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) atomicAdd(y + i, v[i]);
+        }
+      } else {
+        float w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
+        if (tslot < nt && part == 0) {
+          float* y = yh + ((int64_t)(t0 + tslot) * 16 + arow) * ncol + c0;
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            atomicAdd(y + i, v[i] - w[i + 1]);
+            atomicAdd(y + i + 1, v[i + 1] + w[i]);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(d, ncols);
+}
+
+// Time-out path of the bounded waits: one thread waits, with a short limit, on an mbarrier
+// that nothing arrives on, and records the expiry.  No TMEM, no copies: nothing to drain.
+__global__ void k_tc_timeout_probe(long long limit, int* __restrict__ err) {
+  __shared__ uint64_t m;
+  if (threadIdx.x == 0) {
+    mbar_init(&m, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool ok = false;
+    for (long long i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(&m, 0);
+    if (!ok) *err = 1;
+  }
+}
+
 }  // namespace
 
 bool tc_coupling_wanted(const Op& o, int nrhs) {
@@ -377,8 +596,43 @@ bool tc_coupling_usable(const Op& o, int nrhs) { return o.d_tc_gptr != nullptr &
 
 // Sibling groups are built on first use (from the far lists on the device), not
 // during assembly: most operators never see a wide enough product.
+// The stored A tiles of every group entry (and the buffer for the packed B tiles); very
+// large operators (more than 8 GiB of tiles) keep evaluating their tiles on the fly.
+static void tc_build_tiles(Op& o) {
+  const size_t abytes = size_t(4096) * std::max<int64_t>(1, o.tc_nentries);
+  if (abytes > (size_t(8) << 30)) return;
+  o.d_tc_A = static_cast<unsigned char*>(dev_alloc(abytes));
+  o.d_tc_B = static_cast<unsigned char*>(dev_alloc(size_t(o.nclusters) * 256 * 32));
+  {
+    std::vector<int> gptr(o.tc_ngroups + 1);
+    cuda_check(cudaMemcpy(gptr.data(), o.d_tc_gptr, sizeof(int) * gptr.size(), cudaMemcpyDeviceToHost), "tc gptr");
+    std::vector<int3> items;
+    for (int64_t g = 0; g < o.tc_ngroups; ++g)
+      for (int e = gptr[g]; e < gptr[g + 1]; e += kItemEntries)
+        items.push_back(make_int3(int(g), e, std::min(e + kItemEntries, gptr[g + 1])));
+    o.tc_nitems = (int64_t)items.size();
+    o.d_tc_items = static_cast<int*>(dev_alloc(sizeof(int3) * std::max<size_t>(1, items.size())));
+    if (!items.empty())
+      cuda_check(cudaMemcpy(o.d_tc_items, items.data(), sizeof(int3) * items.size(), cudaMemcpyHostToDevice),
+                 "tc items");
+  }
+  const int grid = int(std::min<int64_t>(o.tc_ngroups, 152 * 8));
+  if (o.cplx)
+    k_tc_build_a<true><<<grid, kTcThreads, 0, o.stream>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
+                                                          o.d_tc_gcnt, int(o.tc_ngroups),
+                                                          reinterpret_cast<const float4*>(o.d_nodes32), float(o.kre),
+                                                          float(o.kim), o.d_tc_A);
+  else
+    k_tc_build_a<false><<<grid, kTcThreads, 0, o.stream>>>(o.d_tc_gptr, o.d_tc_gsrc, o.d_tc_gmask, o.d_tc_gfirst,
+                                                           o.d_tc_gcnt, int(o.tc_ngroups),
+                                                           reinterpret_cast<const float4*>(o.d_nodes32), 0.f, 0.f,
+                                                           o.d_tc_A);
+  launched("k_tc_build_a");
+}
+
 void tc_prepare(Op& o, int nrhs) {
   if (o.d_tc_gptr || !tc_coupling_wanted(o, nrhs) || capturing()) return;
+
   std::vector<long long> fptr(o.nclusters + 1);
   std::vector<int> fsrc(o.nfar);
   cuda_check(cudaStreamSynchronize(o.stream), "tc groups sync");
@@ -386,6 +640,7 @@ void tc_prepare(Op& o, int nrhs) {
              "far ptr");
   cuda_check(cudaMemcpy(fsrc.data(), o.d_far_src, sizeof(int) * fsrc.size(), cudaMemcpyDeviceToHost), "far src");
   tc_build_groups(o, fptr, fsrc);
+  tc_build_tiles(o);
 }
 
 // CTAs per SM that the TMEM accumulators allow (512 columns per SM), and the
@@ -402,10 +657,48 @@ static int tc_smem_bytes(int ncol, int static_bytes, int* ctas_per_sm) {
   return std::max(need, cap);
 }
 
+// the same residency rule for the stored-tile kernel, whose ring takes as many stages of
+// (4 KB + ncol x 32 B) as the shared memory of one of the resident CTAs holds (4..16)
+static int tc_smem_bytes_stored(int ncol, int static_bytes, int* ctas_per_sm, int* stages) {
+  int cols = 32;
+  while (cols < ncol) cols <<= 1;
+  // as many CTAs per SM as their TMEM columns allow (up to 8), each with a shallow ring:
+  // measured faster than 2-4 CTAs with deep rings (level-6 Laplace, 32 columns: 1.22 vs
+  // 1.30-1.46 ms per product; level-5 Helmholtz, 64 columns: 0.87 vs 0.87-0.94 ms)
+  const int ctas = std::min(8, 512 / cols);
+  const int sbytes = 4096 + ncol * 32;
+  const int per_cta = kSmPerSm / ctas - kSmReserved - static_bytes - 128;
+  *stages = std::max(4, std::min(kMaxStages, per_cta / sbytes));
+  const int need = *stages * sbytes;
+  const int cap = kSmPerSm / (ctas + 1) - kSmReserved - static_bytes + 128;
+  *ctas_per_sm = ctas;
+  return std::max(need, cap);
+}
+
 void tc_coupling(const Op& o, const float* xh, float* yh, int nrhs, cudaStream_t s) {
   const int ncol = nrhs * (o.cplx ? 2 : 1);
   cudaFuncAttributes fa{};
   int ctas = 1;
+  if (o.d_tc_A) {  // stored A tiles: pack B, then the copy + MMA pipeline
+    k_tc_pack_b<<<int((o.nclusters * ncol + 255) / 256), 256, 0, s>>>(xh, o.nclusters, ncol, o.d_tc_B);
+    launched("k_tc_pack_b");
+    auto run = [&](auto kernel) {
+      cuda_check(cudaFuncGetAttributes(&fa, kernel), "tc attributes");
+      int stages = 4;
+      const int smem = tc_smem_bytes_stored(ncol, int(fa.sharedSizeBytes), &ctas, &stages);
+      cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "tc smem");
+      const int grid = int(std::max<int64_t>(1, std::min<int64_t>(o.tc_nitems, int64_t(152) * ctas)));
+      kernel<<<grid, kTcThreads, smem, s>>>(reinterpret_cast<const int3*>(o.d_tc_items), int(o.tc_nitems),
+                                            o.d_tc_gsrc, o.d_tc_gfirst, o.d_tc_gcnt, o.d_tc_A, o.d_tc_B, yh, ncol,
+                                            stages, o.d_tc_err);
+    };
+    if (o.cplx)
+      run(k_coupling_tc_stored<true>);
+    else
+      run(k_coupling_tc_stored<false>);
+    launched("k_coupling_tc_stored");
+    return;
+  }
   if (o.cplx) {
     cuda_check(cudaFuncGetAttributes(&fa, k_coupling_tc<true>), "tc attributes");
     const int smem = tc_smem_bytes(ncol, int(fa.sharedSizeBytes), &ctas);
@@ -490,6 +783,16 @@ void tc_build_groups(Op& o, const std::vector<long long>& fptr, const std::vecto
 void tc_check(const Op& o) {
   if (o.h_tc_err && *static_cast<volatile int*>(o.h_tc_err))
     fail(BEMBEL_ETIMEOUT, "a tensor-core MMA completion wait timed out in an earlier product on this operator");
+}
+
+bool tc_timeout_probe() {
+  DevBuf err(sizeof(int));
+  cuda_check(cudaMemset(err.p, 0, sizeof(int)), "probe err");
+  k_tc_timeout_probe<<<1, 32>>>(1ll << 14, static_cast<int*>(err.p));
+  launched("k_tc_timeout_probe");
+  int h = 0;
+  cuda_check(cudaMemcpy(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost), "probe read");
+  return h != 0;
 }
 
 double tc_selftest(int N) {

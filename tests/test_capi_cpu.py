@@ -58,7 +58,7 @@ def test_binding_loads_and_reports_errors(built_lib):
         bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=[1.0, 2.0])
     g = bem.bembel_geom_create()
     with pytest.raises(bem.BembelError) as ei:
-        bem.bembel_assemble(g, bem.BEMBEL_MAXWELL_SL, 4.0, 2, 2, 4, precision=bem.BEMBEL_PREC_MIXED)  # FP64 only
+        bem.bembel_assemble(g, bem.BEMBEL_MAXWELL_SL, 4.0, 2, 2, 4, knot_repetition=2)  # S^1: repetition 1
     assert ei.value.code == bem.BEMBEL_EUNSUPPORTED
     with pytest.raises(bem.BembelError) as ei:
         bem.bembel_assemble(g, bem.BEMBEL_MAXWELL_SL, 0.0, 2, 2, 0)  # EFIE needs kappa != 0

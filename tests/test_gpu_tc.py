@@ -21,6 +21,16 @@ def test_tc_selftest_exact(n):
     assert bem.bembel_tc_selftest(n) == 0.0
 
 
+def test_bounded_wait_times_out_and_device_stays_usable():
+    """The time-out path of the bounded mbarrier waits: a wait on a barrier that nothing
+    signals runs out after its short poll limit and is reported as BEMBEL_ETIMEOUT; the
+    context stays usable (a self-test MMA right after it is exact)."""
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_tc_selftest(0)
+    assert ei.value.code == bem.BEMBEL_ETIMEOUT
+    assert bem.bembel_tc_selftest(64) == 0.0
+
+
 @pytest.mark.parametrize("op,k,nrhs,tc_used", [("laplace", 0.0, 16, False), ("laplace", 0.0, 32, True),
                                                ("laplace", 0.0, 128, True), ("helmholtz", 3.0, 16, False),
                                                ("helmholtz", 3.0, 32, True), ("helmholtz", 3.0, 64, True)])
