@@ -625,9 +625,13 @@ def main():
 
     # quadrature orders for 1e-6 relative block accuracy, 50x below the q = 4 far-field
     # interpolation error (~5e-5): autotuned once, cached for the run
+    # the leaf level and the FP32 coupling storage are chosen by timing (leaf_level -1); the
+    # oracle legs use WORKLOAD["leaf"], the tuner's choice on this workload recorded there
     tuned_opts, tune = bem.bembel_autotune(geom, bem.BEMBEL_LAPLACE_SL, 0.0, w["level"], w["p"],
                                            quad_tol=w["quad_tol"], far_tol=1e-4, q_max=w["q"], eta=w["eta"],
-                                           leaf_level=w["leaf"], stream=stream.cuda_stream)
+                                           leaf_level=-1, precision=bem.BEMBEL_PREC_MIXED,
+                                           stream=stream.cuda_stream)
+    leaf = tuned_opts.leaf_level
 
     def assemble(precision):
         o = bem.bembel_opts_default()
@@ -637,8 +641,8 @@ def main():
             for i in range(4):
                 getattr(o, f)[i] = getattr(tuned_opts, f)[i]
         return bem.bembel_assemble(geom, bem.BEMBEL_LAPLACE_SL, 0.0, w["level"], w["p"], w["q"], opts=o,
-                                   eta=w["eta"], leaf_level=w["leaf"], precision=precision,
-                                   stream=stream.cuda_stream)
+                                   eta=w["eta"], leaf_level=leaf, precision=precision,
+                                   far_fp32_stored=tuned_opts.far_fp32_stored, stream=stream.cuda_stream)
 
     state = {}
 
@@ -717,6 +721,9 @@ def main():
     bem.bembel_solve(opmx, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)  # warm (builds D^-1)
     infomx = bem.bembel_solve(opmx, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)
     infomx_np = bem.bembel_solve(opmx, b, x, 1, tol=1e-8)
+    # two-level preconditioner: the first solve includes its set-up (coarse assembly + inverse)
+    infomx_2l_first = bem.bembel_solve(opmx, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_TWO_LEVEL)
+    infomx_2l = bem.bembel_solve(opmx, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_TWO_LEVEL)
     bem.bembel_solve(op64, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)  # warm (builds D^-1)
     info64_bj = bem.bembel_solve(op64, b, x, 1, tol=1e-8, precond=bem.BEMBEL_PRECOND_BLOCK_JACOBI)
 
@@ -819,7 +826,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": "laplace_h2_sphere6_L6_p1_q4_eta1.6", "ndofs": n1, "nrhs": 1, "level": w["level"],
-                   "degree": w["p"], "q": w["q"], "eta": w["eta"], "leaf_level": w["leaf"],
+                   "degree": w["p"], "q": w["q"], "eta": w["eta"], "leaf_level": leaf,
+                   "leaf_level_oracle": w["leaf"], "far_fp32_stored": tuned_opts.far_fp32_stored,
                    "quadrature": f"autotuned for {w['quad_tol']:g} relative block accuracy: separated pairs "
                                  f"{tune['g_regular']}^2 per element next to the touching pairs, "
                                  f"{tune['g_regular_far']}^2 beyond, Duffy per-variable orders identical "
@@ -831,9 +839,14 @@ def main():
         "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
         "roofline": roofline, "cpu_baseline": cpu,
         "assembly_ms": opinfo["setup_ms"] + opinfo["assemble_ms"], "assembly_setup_ms": opinfo["setup_ms"],
+        "assembly_setup_stage_ms": dict(zip(("corner_ids", "balls_block_tree", "pair_lists",
+                                             "extraction_moments_points", "tables_rest"),
+                                            opinfo["setup_phase_ms"])),
         "assembly_kernels_ms": opinfo["assemble_ms"], "phase_ms": dict(zip(names, ph)),
         "gmres": {"mixed_bj_ms": infomx["solve_ms"], "mixed_bj_iters": infomx["iterations"],
                   "mixed_noprec_ms": infomx_np["solve_ms"], "mixed_noprec_iters": infomx_np["iterations"],
+                  "mixed_two_level_ms": infomx_2l["solve_ms"], "mixed_two_level_iters": infomx_2l["iterations"],
+                  "mixed_two_level_with_setup_ms": infomx_2l_first["solve_ms"],
                   "mixed_refinements": infomx["refinements"], "mixed_relres": infomx["rel_residual"],
                   "fp64_ms": info64["solve_ms"], "fp64_iters": info64["iterations"],
                   "fp64_relres": info64["rel_residual"], "speedup_vs_fp64": info64["solve_ms"] / infomx["solve_ms"],

@@ -153,6 +153,11 @@ typedef struct {
    * EINVAL above).  1 <= coarse_level <= level; 0 = max(0, level - 3) (default 0).
    * S^2 operators with knot_repetition 1 only (EUNSUPPORTED otherwise). */
   int coarse_level;
+  /* FP32 products with fewer than 8 real columns (MIXED operators): 0 evaluates the
+   * far-field coupling on the fly from the FP32 cluster points (default), 1 streams
+   * an FP32 copy of the stored coupling (made at the first FP32 product, outside graph
+   * capture).  Wider products always use the stored copy or the tensor cores. */
+  int far_fp32_stored;
 } bembel_opts;
 
 /* Counters describing an assembled operator (host struct). */
@@ -182,6 +187,10 @@ typedef struct {
    * whole batch's, 1-5 are zero) */
   double phase_ms[8];
   int64_t n_pairs_regular_far; /* separated pairs integrated at g_regular_far      */
+  /* host wall time per set-up stage (part of setup_ms): 0 element corner ids, 1 cluster
+   * balls + block tree, 2 near-field pair lists, 3 extraction, moments, transfers and
+   * cluster points, 4 quadrature tables and the rest */
+  double setup_phase_ms[5];
 } bembel_op_info;
 
 /* Solver options and report (Sec. 4.6: GMRES, restarted). */
@@ -215,6 +224,11 @@ typedef struct {
   int g_identical_var[4], g_edge_var[4], g_vertex_var[4]; /* chosen per-variable Duffy orders  */
   int g_regular_far;                              /* separated pairs beyond the ring          */
   double err_regular_far;
+  int leaf_level;                                 /* chosen (or given) leaf level              */
+  double leaf_score_ms[2];                        /* set-up + assembly + 100 products at leaf
+                                                     L-1, L-2 (0: not tried, -1: no memory)   */
+  int far_fp32_stored;                            /* chosen FP32 coupling storage (MIXED)      */
+  double fp32_product_ms[2];                      /* FP32 product: on the fly, stored copy     */
 } bembel_tune_report;
 
 /* Defaults: tol 1e-8, restart 30, max_iter 1000, NONE, refine 1. */
@@ -313,7 +327,13 @@ int bembel_op_destroy(bembel_op* op);
  * fastest of 8..128 for the FP64 matvec.  inout (options used for the sampling
  * assembly: eta, leaf level, stream) receives g_regular, g_identical, g_edge,
  * g_vertex, g_singular and bsr_chunk; rep (may be NULL) receives the choices,
- * q and the error estimates.  Assembles and releases one operator internally.
+ * q and the error estimates.  When inout->leaf_level < 0 the leaf level is chosen
+ * too: operators at the chosen orders and q with leaves on levels L-1 and L-2 are
+ * assembled and scored by host set-up + assembly + 100 products (FP32 for MIXED
+ * options, else FP64), and for MIXED options the FP32 product of the chosen layout is
+ * timed with on-the-fly and stored FP32 coupling (inout->leaf_level and
+ * inout->far_fp32_stored receive the choices).  Assembles and releases these
+ * operators internally.
  * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED. */
 int bembel_autotune(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
                     double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep);

@@ -54,7 +54,8 @@ class Opts(C.Structure):
                 ("tensor_cores", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p), ("g_identical_var", C.c_int * 4),
                 ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4), ("g_regular_far", C.c_int),
-                ("knot_repetition", C.c_int), ("kdiam", C.c_double), ("coarse_level", C.c_int)]
+                ("knot_repetition", C.c_int), ("kdiam", C.c_double), ("coarse_level", C.c_int),
+                ("far_fp32_stored", C.c_int)]
 
 
 class OpInfo(C.Structure):
@@ -63,7 +64,7 @@ class OpInfo(C.Structure):
         "n_pairs_identical", "n_pairs_edge", "n_pairs_vertex", "near_bytes", "far_bytes")] + [
         ("leaf_level", C.c_int), ("q", C.c_int), ("degree", C.c_int), ("level", C.c_int),
         ("assemble_ms", C.c_double), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 8),
-        ("n_pairs_regular_far", C.c_int64)]
+        ("n_pairs_regular_far", C.c_int64), ("setup_phase_ms", C.c_double * 5)]
 
 
 class TuneReport(C.Structure):
@@ -72,7 +73,8 @@ class TuneReport(C.Structure):
                 ("err_edge", C.c_double), ("err_vertex", C.c_double), ("err_far", C.c_double),
                 ("chunk_ms", C.c_double * 5), ("tune_ms", C.c_double), ("g_identical_var", C.c_int * 4),
                 ("g_edge_var", C.c_int * 4), ("g_vertex_var", C.c_int * 4), ("g_regular_far", C.c_int),
-                ("err_regular_far", C.c_double)]
+                ("err_regular_far", C.c_double), ("leaf_level", C.c_int), ("leaf_score_ms", C.c_double * 2),
+                ("far_fp32_stored", C.c_int), ("fp32_product_ms", C.c_double * 2)]
 
 
 class BatchItem(C.Structure):
@@ -132,6 +134,11 @@ def lib():
     L.bembel_near_block.argtypes = [vp, ci, ci, ci, ci, ci, ci, C.POINTER(dbl)]
     L.bembel_eval_h2.argtypes = [vp, vp, i64, vp, ci, ci, dbl, vp]
     L.bembel_sphere_grid.argtypes = [dbl, ci, C.POINTER(dbl)]
+    L.bembel_precond_apply.argtypes = [vp, ci, vp, vp, ci, ci]
+    missing = [n for n in EXPORTED if n not in ("bembel_last_error", "bembel_kernel_launches")
+               and getattr(L, n).argtypes is None]
+    if missing:  # an undeclared signature would pass 64-bit pointers as C ints
+        raise RuntimeError(f"capi: no ctypes signature for {missing}")
     for n in EXPORTED:
         if n not in ("bembel_opts_default", "bembel_solve_opts_default", "bembel_last_error",
                      "bembel_kernel_launches"):
@@ -270,7 +277,7 @@ def bembel_autotune(geom: Geometry, op: int, k: complex, level: int, p: int, qua
     _check(lib().bembel_autotune(geom.handle, op, k.real, k.imag, level, p, quad_tol, far_tol, q_max, C.byref(o),
                                  C.byref(rep)))
     out = {f: getattr(rep, f) for f, _ in TuneReport._fields_}
-    for key in ("chunk_ms", "g_identical_var", "g_edge_var", "g_vertex_var"):
+    for key in ("chunk_ms", "g_identical_var", "g_edge_var", "g_vertex_var", "leaf_score_ms", "fp32_product_ms"):
         out[key] = list(getattr(rep, key))
     return o, out
 
@@ -339,6 +346,7 @@ def bembel_op_info_get(op: Operator) -> dict:
     _check(lib().bembel_op_info_get(op.handle, C.byref(inf)))
     out = {f: getattr(inf, f) for f, _ in OpInfo._fields_}
     out["phase_ms"] = list(inf.phase_ms)
+    out["setup_phase_ms"] = list(inf.setup_phase_ms)
     return out
 
 

@@ -203,6 +203,95 @@ double kernel_interp_error(const Op& o, int q, const std::vector<std::pair<int, 
 
 namespace bembel {
 
+namespace {
+
+// Device time of one product (mean of 5 after a warm-up), FP32 or FP64, one column.
+double product_ms(Op& o, bool fp32) {
+  const int C = o.cplx ? 2 : 1;
+  const size_t el = fp32 ? sizeof(float) : sizeof(double);
+  DevBuf x(el * o.ndofs * C), y(el * o.ndofs * C);
+  cuda_check(cudaMemsetAsync(x.p, 0, el * o.ndofs * C, o.stream), "x");
+  cudaEvent_t e0, e1;
+  cuda_check(cudaEventCreate(&e0), "event");
+  cuda_check(cudaEventCreate(&e1), "event");
+  matvec_device(o, x.p, y.p, 1, fp32, o.stream);
+  cuda_check(cudaEventRecord(e0, o.stream), "event");
+  for (int it = 0; it < 5; ++it) matvec_device(o, x.p, y.p, 1, fp32, o.stream);
+  cuda_check(cudaEventRecord(e1, o.stream), "event");
+  cuda_check(cudaEventSynchronize(e1), "event");
+  float ms = 0.f;
+  cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / 5.0;
+}
+
+}  // namespace
+
+// Leaf level and FP32 coupling storage by timing (inout->leaf_level < 0 only): operators
+// with the chosen orders and q at leaf levels L-1 and L-2 are assembled, each scored by
+// host set-up + assembly + kTunedProducts products (FP32 for MIXED, else FP64), and the
+// cheapest is kept.  For MIXED operators the FP32 product of the chosen layout is then
+// timed with the coupling evaluated on the fly and with a stored FP32 copy.
+constexpr int kTunedProducts = 100;
+
+static void choose_layout(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q, bembel_opts* inout,
+                   bembel_tune_report& r) {
+  r.leaf_level = inout->leaf_level < 0 ? (level > 0 ? level - 1 : 0) : inout->leaf_level;
+  r.far_fp32_stored = inout->far_fp32_stored;
+  if (inout->leaf_level >= 0 || level < 2 || q == 0) return;
+  const bool mixed = inout->precision == BEMBEL_PREC_MIXED;
+  double best = 1e300;
+  int best_leaf = r.leaf_level;
+  for (int c = 0; c < 2; ++c) {
+    const int leaf = level - 1 - c;
+    if (leaf < 1) break;
+    bembel_opts o = *inout;
+    o.leaf_level = leaf;
+    o.far_fp32_stored = 0;
+    bembel_op* h = nullptr;
+    const int rc = bembel_assemble(g, op, k_re, k_im, level, p, q, &o, &h);
+    if (rc == BEMBEL_ENOMEM) {
+      r.leaf_score_ms[c] = -1.0;  // does not fit: not a candidate
+      continue;
+    }
+    if (rc != BEMBEL_OK) fail(rc, std::string("autotune: ") + bembel_last_error());
+    try {
+      Op& oc = *reinterpret_cast<Op*>(h);
+      const double score = oc.info.setup_ms + oc.info.assemble_ms + kTunedProducts * product_ms(oc, mixed);
+      r.leaf_score_ms[c] = score;
+      if (score < best) {
+        best = score;
+        best_leaf = leaf;
+      }
+    } catch (...) {
+      bembel_op_destroy(h);
+      throw;
+    }
+    bembel_op_destroy(h);
+  }
+  r.leaf_level = best_leaf;
+  inout->leaf_level = best_leaf;
+  if (!mixed) return;
+  bembel_opts o = *inout;
+  bembel_op* h = nullptr;
+  const int rc = bembel_assemble(g, op, k_re, k_im, level, p, q, &o, &h);
+  if (rc != BEMBEL_OK) fail(rc, std::string("autotune: ") + bembel_last_error());
+  try {
+    Op& oc = *reinterpret_cast<Op*>(h);
+    r.fp32_product_ms[0] = product_ms(oc, true);
+    oc.opts.far_fp32_stored = 1;
+    coupling_f32_prepare(oc, 1);
+    r.fp32_product_ms[1] = oc.d_K32 ? product_ms(oc, true) : -1.0;
+  } catch (...) {
+    bembel_op_destroy(h);
+    throw;
+  }
+  bembel_op_destroy(h);
+  r.far_fp32_stored = (r.fp32_product_ms[1] > 0 && r.fp32_product_ms[1] < r.fp32_product_ms[0]) ? 1 : 0;
+  inout->far_fp32_stored = r.far_fp32_stored;
+}
+
 int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, int p, double quad_tol,
                                double far_tol, int q_max, bembel_opts* inout, bembel_tune_report* rep) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -384,6 +473,7 @@ int autotune_impl(bembel_geom* g, int op, double k_re, double k_im, int level, i
     throw;
   }
   bembel_op_destroy(handle);
+  choose_layout(g, op, k_re, k_im, level, p, r.q, inout, r);
   r.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (rep) *rep = r;
   return BEMBEL_OK;

@@ -267,6 +267,8 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
   if (rep > 1 && op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE takes knot_repetition 1");
   if (opts.coarse_level < 0 || opts.coarse_level > level)
     fail(BEMBEL_EINVAL, "assemble: coarse_level must be in [0, level]");
+  if (opts.far_fp32_stored != 0 && opts.far_fp32_stored != 1)
+    fail(BEMBEL_EINVAL, "assemble: far_fp32_stored must be 0 or 1");
   Op* res = new Op();
   res->rep = rep;
   res->geom = reinterpret_cast<GeomHandle*>(g)->g;

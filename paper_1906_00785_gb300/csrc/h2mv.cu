@@ -1008,6 +1008,14 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
         launch_bsr_rows<T, true>(o.d_far_ptr, o.d_far_src, o.nclusters, K, xh, yh, q2, nrhs, s);
       else
         launch_bsr_rows<T, false>(o.d_far_ptr, o.d_far_src, o.nclusters, K, xh, yh, q2, nrhs, s);
+    } else if (fp32 && K && o.opts.far_fp32_stored) {
+      // narrow products streaming the stored FP32 coupling (chosen by the autotuner)
+      if (o.cplx)
+        launch_bsr<T, true, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s,
+                                   o.bsr_chunk);
+      else
+        launch_bsr<T, false, false>(o.d_far_tgt, o.d_far_src, o.nfar, K, nullptr, 0.f, 0.f, xh, yh, q2, nrhs, s,
+                                    o.bsr_chunk);
     } else if (o.cplx) {
       if (fp32)
         launch_bsr<T, true, true>(o.d_far_tgt, o.d_far_src, o.nfar, nullptr, o.d_nodes32, float(o.kre),

@@ -531,11 +531,14 @@ __device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geo
 }
 
 // Coupling entry id = blk * q2^2 + a * q2 + b (row-major block):
-// K[blk][a][b] = G(node_a(target), node_b(source)) / (4 pi).
+// K[blk][a][b] = G(node_a(target), node_b(source)) / (4 pi).  f32k (MIXED operators):
+// the difference and r^2 in FP64, the kernel value in FP32 (relative error ~1e-7, far
+// below the interpolation error of the far field), stored in FP64 so that the FP64
+// residual products of the refinement apply one fixed operator.
 template <bool CPLX>
 __device__ __forceinline__ void coupling_entry(int64_t id, const int* __restrict__ tgt, const int* __restrict__ src,
                                                const double* __restrict__ nodes, int q2, double kre, double kim,
-                                               double* __restrict__ K) {
+                                               double* __restrict__ K, bool f32k = false) {
   const int64_t per = (int64_t)q2 * q2;
   const int64_t blk = id / per;
   const int r = int(id % per);
@@ -544,7 +547,14 @@ __device__ __forceinline__ void coupling_entry(int64_t id, const int* __restrict
   const double* xb = nodes + ((int64_t)src[blk] * q2 + b) * 3;
   const double d0 = xa[0] - xb[0], d1 = xa[1] - xb[1], d2 = xa[2] - xb[2];
   double gr, gi;
-  kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+  if (f32k) {
+    float fr, fi;
+    kernel_value_f(CPLX, float(d0 * d0 + d1 * d1 + d2 * d2), float(kre), float(kim), fr, fi);
+    gr = fr;
+    gi = fi;
+  } else {
+    kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
+  }
   if (CPLX) {
     K[id * 2] = gr * kInv4Pi;
     K[id * 2 + 1] = gi * kInv4Pi;

@@ -117,10 +117,11 @@ void launch_singular(int grid, cudaStream_t s, const PairRec* pairs, int64_t npa
 // Thread per coupling entry.
 template <bool CPLX>
 __global__ void k_coupling(const int* __restrict__ tgt, const int* __restrict__ src, int64_t nfar,
-                           const double* __restrict__ nodes, int q2, double kre, double kim, double* __restrict__ K) {
+                           const double* __restrict__ nodes, int q2, double kre, double kim, double* __restrict__ K,
+                           bool f32k) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= nfar * (int64_t)q2 * q2) return;
-  coupling_entry<CPLX>(id, tgt, src, nodes, q2, kre, kim, K);
+  coupling_entry<CPLX>(id, tgt, src, nodes, q2, kre, kim, K, f32k);
 }
 
 template <typename T>
@@ -188,8 +189,8 @@ void coupling_f32(Op& o, cudaStream_t s) {
 
 void coupling_f32_prepare(Op& o, int nrhs) {
   const int C = o.cplx ? 2 : 1;
-  if (o.d_K32 || o.efie || o.nfar == 0 || !o.d_K || o.opts.precision != BEMBEL_PREC_MIXED || nrhs * C < 8 ||
-      capturing())
+  if (o.d_K32 || o.efie || o.nfar == 0 || !o.d_K || o.opts.precision != BEMBEL_PREC_MIXED ||
+      (nrhs * C < 8 && !o.opts.far_fp32_stored) || capturing())
     return;
   o.d_K32 = static_cast<float*>(dev_alloc(sizeof(float) * o.nfar * (int64_t)o.q2 * o.q2 * C));
   coupling_f32(o, o.stream);
@@ -259,12 +260,13 @@ void run_assembly_kernels(Op& o) {
     efie_coupling_assemble(o);
   } else if (o.nfar > 0) {
     const int64_t n = nK;
+    const bool f32k = o.opts.precision == BEMBEL_PREC_MIXED;
     if (o.cplx)
       k_coupling<true><<<grid_for(n, 256), 256, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre,
-                                                        o.kim, o.d_K);
+                                                        o.kim, o.d_K, f32k);
     else
       k_coupling<false><<<grid_for(n, 256), 256, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre,
-                                                         o.kim, o.d_K);
+                                                         o.kim, o.d_K, f32k);
     launched("k_coupling");
   }
   cuda_check(cudaEventRecord(ev[6], s), "event");

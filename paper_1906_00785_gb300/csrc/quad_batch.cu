@@ -32,6 +32,7 @@ struct MeshWork {
   const float4* Xqf32;  // MIXED: FP32 far-order points (regular_pair_f32), else null
   const double* cen;
   const float* BWf32;
+  int f32k;             // MIXED: coupling entries evaluated in FP32 (coupling_entry)
   double kre, kim, h;
   int64_t nelem;
   double* Xq;
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_assemble_multi(const MeshWork* 
       default: {
         const long long per = (long long)q2 * q2;
         for (long long id = first * per + lane; id < last * per; id += 32)
-          coupling_entry<CPLX>(id, m.far_tgt, m.far_src, m.nodes, q2, m.kre, m.kim, m.K);
+          coupling_entry<CPLX>(id, m.far_tgt, m.far_src, m.nodes, q2, m.kre, m.kim, m.K, m.f32k != 0);
         break;
       }
     }
@@ -186,6 +187,7 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
     w.BWf = o.d_BW_far;
     w.Xqf = o.d_Xq_far;
     w.Xqf32 = reinterpret_cast<const float4*>(o.d_Xq_far32);
+    w.f32k = o.opts.precision == BEMBEL_PREC_MIXED ? 1 : 0;
     w.cen = o.d_cen;
     w.BWf32 = o.d_BW_far32;
     w.kre = o.kre;

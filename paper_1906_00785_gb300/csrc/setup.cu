@@ -646,6 +646,13 @@ void build_structure(Op& o) {
   const int nld = o.nld, nloc = o.nloc;
   const long long blk2 = (long long)nld * nld;
 
+  auto tstage = std::chrono::steady_clock::now();
+  auto stage_done = [&](int k) {  // host time per set-up stage, into the operator's report
+    const auto now = std::chrono::steady_clock::now();
+    o.info.setup_phase_ms[k] += std::chrono::duration<double, std::milli>(now - tstage).count();
+    tstage = now;
+  };
+
   // ---- element corner ids (physical matching, App. D) --------------------------
   // A grid node inside a patch belongs to that patch alone; the nodes on patch
   // boundaries are matched across patches by rounded position.
@@ -681,6 +688,8 @@ void build_structure(Op& o) {
         cid[e * 4 + c] = node[patch * nn + (i1 + (c & 1)) + int64_t(nel1 + 1) * (i2 + (c >> 1))];
     }
   }
+
+  stage_done(0);
 
   // ---- cluster balls on levels 0..leaf -----------------------------------------
   o.lvl_off.assign(o.leaf + 2, 0);
@@ -802,6 +811,8 @@ void build_structure(Op& o) {
     o.d_near_tgt = upload(ntgt);
   }
 
+  stage_done(1);
+
   // ---- element pairs of the near field (classified on the device) -----------------
   {
     std::vector<int> cid32(cid.begin(), cid.end());
@@ -847,6 +858,8 @@ void build_structure(Op& o) {
     dev_free(d_cid);
     dev_free(d_cnt);
   }
+
+  stage_done(2);
 
   // ---- Bezier extraction (1-D, per element index); S^1: signed CSR with glue ------
   if (!o.efie) o.d_ex = upload(extraction_1d(d, nel1, o.rep));
@@ -946,6 +959,8 @@ void build_structure(Op& o) {
     o.d_nodes32 = upload(nodes32);
   }
 
+  stage_done(3);
+
   // ---- quadrature tables -------------------------------------------------------------
   {
     std::vector<double> gx, gw;
@@ -990,6 +1005,8 @@ void build_structure(Op& o) {
     rg.insert(rg.end(), gw.begin(), gw.end());
     o.d_gauss = upload(rg);
   }
+
+  stage_done(4);
 
   // ---- report -------------------------------------------------------------------------
   bembel_op_info& in = o.info;

@@ -46,6 +46,12 @@ def test_binding_loads_and_reports_errors(built_lib):
     L = bem.lib()
     for n in declared_functions():
         assert hasattr(L, n)
+        # every call with arguments has a ctypes signature: an undeclared one would pass
+        # 64-bit device pointers as C ints
+        if n not in ("bembel_last_error", "bembel_kernel_launches"):
+            assert getattr(L, n).argtypes is not None, n
+    # NULL operator / vectors and unknown kinds are rejected before any device work
+    assert L.bembel_precond_apply(None, 1, None, None, 1, 0) == bem.BEMBEL_EINVAL
     # argument validation happens before any device work
     o = bem.bembel_opts_default()
     assert abs(o.eta - 1.6) < 1e-15 and o.leaf_level == -1
