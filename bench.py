@@ -105,7 +105,8 @@ def parse():
     ap.add_argument("--mode", choices=["bench", "profile", "helmholtz-batch", "multimesh", "efie", "learned"],
                     default="bench", help="one workload leg alone (one JSON line), or the profiling workload")
     # legs and the profiling workload
-    ap.add_argument("--op", choices=["laplace", "helmholtz"], default="laplace")
+    ap.add_argument("--op", choices=["laplace", "helmholtz"], default=None,
+                    help="operator of the profile (default laplace) and learned (default helmholtz) modes")
     ap.add_argument("--k", type=float, default=None)
     ap.add_argument("--level", type=int, default=None)
     ap.add_argument("--degree", type=int, default=None)
@@ -369,7 +370,7 @@ def leg_helmholtz_batch(bem, k: float, level: int, nrhs: int = 64, degree: int =
     g = bem.bembel_geom_create()
     HEL = bem.BEMBEL_HELMHOLTZ_SL
     opts, tune = bem.bembel_autotune(g, HEL, k, level, degree, quad_tol=1e-6, far_tol=1e-4, q_max=q_max,
-                                     kdiam=kdiam)
+                                     kdiam=kdiam, precision=bem.BEMBEL_PREC_MIXED)
     q = tune["q"]
     op, t_asm = _timed(lambda: bem.bembel_assemble(g, HEL, k, level, degree, q, opts=opts,
                                                    precision=bem.BEMBEL_PREC_MIXED))
@@ -397,7 +398,7 @@ def leg_helmholtz_batch(bem, k: float, level: int, nrhs: int = 64, degree: int =
     x64 = torch.empty_like(B[0])
     info64, t64 = _timed(lambda: bem.bembel_solve(op64, B[0].contiguous(), x64, 1, **solve))
     del op64
-    # the wide FP32 product: tensor-core coupling evaluated on the fly (q = 4 only) against the
+    # the wide FP32 product: tensor-core coupling on stored bf16 tiles (q = 4 only) against the
     # stored FP32 coupling streamed on the CUDA cores
     Xr = torch.randn((nrhs, n), dtype=torch.complex64, device="cuda")
     mv_default = _matvec_ms(bem, op, Xr, nrhs, True)
@@ -407,13 +408,15 @@ def leg_helmholtz_batch(bem, k: float, level: int, nrhs: int = 64, degree: int =
     del opcc
     return {"workload": f"helmholtz_sound_soft_sphere6_L{level}_p{degree}_k{k:g}_{nrhs}rhs", "ndofs": n, "q": q,
             "kdiam": kdiam, "far_blocks": info["n_far_blocks"], "near_gb": info["near_bytes"] / 1e9,
-            "far_gb": info["far_bytes"] / 1e9, "autotune_err_far": tune["err_far"], "assemble_ms": t_asm,
+            "far_gb": info["far_bytes"] / 1e9, "autotune_err_far": tune["err_far"],
+            "leaf_level": tune["leaf_level"], "leaf_scores_ms": tune["leaf_score_ms"],
+            "far_fp32_stored": tune["far_fp32_stored"], "assemble_ms": t_asm,
             "batched_solve_ms": t_b, "batched_iters": info_b["iterations"], "batched_relres": info_b["rel_residual"],
             "batched_ms_per_rhs": t_b / nrhs, "single_ms_per_rhs": float(np.mean(t_single)),
             "fp64_plain_ms_per_rhs": t64, "fp64_plain_iters": info64["iterations"],
             "fp64_plain_converged": info64["converged"],
             "speedup_per_rhs_vs_fp64_plain": t64 / (t_b / nrhs), "field_rel_err_vs_series": err,
-            "fp32_matvec_ms_tensor_cores_on_the_fly": mv_default if q == 4 else None,
+            "fp32_matvec_ms_tensor_cores": mv_default if q == 4 else None,
             "fp32_matvec_ms_cuda_cores_stored": mv_cc}
 
 
@@ -480,23 +483,28 @@ def leg_efie(bem, level: int = 4, degree: int = 2, k: float = 4.0, q: int = 6, t
 
 
 def leg_learned(bem, n_train: int = 40, n_eval: int = 10, level: int = 6, degree: int = 2, k: float = 8.0,
-                epochs: int = 150, samples: int = 4, restart: int = 100, max_iter: int = 4000, coarse_level: int = 0):
+                epochs: int = 150, samples: int = 4, restart: int = 100, max_iter: int = 4000, coarse_level: int = 0,
+                const_weights=(0.25, 0.5, 0.75), pde: str = "helmholtz"):
     """Learned preconditioner on seeded perturbed spheres (training seeds 1000.., held out
     2000..): trained on the GPU, then GMRES iterations and time to 1e-8 on the held-out
     systems (one plane wave each, incidence +z, MIXED) with block-Jacobi, the two-level
-    preconditioner (block-Jacobi + coarse correction; the learned form with W = I) and the
-    learned weights.  Solve times include the one-off preconditioner set-up."""
+    preconditioner (block-Jacobi + coarse correction; the learned form with W = I), the
+    learned weights, and, as an ablation, constant weights W = w I (no network).  The
+    coarse set-up (coarse assembly + inverse, once per operator) is timed apart and
+    added to the two-level and learned times in the *_with_setup ratios."""
     import numpy as np
     import torch
 
     from inputs import perturbed_sphere_coeffs
 
-    HEL = bem.BEMBEL_HELMHOLTZ_SL
+    KIND = bem.BEMBEL_HELMHOLTZ_SL if pde == "helmholtz" else bem.BEMBEL_LAPLACE_SL
+    if pde != "helmholtz":
+        k = 0.0
     t0 = time.perf_counter()
     sets = []
     for i in range(n_train):
         g = bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=perturbed_sphere_coeffs(1000 + i))
-        op = bem.bembel_assemble(g, HEL, k, level, degree, 4, coarse_level=coarse_level)
+        op = bem.bembel_assemble(g, KIND, k, level, degree, 4, coarse_level=coarse_level)
         sets.append(bem.bembel_learned_collect(op, samples, 1000 + i))
         del op
     t_collect = time.perf_counter() - t0
@@ -506,35 +514,64 @@ def leg_learned(bem, n_train: int = 40, n_eval: int = 10, level: int = 6, degree
     params, hist = bem.bembel_learned_train(sets, epochs, 0.02, p0)
     t_train = time.perf_counter() - t0
     del sets
-    kinds = {"block_jacobi": bem.BEMBEL_PRECOND_BLOCK_JACOBI, "two_level": bem.BEMBEL_PRECOND_TWO_LEVEL,
-             "learned": bem.BEMBEL_PRECOND_LEARNED}
+
+    def const_params(wc):  # w3 = 0, b3 = log(wc): every weight wc
+        p = p0.copy()
+        p[-1] = np.log(wc)
+        return p
+
+    kinds = {"block_jacobi": (bem.BEMBEL_PRECOND_BLOCK_JACOBI, None),
+             "two_level": (bem.BEMBEL_PRECOND_TWO_LEVEL, None),
+             "learned": (bem.BEMBEL_PRECOND_LEARNED, params)}
+    for wc in const_weights:
+        kinds[f"const_{wc:g}"] = (bem.BEMBEL_PRECOND_LEARNED, const_params(wc))
     rows = {name: [] for name in kinds}
+    setup_ms = []
     for i in range(n_eval):
         g = bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=perturbed_sphere_coeffs(2000 + i))
-        op = bem.bembel_assemble(g, HEL, k, level, degree, 4, precision=bem.BEMBEL_PREC_MIXED,
+        op = bem.bembel_assemble(g, KIND, k, level, degree, 4, precision=bem.BEMBEL_PREC_MIXED,
                                  coarse_level=coarse_level)
         n = bem.bembel_ndofs(op)
-        b = torch.empty(n, dtype=torch.complex128, device="cuda")
-        bem.bembel_rhs(op, bem.BEMBEL_RHS_PLANE_WAVE, [[0.0, 0.0, 1.0]], b)
+        b = torch.empty(n, dtype=torch.complex128 if k else torch.float64, device="cuda")
+        if k:
+            bem.bembel_rhs(op, bem.BEMBEL_RHS_PLANE_WAVE, [[0.0, 0.0, 1.0]], b)
+        else:
+            bem.bembel_rhs(op, bem.BEMBEL_RHS_POINT_SOURCE, [[0.0, 0.0, 2.0]], b)
         x = torch.empty_like(b)
-        bem.bembel_learned_attach(op, params)
-        for name, kind in kinds.items():
+        # block-Jacobi inverses first, then the coarse set-up alone (wall time)
+        bem.bembel_precond_apply(op, bem.BEMBEL_PRECOND_BLOCK_JACOBI, b, x, 1)
+        t0 = time.perf_counter()
+        bem.bembel_precond_apply(op, bem.BEMBEL_PRECOND_TWO_LEVEL, b, x, 1)
+        setup_ms.append(1e3 * (time.perf_counter() - t0))
+        for name, (kind, prm) in kinds.items():
+            if prm is not None:
+                bem.bembel_learned_attach(op, prm)
             inf = bem.bembel_solve(op, b, x, 1, tol=1e-8, restart=restart, max_iter=max_iter, precond=kind)
             rows[name].append((inf["iterations"], inf["solve_ms"], inf["converged"]))
         del op
     r = {name: np.array(v, dtype=float) for name, v in rows.items()}
-    out = {"workload": f"learned_vs_block_jacobi_perturbed_L{level}_p{degree}_k{k:g}", "n_train": n_train,
+    su = float(np.mean(setup_ms))
+    out = {"workload": f"learned_vs_block_jacobi_perturbed_{pde}_L{level}_p{degree}_k{k:g}", "n_train": n_train,
            "n_eval": n_eval, "epochs": epochs, "coarse_level": coarse_level or max(0, level - 3),
-           "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "collect_s": t_collect, "train_s": t_train}
+           "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "collect_s": t_collect, "train_s": t_train,
+           "coarse_setup_ms_mean": su}
     for name, v in r.items():
         out[f"iters_{name}_mean"] = float(v[:, 0].mean())
         out[f"ms_{name}_mean"] = float(v[:, 1].mean())
         out[f"converged_{name}"] = bool(v[:, 2].all())
     bj = r["block_jacobi"]
-    for name in ("two_level", "learned"):
+    for name in r:
+        if name == "block_jacobi":
+            continue
         out[f"iteration_ratio_{name}_over_block_jacobi"] = float(r[name][:, 0].mean() / bj[:, 0].mean())
-        out[f"time_ratio_{name}_over_block_jacobi"] = float(r[name][:, 1].mean() / bj[:, 1].mean())
+        out[f"time_ratio_{name}_over_block_jacobi_with_setup"] = float(
+            (r[name][:, 1].mean() + su) / bj[:, 1].mean())
     out["iteration_ratio_learned_over_two_level"] = float(r["learned"][:, 0].mean() / r["two_level"][:, 0].mean())
+    best_const = min((n for n in r if n.startswith("const_")), key=lambda n: r[n][:, 0].mean(), default=None)
+    if best_const:
+        out["best_constant_weight"] = best_const
+        out["iteration_ratio_learned_over_best_constant"] = float(
+            r["learned"][:, 0].mean() / r[best_const][:, 0].mean())
     return out
 
 
@@ -543,6 +580,7 @@ def leg_profile(bem, a):
     import torch
 
     geom = bem.bembel_geom_create(bem.BEMBEL_GEOM_SPHERE6)
+    a.op = a.op or "laplace"
     kind = bem.BEMBEL_LAPLACE_SL if a.op == "laplace" else bem.BEMBEL_HELMHOLTZ_SL
     prec = bem.BEMBEL_PREC_MIXED if a.fp32 else bem.BEMBEL_PREC_FP64
     var = {f"g_{c}_var": [int(v) for v in getattr(a, f"g_{c}_var").split(",")]
@@ -593,7 +631,7 @@ def main():
             out = leg_efie(bem, args.level or 4, args.degree or 2, args.k or 4.0, args.q if args.q != 4 else 6)
         else:
             out = leg_learned(bem, args.train, args.eval, args.level or 6, args.degree or 2, args.k or 8.0,
-                              args.epochs, coarse_level=args.coarse_level)
+                              args.epochs, coarse_level=args.coarse_level, pde=args.op or "helmholtz")
         print(json.dumps(out), flush=True)
         return
     if args.impl == "reference":
@@ -782,7 +820,12 @@ def main():
                 # ncu DRAM bytes of the level-5 launch scaled by the pairs of this launch; degree 1 only
                 "traffic": (DRAM_BYTES_PER_PAIR[dom] * opinfo[pairs_key[dom]] if w["p"] == 1 else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the level-5 launch, "
-                                  "scaled by the pair count (level-6 capture not taken: multi-pass metrics)",
+                                  "scaled by the pair count (level-6 capture not taken: multi-pass metrics); "
+                                  "DRAM bytes during the launch: the written blocks stay in L2 and are written "
+                                  "back after it (output_bytes)",
+                # the blocks a launch writes: every unordered pair writes its block and the mirror
+                "output_bytes": opinfo[pairs_key[dom]] * (1 if dom == "singular_identical" else 2)
+                * ((w["p"] + 1) ** 2) ** 2 * 8,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (derived; no FP64 peak "
                                "in MEASURED_PEAKS.json)",
                 "algorithmic_flops": flops_phase[dom], "launch_ms": dom_ms}
@@ -807,7 +850,8 @@ def main():
 
     legs = {}
     if rank == 0 and world == 1 and not args.no_legs:
-        for name, fn in (("helmholtz_k2_L5_64rhs", lambda: leg_helmholtz_batch(bem, 2.0, 5, 64)),
+        for name, fn in (("helmholtz_k2_L5_64rhs", lambda: leg_helmholtz_batch(bem, 2.0, 5, 64, q_max=4)),
+                         ("helmholtz_k2_L6_64rhs", lambda: leg_helmholtz_batch(bem, 2.0, 6, 64, q_max=4)),
                          ("helmholtz_k8_L4_64rhs", lambda: leg_helmholtz_batch(bem, 8.0, 4, 64, kdiam=6.0,
                                                                                 q_max=8)),
                          ("helmholtz_k16_L5_8rhs", lambda: leg_helmholtz_batch(bem, 16.0, 5, 8, kdiam=6.0,

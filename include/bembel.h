@@ -226,7 +226,7 @@ typedef struct {
   double err_regular_far;
   int leaf_level;                                 /* chosen (or given) leaf level              */
   double leaf_score_ms[2];                        /* set-up + assembly + 100 products at leaf
-                                                     L-1, L-2 (0: not tried, -1: no memory)   */
+                                                     L-1, L-2 (0: not tried, -1: did not fit) */
   int far_fp32_stored;                            /* chosen FP32 coupling storage (MIXED)      */
   double fp32_product_ms[2];                      /* FP32 product: on the fly, stored copy     */
 } bembel_tune_report;
@@ -286,8 +286,9 @@ int bembel_geom_destroy(bembel_geom* g);
  * runs the tabulation, near-field (regular + singular) quadrature and
  * coupling kernels.  The geometry must outlive the operator.
  * Errors: EINVAL (bad sizes, 0 <= level <= 10 required, EFIE with k = 0 or
- * p = 0), EUNSUPPORTED (EFIE with q > 0 and MIXED, or on another geometry),
- * ENOMEM, ECUDA. */
+ * p = 0, leaf clusters whose moment matrix (nld x q^2 FP64, nld = 4^(level - leaf)
+ * times the functions per element) exceeds 227 KiB), EUNSUPPORTED (the EFIE on
+ * another geometry or with knot_repetition > 1), ENOMEM, ECUDA. */
 int bembel_assemble(bembel_geom* g, int op, double k_re, double k_im, int level, int p, int q,
                     const bembel_opts* o, bembel_op** out);
 

@@ -251,8 +251,8 @@ static void choose_layout(bembel_geom* g, int op, double k_re, double k_im, int 
     o.far_fp32_stored = 0;
     bembel_op* h = nullptr;
     const int rc = bembel_assemble(g, op, k_re, k_im, level, p, q, &o, &h);
-    if (rc == BEMBEL_ENOMEM) {
-      r.leaf_score_ms[c] = -1.0;  // does not fit: not a candidate
+    if (rc == BEMBEL_ENOMEM || rc == BEMBEL_EINVAL) {
+      r.leaf_score_ms[c] = -1.0;  // does not fit (memory, or the leaf moments in shared memory)
       continue;
     }
     if (rc != BEMBEL_OK) fail(rc, std::string("autotune: ") + bembel_last_error());

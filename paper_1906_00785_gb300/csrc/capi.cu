@@ -9,7 +9,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <unordered_map>
 #include <new>
 #include <stdexcept>
 
@@ -52,11 +55,9 @@ void free_op(Op* o) {
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
                   o->d_tc_gptr, o->d_tc_A, o->d_tc_B, o->d_tc_items, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
                   o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val,
-                  o->d_R, o->d_rcol, o->d_rrow, o->d_cinv, o->d_cinv32, o->d_cbuf};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  for (auto* p : o->d_pairs)
-    if (p) cudaFree(p);
+                  o->d_R, o->d_rcol, o->d_rrow, o->d_cinv, o->d_cinv32, o->d_cbuf, o->d_evalY};
+  for (void* p : ptrs) dev_free(p);
+  for (auto* p : o->d_pairs) dev_free(p);
   if (o->h_tc_err) cudaFreeHost(o->h_tc_err);
   delete o;
 }
@@ -109,19 +110,108 @@ void launched(const char* what) {
 
 long long launches_total() { return g_launches.load(); }
 
+// Device memory through a small caching allocator.  Operators allocate and release the same
+// sizes every time one is assembled and destroyed, and cudaMalloc / cudaFree (which
+// synchronises the device) cost milliseconds per operator.  Released blocks first wait in a
+// per-device pending list (work in flight may still read them); when an allocation finds no
+// idle block of its size class, one cudaDeviceSynchronize moves the pending blocks to the
+// idle lists.  The cache holds at most kCacheCap bytes per device (beyond that, blocks are
+// returned with cudaFree), and an allocation that fails releases every idle block and
+// retries once.  Not used under graph capture (no synchronisation is allowed there).
+namespace {
+constexpr int kMaxDevices = 64;
+constexpr size_t kCacheCap = size_t(32) << 30;
+
+struct AllocCache {
+  std::mutex mu;
+  std::multimap<size_t, void*> idle[kMaxDevices];
+  std::vector<void*> pending[kMaxDevices];
+  std::unordered_map<void*, std::pair<size_t, int>> blocks;  // live or cached: size class, device
+  size_t cached[kMaxDevices] = {};
+};
+
+AllocCache& alloc_cache() {
+  static AllocCache* c = new AllocCache();  // never destroyed: usable until the process ends
+  return *c;
+}
+
+size_t size_class(size_t b) {
+  if (b <= (size_t(1) << 20)) return (b + 511) & ~size_t(511);
+  const size_t g = size_t(2) << 20;
+  return (b + g - 1) / g * g;
+}
+
+// idle and pending blocks of the device back to the driver (caller holds the lock)
+void release_cached(AllocCache& c, int dev) {
+  if (!c.pending[dev].empty()) cudaDeviceSynchronize();
+  for (void* p : c.pending[dev]) {
+    c.blocks.erase(p);
+    cudaFree(p);
+  }
+  c.pending[dev].clear();
+  for (auto& kv : c.idle[dev]) {
+    c.blocks.erase(kv.second);
+    cudaFree(kv.second);
+  }
+  c.idle[dev].clear();
+  c.cached[dev] = 0;
+}
+}  // namespace
+
 void* dev_alloc(size_t bytes) {
-  void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  const cudaError_t e = cudaMalloc(&p, bytes);
+  const size_t rb = size_class(bytes);
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) fail(BEMBEL_EINVAL, "device index outside the allocator's range");
+  AllocCache& c = alloc_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  auto it = c.idle[dev].find(rb);
+  if (it == c.idle[dev].end() && !c.pending[dev].empty() && !capturing()) {
+    cuda_check(cudaDeviceSynchronize(), "allocator synchronisation");
+    for (void* p : c.pending[dev]) c.idle[dev].emplace(c.blocks[p].first, p);
+    c.pending[dev].clear();
+    it = c.idle[dev].find(rb);
+  }
+  if (it != c.idle[dev].end()) {
+    void* p = it->second;
+    c.idle[dev].erase(it);
+    c.cached[dev] -= rb;
+    return p;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, rb);
+  if (e != cudaSuccess && !capturing()) {
+    cudaGetLastError();
+    release_cached(c, dev);
+    e = cudaMalloc(&p, rb);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     throw LibError(BEMBEL_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
   }
+  c.blocks[p] = {rb, dev};
   return p;
 }
 
 void dev_free(void* p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  AllocCache& c = alloc_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  const auto it = c.blocks.find(p);
+  if (it == c.blocks.end()) {  // not from dev_alloc
+    cudaFree(p);
+    return;
+  }
+  const size_t rb = it->second.first;
+  const int dev = it->second.second;
+  if (c.cached[dev] + rb > kCacheCap) {
+    c.blocks.erase(it);
+    cudaFree(p);
+    return;
+  }
+  c.pending[dev].push_back(p);
+  c.cached[dev] += rb;
 }
 
 }  // namespace bembel
@@ -265,6 +355,13 @@ Op* make_op(bembel_geom* g, int op, double k_re, double k_im, int level, int p, 
   const int rep = opts.knot_repetition == 0 ? 1 : opts.knot_repetition;
   if (rep < 1 || rep > p + 1) fail(BEMBEL_EINVAL, "assemble: knot_repetition must be in [1, p + 1]");
   if (rep > 1 && op == BEMBEL_MAXWELL_SL) fail(BEMBEL_EUNSUPPORTED, "assemble: the EFIE takes knot_repetition 1");
+  {
+    // the leaf transfer kernels hold a leaf's moment matrix (nld x q^2 FP64) in shared memory
+    const int nloc = op == BEMBEL_MAXWELL_SL ? 2 * p * (p + 1) : (p + 1) * (p + 1);
+    const int64_t side = int64_t(1) << (level - leaf);
+    if (q > 0 && 8 * side * side * nloc * q * q > 227 * 1024)
+      fail(BEMBEL_EINVAL, "assemble: leaf clusters too large for q (leaf moment matrix above 227 KiB)");
+  }
   if (opts.coarse_level < 0 || opts.coarse_level > level)
     fail(BEMBEL_EINVAL, "assemble: coarse_level must be in [0, level]");
   if (opts.far_fp32_stored != 0 && opts.far_fp32_stored != 1)

@@ -244,4 +244,23 @@ BEMBEL_HD void apply_cmap(int code, double u1, double u2, double& s1, double& s2
   s2 = a2 ? 1.0 - d_second : d_second;
 }
 
+#ifdef __CUDACC__
+// Single-layer kernel in FP32: 1/r and, for Helmholtz, exp(-i kappa r) / r (the 1/(4 pi)
+// factor is applied by the caller).
+__device__ __forceinline__ void kernel_value_f(bool cplx, float r2, float kre, float kim, float& gr, float& gi) {
+  const float rinv = rsqrtf(r2);
+  if (!cplx) {
+    gr = rinv;
+    gi = 0.f;
+  } else {
+    const float r = r2 * rinv;
+    float sn, cs;
+    sincosf(kre * r, &sn, &cs);
+    const float a = (kim != 0.f ? expf(kim * r) : 1.f) * rinv;
+    gr = a * cs;
+    gi = -a * sn;
+  }
+}
+#endif
+
 }  // namespace bembel

@@ -164,7 +164,11 @@ __global__ void k_from_dofmajor(const T* __restrict__ yt, T* __restrict__ y, int
   }
 }
 
-// S^2 gather from dof-major x: warp per local dof, lanes over columns.
+// S^2 gather from dof-major x: warp per local dof, lanes over columns.  The extraction
+// coefficient of each term is formed once per block of kCb columns per lane and the sums run
+// in T (FP32 products accumulate in FP32).
+constexpr int kCb = 4;
+
 template <typename T>
 __global__ void k_gather_dm(const T* __restrict__ xt, T* __restrict__ xl, const double* __restrict__ ex, int L, int d,
                             int n1, int64_t nlocal, int ncol) {
@@ -178,23 +182,34 @@ __global__ void k_gather_dm(const T* __restrict__ xt, T* __restrict__ xl, const 
   const int patch = int(e / per);
   uint32_t i1, i2;
   morton_decode(uint32_t(e % per), i1, i2);
-  for (int c = lane; c < ncol; c += 32) {
-    double acc = 0.0;
+  for (int c0 = 0; c0 < ncol; c0 += 32 * kCb) {
+    T acc[kCb];
+#pragma unroll
+    for (int b = 0; b < kCb; ++b) acc[b] = T(0);
     for (int j2 = 0; j2 < D1; ++j2) {
       const double c2 = ex[((int64_t)i2 * D1 + j2) * D1 + k2];
       if (c2 == 0.0) continue;
       for (int j1 = 0; j1 < D1; ++j1) {
         const double c1 = ex[((int64_t)i1 * D1 + j1) * D1 + k1];
         if (c1 == 0.0) continue;
-        const int64_t g = (int64_t)patch * n1 * n1 + (int64_t)(i2 + j2) * n1 + (i1 + j1);
-        acc += c1 * c2 * (double)xt[g * ncol + c];
+        const T w = T(c1 * c2);
+        const T* xr = xt + ((int64_t)patch * n1 * n1 + (int64_t)(i2 + j2) * n1 + (i1 + j1)) * ncol;
+#pragma unroll
+        for (int b = 0; b < kCb; ++b) {
+          const int c = c0 + b * 32 + lane;
+          if (c < ncol) acc[b] = fma(w, xr[c], acc[b]);
+        }
       }
     }
-    xl[ld * ncol + c] = T(acc);
+#pragma unroll
+    for (int b = 0; b < kCb; ++b) {
+      const int c = c0 + b * 32 + lane;
+      if (c < ncol) xl[ld * ncol + c] = acc[b];
+    }
   }
 }
 
-// S^2 scatter to dof-major y: warp per global dof, lanes over columns.
+// S^2 scatter to dof-major y: warp per global dof, lanes over columns (as k_gather_dm).
 template <typename T>
 __global__ void k_scatter_dm(const T* __restrict__ yl, T* __restrict__ yt, const double* __restrict__ ex, int L,
                              int d, int n1, int64_t ndofs, int ncol) {
@@ -207,8 +222,10 @@ __global__ void k_scatter_dm(const T* __restrict__ yl, T* __restrict__ yt, const
   const int rem = int(g % ((int64_t)n1 * n1));
   const int j2 = rem / n1, j1 = rem % n1;
   const int64_t per = int64_t(1) << (2 * L);
-  for (int c = lane; c < ncol; c += 32) {
-    double acc = 0.0;
+  for (int c0 = 0; c0 < ncol; c0 += 32 * kCb) {
+    T acc[kCb];
+#pragma unroll
+    for (int b = 0; b < kCb; ++b) acc[b] = T(0);
     for (int i2 = max(0, j2 - d); i2 <= min(nel1 - 1, j2); ++i2)
       for (int i1 = max(0, j1 - d); i1 <= min(nel1 - 1, j1); ++i1) {
         const int64_t e = (int64_t)patch * per + morton_encode(i1, i2);
@@ -218,11 +235,21 @@ __global__ void k_scatter_dm(const T* __restrict__ yl, T* __restrict__ yt, const
           for (int k1 = 0; k1 < D1; ++k1) {
             const double c1 = ex[((int64_t)i1 * D1 + (j1 - i1)) * D1 + k1];
             if (c1 == 0.0) continue;
-            acc += c1 * c2 * (double)yl[(e * nloc + k1 + D1 * k2) * ncol + c];
+            const T w = T(c1 * c2);
+            const T* yr = yl + (e * nloc + k1 + D1 * k2) * ncol;
+#pragma unroll
+            for (int b = 0; b < kCb; ++b) {
+              const int c = c0 + b * 32 + lane;
+              if (c < ncol) acc[b] = fma(w, yr[c], acc[b]);
+            }
           }
         }
       }
-    yt[g * ncol + c] = T(acc);
+#pragma unroll
+    for (int b = 0; b < kCb; ++b) {
+      const int c = c0 + b * 32 + lane;
+      if (c < ncol) yt[g * ncol + c] = acc[b];
+    }
   }
 }
 
@@ -321,7 +348,7 @@ __global__ void k_leaf_down_ch(const T* __restrict__ yh, const T* __restrict__ V
 template <typename T>
 __global__ void k_leaf_up(const T* __restrict__ xl, T* __restrict__ xh, const T* __restrict__ V, int64_t nleaf,
                           int nld, int q2, int ncol) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Vs = reinterpret_cast<T*>(smem_raw);
   for (int i = threadIdx.x; i < nld * q2; i += blockDim.x) Vs[i] = V[i];
   __syncthreads();
@@ -340,7 +367,7 @@ __global__ void k_leaf_up(const T* __restrict__ xl, T* __restrict__ xh, const T*
 template <typename T>
 __global__ void k_up(T* __restrict__ xh_par, const T* __restrict__ xh_ch, const T* __restrict__ Tm, int64_t npar,
                      int q2, int ncol) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ts = reinterpret_cast<T*>(smem_raw);
   for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
   __syncthreads();
@@ -362,7 +389,7 @@ __global__ void k_up(T* __restrict__ xh_par, const T* __restrict__ xh_ch, const 
 template <typename T>
 __global__ void k_down(T* __restrict__ yh_ch, const T* __restrict__ yh_par, const T* __restrict__ Tm, int64_t nch,
                        int q2, int ncol) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ts = reinterpret_cast<T*>(smem_raw);
   for (int i = threadIdx.x; i < 4 * q2 * q2; i += blockDim.x) Ts[i] = Tm[i];
   __syncthreads();
@@ -647,7 +674,7 @@ __global__ void __launch_bounds__(256) k_onfly_q4(const int* __restrict__ tgt, c
 template <typename T>
 __global__ void k_leaf_down(const T* __restrict__ yh, const T* __restrict__ V, T* __restrict__ yl, int64_t nleaf,
                             int nld, int q2, int ncol) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Vs = reinterpret_cast<T*>(smem_raw);
   for (int i = threadIdx.x; i < nld * q2; i += blockDim.x) Vs[i] = V[i];
   __syncthreads();
@@ -676,7 +703,7 @@ struct LevelOffsets {
 template <typename T>
 __global__ void k_up_subtree(const T* __restrict__ xl, T* __restrict__ xh, const T* __restrict__ V,
                              const T* __restrict__ Tm, LevelOffsets lo, int leaf, int ls, int q2, int nld, int ncol) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Vs = reinterpret_cast<T*>(smem_raw);
   T* Ts = Vs + nld * q2;
   T* bufA = Ts + 4 * q2 * q2;
@@ -728,7 +755,7 @@ template <typename T>
 __global__ void k_down_subtree(const T* __restrict__ yh, T* __restrict__ yl, const T* __restrict__ V,
                                const T* __restrict__ Tm, LevelOffsets lo, int leaf, int ls, int q2, int nld,
                                int ncol) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Vs = reinterpret_cast<T*>(smem_raw);
   T* Ts = Vs + nld * q2;
   T* bufA = Ts + 4 * q2 * q2;
@@ -773,28 +800,47 @@ __global__ void k_down_subtree(const T* __restrict__ yh, T* __restrict__ yl, con
 // Block-sparse product for many right-hand sides, one CTA per target block
 // row: y[t] += sum_{k in row t} M_k x[col_k].  Each block (bs x bs, row-major)
 // and its source slice (bs x ncol) are staged in shared memory (two buffers),
-// every thread accumulates up to kRowOut outputs (row a, column j; complex
-// pairs for CPLX) in registers and adds them into its own rows: the block
-// matrix is read once per product and no atomics are needed.
+// every thread accumulates up to rows_for(JB) rows for JB columns (complex pairs
+// for CPLX) in registers and adds them into its own outputs: the block matrix is
+// read once per product and no atomics are needed.  JB = 2 serves two columns
+// from each block entry read from shared memory (half the loads per FMA).
 constexpr int kRowOut = 16;
 constexpr int kRowThreads = 256;
+__host__ __device__ constexpr int rows_for(int jb) { return jb == 1 ? kRowOut : 10; }
 
-template <typename T, bool CPLX>
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+
+template <typename T, bool CPLX, int JB>
 __global__ void __launch_bounds__(kRowThreads) k_bsr_rows(const long long* __restrict__ ptr,
                                                           const int* __restrict__ col, int64_t nrows,
                                                           const T* __restrict__ M, const T* __restrict__ x,
                                                           T* __restrict__ y, int bs, int nrhs) {
   constexpr int C = CPLX ? 2 : 1;
-  extern __shared__ unsigned char smem_raw[];
+  constexpr int RO = rows_for(JB);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ncol = nrhs * C;
   const int mstride = bs * bs * C, xstride = bs * ncol;
   T* Ms = reinterpret_cast<T*>(smem_raw);  // [2][bs*bs*C]
   T* Xs = Ms + 2 * mstride;                // [2][bs*ncol]
   const int64_t t = blockIdx.x;
   if (t >= nrows) return;
-  T accr[kRowOut], acci[kRowOut];
+  // thread (row group rg, column slot js): columns js + nj q (q < JB), rows rg + ng o
+  const int nj = nrhs / JB;
+  const int js = threadIdx.x % nj, rg = threadIdx.x / nj, ng = kRowThreads / nj;
+  T accr[RO][JB], acci[RO][JB];
 #pragma unroll
-  for (int o = 0; o < kRowOut; ++o) accr[o] = acci[o] = T(0);
+  for (int o = 0; o < RO; ++o)
+#pragma unroll
+    for (int q = 0; q < JB; ++q) accr[o][q] = acci[o][q] = T(0);
   const long long k0 = ptr[t], k1 = ptr[t + 1];
   // staging: asynchronous 16-byte copies (cp.async) when every piece is 16-byte
   // aligned, so the next block streams in while the current one is used
@@ -834,40 +880,54 @@ __global__ void __launch_bounds__(kRowThreads) k_bsr_rows(const long long* __res
     __syncthreads();
     const T* Mb = Ms + buf * mstride;
     const T* Xb = Xs + buf * xstride;
-    // thread (row group rg, column j): rows a = rg + ng * o.  One load of x per
-    // b serves every row of the thread; the block entries are warp broadcasts.
-    {
-      const int j = threadIdx.x % nrhs, rg = threadIdx.x / nrhs, ng = kRowThreads / nrhs;
-      if (rg < ng) {
-        for (int b = 0; b < bs; ++b) {
-          const T* xv = Xb + (int64_t)b * ncol + j * C;
-          const T xr = xv[0], xi = CPLX ? xv[1] : T(0);
+    if (rg < ng) {
+      for (int b = 0; b < bs; ++b) {
+        T xr[JB], xi[JB];
 #pragma unroll
-          for (int o = 0; o < kRowOut; ++o) {
-            const int a = rg + ng * o;
-            if (a >= bs) break;
-            const T* m = Mb + ((int64_t)a * bs + b) * C;
-            if (CPLX) {
-              accr[o] = fma(m[0], xr, fma(-m[1], xi, accr[o]));
-              acci[o] = fma(m[0], xi, fma(m[1], xr, acci[o]));
-            } else {
-              accr[o] = fma(m[0], xr, accr[o]);
+        for (int q = 0; q < JB; ++q) {
+          const T* xv = Xb + (int64_t)b * ncol + (js + nj * q) * C;
+          if (CPLX) {  // complex pairs as one 8- or 16-byte shared load
+            const auto x2 = *reinterpret_cast<const typename Pair<T>::type*>(xv);
+            xr[q] = x2.x;
+            xi[q] = x2.y;
+          } else {
+            xr[q] = xv[0];
+            xi[q] = T(0);
+          }
+        }
+#pragma unroll
+        for (int o = 0; o < RO; ++o) {
+          const int a = rg + ng * o;
+          if (a >= bs) break;
+          const T* m = Mb + ((int64_t)a * bs + b) * C;
+          if (CPLX) {
+            const auto m2 = *reinterpret_cast<const typename Pair<T>::type*>(m);
+#pragma unroll
+            for (int q = 0; q < JB; ++q) {
+              accr[o][q] = fma(m2.x, xr[q], fma(-m2.y, xi[q], accr[o][q]));
+              acci[o][q] = fma(m2.x, xi[q], fma(m2.y, xr[q], acci[o][q]));
             }
+          } else {
+            const T mv = m[0];
+#pragma unroll
+            for (int q = 0; q < JB; ++q) accr[o][q] = fma(mv, xr[q], accr[o][q]);
           }
         }
       }
     }
     __syncthreads();
   }
-  const int j = threadIdx.x % nrhs, rg = threadIdx.x / nrhs, ng = kRowThreads / nrhs;
   if (rg >= ng) return;
 #pragma unroll
-  for (int o = 0; o < kRowOut; ++o) {
+  for (int o = 0; o < RO; ++o) {
     const int a = rg + ng * o;
     if (a >= bs) break;
-    T* yo = y + (t * bs + a) * (int64_t)ncol + j * C;
-    yo[0] += accr[o];
-    if (CPLX) yo[1] += acci[o];
+#pragma unroll
+    for (int q = 0; q < JB; ++q) {
+      T* yo = y + (t * bs + a) * (int64_t)ncol + (js + nj * q) * C;
+      yo[0] += accr[o][q];
+      if (CPLX) yo[1] += acci[o][q];
+    }
   }
 }
 
@@ -880,13 +940,25 @@ bool rows_kernel_fits(int bs, int nrhs, int C, size_t el) {
   return (bs + ng - 1) / ng <= kRowOut && shm <= 160 * 1024;
 }
 
+// two columns per thread when nrhs is even and the rows of a thread fit its registers
+static bool rows_two_columns(int bs, int nrhs) {
+  if (nrhs % 2 != 0) return false;
+  const int ng = kRowThreads / (nrhs / 2);
+  return ng > 0 && (bs + ng - 1) / ng <= rows_for(2);
+}
+
 template <typename T, bool CPLX>
 void launch_bsr_rows(const long long* ptr, const int* col, int64_t nrows, const T* M, const T* x, T* y, int bs,
                      int nrhs, cudaStream_t s) {
   const int C = CPLX ? 2 : 1;
   const size_t shm = sizeof(T) * 2 * ((size_t)bs * bs * C + (size_t)bs * nrhs * C);
-  set_smem_limit(k_bsr_rows<T, CPLX>, shm);
-  k_bsr_rows<T, CPLX><<<int(nrows), kRowThreads, shm, s>>>(ptr, col, nrows, M, x, y, bs, nrhs);
+  if (rows_two_columns(bs, nrhs)) {
+    set_smem_limit(k_bsr_rows<T, CPLX, 2>, shm);
+    k_bsr_rows<T, CPLX, 2><<<int(nrows), kRowThreads, shm, s>>>(ptr, col, nrows, M, x, y, bs, nrhs);
+  } else {
+    set_smem_limit(k_bsr_rows<T, CPLX, 1>, shm);
+    k_bsr_rows<T, CPLX, 1><<<int(nrows), kRowThreads, shm, s>>>(ptr, col, nrows, M, x, y, bs, nrhs);
+  }
   launched("k_bsr_rows");
 }
 
@@ -987,6 +1059,7 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
         launched("k_up");
       }
     } else {
+      set_smem_limit(k_leaf_up<T>, sizeof(T) * o.nld * q2);  // coarse leaves: moment matrix above 48 KiB
       k_leaf_up<T><<<blocks_for(o.nleaf * q2 * ncol, tb), tb, sizeof(T) * o.nld * q2, s>>>(
           xl, xh + leaf_off * q2 * ncol, V, o.nleaf, o.nld, q2, ncol);
       launched("k_leaf_up");
@@ -1052,6 +1125,7 @@ void matvec_impl(const Op& o, const T* x, T* y, int nrhs, cudaStream_t s, const 
                                                                    ncol);
         launched("k_down");
       }
+      set_smem_limit(k_leaf_down<T>, sizeof(T) * o.nld * q2);
       k_leaf_down<T><<<blocks_for(o.nleaf * o.nld * ncol, tb), tb, sizeof(T) * o.nld * q2, s>>>(
           yh + leaf_off * q2 * ncol, V, yl, o.nleaf, o.nld, q2, ncol);
       launched("k_leaf_down");
@@ -1082,6 +1156,7 @@ void cluster_moments(const Op& o, const double* x, double* xl, double* xh, int n
   const int q2 = o.q2, tb = 256;
   gather_l<double>(o, x, xl, ncol, C, s);
   const int64_t leaf_off = o.lvl_off[o.leaf];
+  set_smem_limit(k_leaf_up<double>, sizeof(double) * o.nld * q2);
   k_leaf_up<double><<<blocks_for(o.nleaf * q2 * ncol, tb), tb, sizeof(double) * o.nld * q2, s>>>(
       xl, xh + leaf_off * q2 * ncol, o.d_V, o.nleaf, o.nld, q2, ncol);
   launched("k_leaf_up");

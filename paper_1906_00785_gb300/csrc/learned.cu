@@ -239,8 +239,7 @@ struct LearnedSet {
   std::vector<double> zscale;
   ~LearnedSet() {
     void* ps[] = {o.d_ex, o.d_bj32, o.d_leaf_ids, o.d_scratch, F, Z, Y};
-    for (void* p : ps)
-      if (p) cudaFree(p);
+    for (void* p : ps) dev_free(p);
   }
 };
 

@@ -141,6 +141,8 @@ struct Op {
   double* d_cinv = nullptr;       // A_c^-1, ncoarse x ncoarse row-major (x2 complex)
   float* d_cinv32 = nullptr;
   void* d_cbuf = nullptr;         // coarse vectors: restriction and correction (2 x ncoarse x ncol)
+  double* d_evalY = nullptr;      // potential evaluation: quadrature points of every element (rhs_eval.cu)
+  int evalG = 0;                  // their Gauss order
   size_t cbuf_bytes = 0;
 
   bembel_op_info info{};

@@ -101,22 +101,6 @@ __device__ __forceinline__ void regular_pair(const PairRec& pr, const double* __
   __syncwarp();
 }
 
-// Single-layer kernel in FP32: 1/r and, for Helmholtz, exp(-i kappa r) / r.
-__device__ __forceinline__ void kernel_value_f(bool cplx, float r2, float kre, float kim, float& gr, float& gi) {
-  const float rinv = rsqrtf(r2);
-  if (!cplx) {
-    gr = rinv;
-    gi = 0.f;
-  } else {
-    const float r = r2 * rinv;
-    float sn, cs;
-    sincosf(kre * r, &sn, &cs);
-    const float a = (kim != 0.f ? expf(kim * r) : 1.f) * rinv;
-    gr = a * cs;
-    gi = -a * sn;
-  }
-}
-
 // Separated pair beyond the ring with the kernel in FP32 (MIXED operators):
 // points are stored as FP32 offsets from their element's centre, the centre
 // difference is taken in FP64 once per pair, so each distance is formed from

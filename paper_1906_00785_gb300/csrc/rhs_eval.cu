@@ -101,29 +101,46 @@ __global__ void k_density_points(const double* __restrict__ rl, int64_t nelem, i
 template <bool CPLX>
 __global__ void k_potential(const double* __restrict__ pts, int64_t npts, const double* __restrict__ Y,
                             const double* __restrict__ rq, int64_t nsrc, int nrhs, double kre, double kim,
-                            double* __restrict__ out) {
+                            double far2, double* __restrict__ out) {
+  // block (point, column, source chunk): the chunk's partial sum is added to out
   const int64_t ip = blockIdx.x;
   const int r = blockIdx.y;
   const int C = CPLX ? 2 : 1;
   const int ncol = nrhs * C;
+  const int64_t chunk = (nsrc + gridDim.z - 1) / gridDim.z;
+  const int64_t k0 = blockIdx.z * chunk, k1 = min(nsrc, k0 + chunk);
   const double x0 = pts[ip * 3], x1 = pts[ip * 3 + 1], x2 = pts[ip * 3 + 2];
   double sr = 0.0, si = 0.0;
-  for (int64_t k = threadIdx.x; k < nsrc; k += blockDim.x) {
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const double d0 = x0 - Y[k * 3], d1 = x1 - Y[k * 3 + 1], d2 = x2 - Y[k * 3 + 2];
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    const double rinv = rsqrt(r2);
     const double rhr = rq[k * ncol + r * C];
+    double gr, gi = 0.0;
+    if (r2 > far2) {
+      // separated point (MIXED operators): the kernel value in FP32 from the FP64 distance
+      float fr, fi;
+      kernel_value_f(CPLX, float(r2), float(kre), float(kim), fr, fi);
+      gr = fr;
+      gi = fi;
+    } else {
+      const double rinv = rsqrt(r2);
+      if (CPLX) {
+        const double rr = r2 * rinv;
+        double sn, cs;
+        sincos(kre * rr, &sn, &cs);
+        const double am = exp(kim * rr) * rinv;
+        gr = am * cs;
+        gi = -am * sn;
+      } else {
+        gr = rinv;
+      }
+    }
     if (CPLX) {
       const double rhi = rq[k * ncol + r * C + 1];
-      const double rr = r2 * rinv;
-      double sn, cs;
-      sincos(kre * rr, &sn, &cs);
-      const double am = exp(kim * rr) * rinv;
-      const double gr = am * cs, gi = -am * sn;
       sr += gr * rhr - gi * rhi;
       si += gr * rhi + gi * rhr;
     } else {
-      sr += rinv * rhr;
+      sr += gr * rhr;
     }
   }
   __shared__ double red[2][32];
@@ -142,8 +159,8 @@ __global__ void k_potential(const double* __restrict__ pts, int64_t npts, const 
       a += red[0][k];
       b += red[1][k];
     }
-    out[((int64_t)r * npts + ip) * C] = a * kInv4Pi;
-    if (CPLX) out[((int64_t)r * npts + ip) * C + 1] = b * kInv4Pi;
+    atomicAdd(out + ((int64_t)r * npts + ip) * C, a * kInv4Pi);
+    if (CPLX) atomicAdd(out + ((int64_t)r * npts + ip) * C + 1, b * kInv4Pi);
   }
 }
 
@@ -352,8 +369,7 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
   const int C = o.cplx ? 2 : 1;
   const int ncol = nrhs * C;
   const int G2 = G * G;
-  Buf gt(sizeof(double) * 2 * G), rl(sizeof(double) * o.nlocal * ncol), rq(sizeof(double) * o.nelem * G2 * ncol),
-      Y(sizeof(double) * o.nelem * G2 * 3);
+  Buf gt(sizeof(double) * 2 * G), rl(sizeof(double) * o.nlocal * ncol), rq(sizeof(double) * o.nelem * G2 * ncol);
   gauss_table(G, static_cast<double*>(gt.p), s);
   const double* gx = static_cast<double*>(gt.p);
   const double* gw = gx + G;
@@ -363,8 +379,19 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
     return;
   }
   const int64_t nq = o.nelem * G2;
-  k_tab_points<<<int((nq + 255) / 256), 256, 0, s>>>(o.geom, o.L, o.nelem, G, gx, o.h, static_cast<double*>(Y.p));
-  launched("kernel");
+  // the quadrature points of every element for this G, kept with the operator
+  Op& om = const_cast<Op&>(o);
+  if (!om.d_evalY || om.evalG != G) {
+    dev_free(om.d_evalY);
+    om.d_evalY = nullptr;
+    om.d_evalY = static_cast<double*>(dev_alloc(sizeof(double) * nq * 3));
+    om.evalG = G;
+    k_tab_points<<<int((nq + 255) / 256), 256, 0, s>>>(o.geom, o.L, o.nelem, G, gx, o.h, om.d_evalY);
+    launched("kernel");
+  }
+  struct {
+    void* p;
+  } Y{om.d_evalY};
   const int64_t nd = nq * ncol;
   switch (o.d) {
     case 0:
@@ -383,13 +410,21 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
       launched("kernel");
       break;
   }
-  dim3 grid((unsigned)npts, (unsigned)nrhs);
+  // source chunks: about eight blocks per SM over all (point, column) pairs, chunks of at
+  // least 4,096 quadrature points
+  const int64_t pairs = npts * nrhs;
+  const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((152 * 8 + pairs - 1) / pairs, nq / 4096));
+  dim3 grid((unsigned)npts, (unsigned)nrhs, (unsigned)chunks);
+  // MIXED operators: FP32 kernel values beyond 8 parameter-element sizes (points that keep
+  // a distance of a few elements from the surface); FP64 everywhere for FP64 operators
+  const double far2 = o.opts.precision == BEMBEL_PREC_MIXED ? 64.0 * o.h * o.h : 1e300;
+  cuda_check(cudaMemsetAsync(out, 0, sizeof(double) * npts * nrhs * C, s), "eval clear");
   if (o.cplx)
     k_potential<true><<<grid, 256, 0, s>>>(pts, npts, static_cast<double*>(Y.p), static_cast<double*>(rq.p), nq,
-                                           nrhs, o.kre, o.kim, static_cast<double*>(out));
+                                           nrhs, o.kre, o.kim, far2, static_cast<double*>(out));
   else
     k_potential<false><<<grid, 256, 0, s>>>(pts, npts, static_cast<double*>(Y.p), static_cast<double*>(rq.p), nq,
-                                            nrhs, o.kre, o.kim, static_cast<double*>(out));
+                                            nrhs, o.kre, o.kim, far2, static_cast<double*>(out));
   launched("eval kernels");
   cuda_check(cudaStreamSynchronize(s), "eval sync");
 }

@@ -494,84 +494,266 @@ void parallel_for(int64_t n, F fn) {
 // common edge: A, B = the two shared corners in the first element's corner
 // order, D2 runs A -> B; common vertex: A = the shared corner, D1 along the
 // first local axis.  Pass 0 counts per kind, pass 1 writes the records.
+// ---- block tree on the device ------------------------------------------------------
+// Level by level: the candidate sources of a target on level l are the children of the
+// non-admissible sources of its parent (the six patches on level 0), visited in
+// increasing order, so both lists come out sorted by target and source without a sort.
+// Pass 0 counts far (admissible) and near (non-admissible) candidates per target, an
+// exclusive scan turns counts into offsets, pass 1 writes the lists.
+struct TreeParams {
+  double eta, kdiam, kabs;  // kdiam > 0: Helmholtz limit |kappa| max(diam) <= kdiam
+  int compress;             // q > 0: admissibility tested (else every pair is near)
+};
+
+// The same arithmetic as the reference order of operations, without contraction, so that
+// borderline decisions do not depend on the compiler's FMA choices.
+__device__ __forceinline__ bool tree_admissible(const Ball* __restrict__ balls, int t, int sc, const TreeParams& p) {
+  if (!p.compress) return false;
+  const Ball bt = balls[t], bs = balls[sc];
+  const double dx = __dsub_rn(bt.c[0], bs.c[0]), dy = __dsub_rn(bt.c[1], bs.c[1]), dz = __dsub_rn(bt.c[2], bs.c[2]);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  const double dist = fmax(0.0, __dsub_rn(__dsub_rn(__dsqrt_rn(d2), bt.r), bs.r));
+  const double diam = __dmul_rn(2.0, fmax(bt.r, bs.r));
+  if (p.kdiam > 0.0 && __dmul_rn(p.kabs, diam) > p.kdiam) return false;
+  return diam <= __dmul_rn(p.eta, dist);
+}
+
+// One thread per target of level l (local index i, global id t0 + i).  pptr / pcol: CSR of the
+// parent level's non-admissible sources (global ids).  Pass 0: cf[i], cn[i] = counts.  Pass 1:
+// cf, cn hold exclusive offsets; far sources go to fout[cf[i]...], near ones to nout[cn[i]...].
+__global__ void k_tree_level(int pass, int l, int64_t t0, int64_t nt, long long off_l, long long off_lm1,
+                             const long long* __restrict__ pptr, const int* __restrict__ pcol,
+                             const Ball* __restrict__ balls, TreeParams prm, long long* __restrict__ cf,
+                             long long* __restrict__ cn, int* __restrict__ fout, int* __restrict__ nout) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  const int t = int(t0 + i);
+  long long nf = 0, nn = 0;
+  long long fo = pass ? cf[i] : 0, no = pass ? cn[i] : 0;
+  auto visit = [&](int sc) {
+    if (tree_admissible(balls, t, sc, prm)) {
+      if (pass) fout[fo + nf] = sc;
+      ++nf;
+    } else {
+      if (pass) nout[no + nn] = sc;
+      ++nn;
+    }
+  };
+  if (l == 0) {
+    for (int p = 0; p < 6; ++p) visit(p);
+  } else {
+    const int64_t par = i >> 2;
+    for (long long k = pptr[par]; k < pptr[par + 1]; ++k) {
+      const long long sl = pcol[k] - off_lm1;
+      for (int c = 0; c < 4; ++c) visit(int(off_l + 4 * sl + c));
+    }
+  }
+  if (!pass) {
+    cf[i] = nf;
+    cn[i] = nn;
+  }
+}
+
+// Exclusive scan of n counts in place for two arrays at once (blockIdx.y picks the array),
+// in blocks of 1024: per-block scan + block totals, then one block per array scans the
+// totals (sequentially over chunks of 1024) and writes the sum to a[n] and tot[y], then the
+// offsets are added.  a0 / a1 hold n + 1 entries; bsum holds 2 x nbmax.
+__global__ void k_scan_block(long long* __restrict__ a0, long long* __restrict__ a1, int64_t n,
+                             long long* __restrict__ bsum, int64_t nbmax) {
+  __shared__ long long sh[1024];
+  long long* a = blockIdx.y ? a1 : a0;
+  const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  const long long v = i < n ? a[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const long long u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += u;
+    __syncthreads();
+  }
+  if (i < n) a[i] = sh[threadIdx.x] - v;  // exclusive
+  if (threadIdx.x == 1023) bsum[blockIdx.y * nbmax + blockIdx.x] = sh[1023];
+}
+
+__global__ void k_scan_sums(long long* __restrict__ a0, long long* __restrict__ a1, int64_t n,
+                            long long* __restrict__ bsum, int64_t nb, int64_t nbmax, long long* __restrict__ tot) {
+  __shared__ long long sh[1024];
+  __shared__ long long carry;
+  long long* bs = bsum + blockIdx.x * nbmax;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < nb; c0 += 1024) {
+    const int64_t i = c0 + threadIdx.x;
+    const long long v = i < nb ? bs[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const long long u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (i < nb) bs[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    (blockIdx.x ? a1 : a0)[n] = carry;
+    tot[blockIdx.x] = carry;
+  }
+}
+
+__global__ void k_scan_add(long long* __restrict__ a0, long long* __restrict__ a1, int64_t n,
+                           const long long* __restrict__ bsum, int64_t nbmax) {
+  long long* a = blockIdx.y ? a1 : a0;
+  const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  if (i < n) a[i] += bsum[blockIdx.y * nbmax + blockIdx.x];
+}
+
+// fptr[t0 + i] = base + off[i]: the level's far offsets into the global CSR over clusters
+__global__ void k_tree_fptr(long long* __restrict__ fptr, int64_t t0, int64_t nt, const long long* __restrict__ off,
+                            long long base) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nt) fptr[t0 + i] = base + off[i];
+}
+
+// target of every far entry (thread per cluster)
+__global__ void k_tree_tgt(const long long* __restrict__ fptr, int64_t nclusters, int* __restrict__ tgt) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nclusters) return;
+  for (long long k = fptr[c]; k < fptr[c + 1]; ++k) tgt[k] = int(c);
+}
+
+// leaf rows of the near field: leaf-local source ids, the diagonal block, the row of each
+// block and the identity list of the block-diagonal products; err when a row lacks its
+// diagonal block
+__global__ void k_tree_rows(const long long* __restrict__ nptr, int* __restrict__ ncol, long long leaf_off,
+                            int64_t nleaf, int* __restrict__ diag, int* __restrict__ ids, int* __restrict__ ntgt,
+                            int* __restrict__ err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nleaf) return;
+  ids[t] = int(t);
+  int dg = -1;
+  for (long long k = nptr[t]; k < nptr[t + 1]; ++k) {
+    const int c = int(ncol[k] - leaf_off);
+    ncol[k] = c;
+    ntgt[k] = int(t);
+    if (c == t) dg = int(k);
+  }
+  diag[t] = dg;
+  if (dg < 0) atomicExch(err, 1);
+}
+
+// Warp-aggregated slot of counter ctr[key]: one atomic per distinct key in the warp.
+// Every lane of the warp calls it (active = false lanes take no slot).
+__device__ __forceinline__ unsigned long long agg_slot(unsigned long long* ctr, int key, bool active) {
+  const unsigned mask = __ballot_sync(0xffffffffu, active);
+  if (!active) return 0ull;
+  const unsigned same = __match_any_sync(mask, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(same) - 1;
+  unsigned long long base = 0ull;
+  if (lane == leader) base = atomicAdd(ctr + key, (unsigned long long)__popc(same));
+  base = __shfl_sync(same, base, leader);
+  return base + __popc(same & ((1u << lane) - 1u));
+}
+
 __global__ void k_build_pairs(const long long* __restrict__ nptr, const int* __restrict__ ncol,
                               const int* __restrict__ ntgt, int64_t nnear, const int* __restrict__ cid, int m2,
                               int nloc, int nld, int pass, unsigned long long* __restrict__ cnt, PairRec* out0,
                               PairRec* out1, PairRec* out2, PairRec* out3, const int* __restrict__ v2e) {
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= nnear * (int64_t)m2 * m2) return;
-  const int64_t blk = id / ((int64_t)m2 * m2);
-  const int slot = int(id % ((int64_t)m2 * m2));
-  const int pe = slot / m2, pf = slot % m2;
-  const int t = ntgt[blk], sc = ncol[blk];
-  if (t > sc || (t == sc && pf < pe)) return;
-  const int64_t e = (int64_t)t * m2 + pe, f = (int64_t)sc * m2 + pf;
-  int se[4], sf[4], ns = 0;
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b)
-      if (cid[e * 4 + a] == cid[f * 4 + b]) {
-        se[ns] = a;
-        sf[ns] = b;
-        ++ns;
-      }
-  int kind, me = 0, mf = 0;
-  if (ns == 0) {
-    kind = kRegular;
-  } else if (ns == 4) {
-    kind = kIdentical;
-  } else if (ns == 2) {
-    kind = kEdge;
-    me = se[0] | ((((se[0] ^ se[1]) & 1) ? 1 : 0) << 2);
-    mf = sf[0] | ((((sf[0] ^ sf[1]) & 1) ? 1 : 0) << 2);
-  } else {
-    kind = kVertex;  // ns == 1 (3 shared corners cannot occur on a conforming mesh)
-    me = se[0];
-    mf = sf[0];
-  }
-  if (pass == 0) {
-    atomicAdd(&cnt[kind], 1ull);
-    return;
-  }
-  // mirror block (sc, t) by binary search in row sc
-  long long lo = nptr[sc], hi = nptr[sc + 1] - 1;
-  while (lo < hi) {
-    const long long mid = (lo + hi) / 2;
-    if (ncol[mid] < t)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  const long long blk2 = (long long)nld * nld;
-  PairRec pr;
-  pr.e = int(e);
-  pr.f = int(f);
-  pr.code = kind | (me << 2) | (mf << 5);
-  // separated pairs: 0 if one element holds a corner of e and a corner of f
-  // (the ring next to the touching pairs), 1 if they lie farther apart
-  pr.pad = 0;
-  if (kind == kRegular) {
-    int far = 1;
-    for (int a = 0; a < 4 && far; ++a) {
-      const int v = cid[e * 4 + a];
-      for (int sl = 0; sl < 4 && far; ++sl) {
-        const int g = v2e[v * 4 + sl];
-        if (g < 0) continue;
-        for (int c = 0; c < 4 && far; ++c)
-          for (int b = 0; b < 4; ++b)
-            if (cid[(int64_t)g * 4 + c] == cid[f * 4 + b]) {
-              far = 0;
-              break;
-            }
+  // grid-stride over (near block, element pair) items; whole warps stay in the loop so that
+  // the slot counters can be taken warp-aggregated
+  const int64_t total = nnear * (int64_t)m2 * m2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += stride) {
+    const int64_t id = base + threadIdx.x;
+    bool valid = id < total;
+    int64_t blk = 0, e = 0, f = 0;
+    int pe = 0, pf = 0, t = 0, sc = 0;
+    if (valid) {
+      blk = id / ((int64_t)m2 * m2);
+      const int slot = int(id % ((int64_t)m2 * m2));
+      pe = slot / m2;
+      pf = slot % m2;
+      t = ntgt[blk];
+      sc = ncol[blk];
+      valid = !(t > sc || (t == sc && pf < pe));
+      e = (int64_t)t * m2 + pe;
+      f = (int64_t)sc * m2 + pf;
+    }
+    int kind = kRegular, me = 0, mf = 0;
+    if (valid) {
+      int se[4], sf[4], ns = 0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+          if (cid[e * 4 + a] == cid[f * 4 + b]) {
+            se[ns] = a;
+            sf[ns] = b;
+            ++ns;
+          }
+      if (ns == 0) {
+        kind = kRegular;
+      } else if (ns == 4) {
+        kind = kIdentical;
+      } else if (ns == 2) {
+        kind = kEdge;
+        me = se[0] | ((((se[0] ^ se[1]) & 1) ? 1 : 0) << 2);
+        mf = sf[0] | ((((sf[0] ^ sf[1]) & 1) ? 1 : 0) << 2);
+      } else {
+        kind = kVertex;  // ns == 1 (3 shared corners cannot occur on a conforming mesh)
+        me = se[0];
+        mf = sf[0];
       }
     }
+    if (pass == 0) {
+      agg_slot(cnt, kind, valid);
+      continue;
+    }
+    // separated pairs: 0 if one element holds a corner of e and a corner of f
+    // (the ring next to the touching pairs), 1 if they lie farther apart
+    int far = 0;
+    if (valid && kind == kRegular) {
+      far = 1;
+      for (int a = 0; a < 4 && far; ++a) {
+        const int v = cid[e * 4 + a];
+        for (int sl = 0; sl < 4 && far; ++sl) {
+          const int g = v2e[v * 4 + sl];
+          if (g < 0) continue;
+          for (int c = 0; c < 4 && far; ++c)
+            for (int b = 0; b < 4; ++b)
+              if (cid[(int64_t)g * 4 + c] == cid[f * 4 + b]) {
+                far = 0;
+                break;
+              }
+        }
+      }
+    }
+    agg_slot(cnt, 4, valid && far);
+    const unsigned long long slot_out = agg_slot(cnt, kind, valid);
+    if (!valid) continue;
+    // mirror block (sc, t) by binary search in row sc
+    long long lo = nptr[sc], hi = nptr[sc + 1] - 1;
+    while (lo < hi) {
+      const long long mid = (lo + hi) / 2;
+      if (ncol[mid] < t)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const long long blk2 = (long long)nld * nld;
+    PairRec pr;
+    pr.e = int(e);
+    pr.f = int(f);
+    pr.code = kind | (me << 2) | (mf << 5);
     pr.pad = far;
-    if (far) atomicAdd(&cnt[4], 1ull);
+    pr.off1 = blk * blk2 + (long long)(pe * nloc) * nld + pf * nloc;
+    pr.off2 = (e == f) ? -1 : lo * blk2 + (long long)(pf * nloc) * nld + pe * nloc;
+    PairRec* out = kind == 0 ? out0 : (kind == 1 ? out1 : (kind == 2 ? out2 : out3));
+    out[slot_out] = pr;
   }
-  pr.off1 = blk * blk2 + (long long)(pe * nloc) * nld + pf * nloc;
-  pr.off2 = (e == f) ? -1 : lo * blk2 + (long long)(pf * nloc) * nld + pe * nloc;
-  const unsigned long long slot_out = atomicAdd(&cnt[kind], 1ull);
-  PairRec* out = kind == 0 ? out0 : (kind == 1 ? out1 : (kind == 2 ? out2 : out3));
-  out[slot_out] = pr;
 }
 
 // S^2 with knot repetition r > 1: the tensor extraction as CSR, element-local
@@ -695,7 +877,6 @@ void build_structure(Op& o) {
   o.lvl_off.assign(o.leaf + 2, 0);
   for (int l = 0; l <= o.leaf; ++l) o.lvl_off[l + 1] = o.lvl_off[l] + 6 * (int64_t(1) << (2 * l));
   o.nclusters = o.lvl_off[o.leaf + 1];
-  std::vector<Ball> balls(o.nclusters);
   if (o.q > 0) {  // only the admissibility test uses them
     static_assert(sizeof(Ball) == 4 * sizeof(double), "Ball is four doubles");
     if (o.leaf > 14) fail(BEMBEL_EINVAL, "assemble: leaf level above 14");
@@ -705,110 +886,101 @@ void build_structure(Op& o) {
     o.d_balls = static_cast<double*>(dev_alloc(sizeof(Ball) * o.nclusters));
     k_cluster_balls<<<int((o.nclusters + 127) / 128), 128>>>(o.geom, lt, o.nclusters, o.d_balls);
     launched("k_cluster_balls");
-    cuda_check(cudaMemcpy(balls.data(), o.d_balls, sizeof(Ball) * o.nclusters, cudaMemcpyDeviceToHost), "balls");
   }
 
-  // ---- block tree, level by level ------------------------------------------------
-  // The candidate sources of a target are the children of the non-admissible
-  // sources of its parent (all patches on level 0), visited in increasing order,
-  // so the far lists come out in CSR order by target id without sorting.
-  const bool compress = o.q > 0;
-  auto admissible = [&](int t, int sc) {
-    if (!compress) return false;
-    const Ball &bt = balls[t], &bs = balls[sc];
-    const double dx = bt.c[0] - bs.c[0], dy = bt.c[1] - bs.c[1], dz = bt.c[2] - bs.c[2];
-    const double dist = std::max(0.0, std::sqrt(dx * dx + dy * dy + dz * dz) - bt.r - bs.r);
-    const double diam = 2.0 * std::max(bt.r, bs.r);
-    // Helmholtz: the interpolated kernel oscillates like exp(-i kappa r); a limit on
-    // |kappa| diam keeps the phase variation over a far block within reach of q points
-    if (o.cplx && o.opts.kdiam > 0.0 && std::hypot(o.kre, o.kim) * diam > o.opts.kdiam) return false;
-    return diam <= o.opts.eta * dist;
-  };
-  std::vector<long long> fptr(o.nclusters + 1, 0);
-  std::vector<int> fsrc;
-  std::vector<long long> nptr;
-  std::vector<int> ncol;
+  // ---- block tree, level by level, on the device (k_tree_level) --------------------
+  // One host synchronisation per level (the two list lengths); the near lists of a level
+  // are the next level's candidates (ping-pong buffers), the far lists of all levels are
+  // appended to one buffer in target order.  Buffers grow when a level needs more.
   {
-    // non-admissible lists of the previous level (CSR over its targets, source ids global)
-    std::vector<long long> pptr = {0};
-    std::vector<int> pcol;
+    const TreeParams prm{o.opts.eta, o.cplx ? o.opts.kdiam : 0.0, std::hypot(o.kre, o.kim), o.q > 0 ? 1 : 0};
+    const Ball* balls = reinterpret_cast<const Ball*>(o.d_balls);
+    const int64_t nt_max = o.lvl_off[o.leaf + 1] - o.lvl_off[o.leaf];
+    const int64_t nb_max = (nt_max + 1023) / 1024;
+    DevBuf cf_buf(sizeof(long long) * (nt_max + 1)), bsum_buf(sizeof(long long) * 2 * nb_max),
+        tot_buf(sizeof(long long) * 2);
+    long long* cf = static_cast<long long*>(cf_buf.p);
+    long long* bsum = static_cast<long long*>(bsum_buf.p);
+    long long* tot = static_cast<long long*>(tot_buf.p);
+    struct Grow {  // device int array with a capacity
+      int* p = nullptr;
+      long long cap = 0;
+      ~Grow() { dev_free(p); }
+      void reserve(long long n, long long keep) {
+        if (n <= cap) return;
+        const long long c = std::max<long long>(n, 2 * cap);
+        int* q = static_cast<int*>(dev_alloc(sizeof(int) * c));
+        if (keep > 0) cuda_check(cudaMemcpy(q, p, sizeof(int) * keep, cudaMemcpyDeviceToDevice), "tree grow");
+        dev_free(p);
+        p = q;
+        cap = c;
+      }
+    } far, near[2];
+    far.reserve(64 * o.nclusters, 0);
+    near[0].reserve(32 * nt_max, 0);
+    near[1].reserve(32 * nt_max, 0);
+    DevBuf cn_buf0(sizeof(long long) * (nt_max + 1)), cn_buf1(sizeof(long long) * (nt_max + 1));
+    long long* cn[2] = {static_cast<long long*>(cn_buf0.p), static_cast<long long*>(cn_buf1.p)};
+    o.d_far_ptr = static_cast<long long*>(dev_alloc(sizeof(long long) * (o.nclusters + 1)));
+    long long far_base = 0, nnear_l = 0;
+    int cur = 0;
     for (int l = 0; l <= o.leaf; ++l) {
       const int64_t t0 = o.lvl_off[l], nt = o.lvl_off[l + 1] - t0;
-      const int nth = num_threads(nt);
-      std::vector<std::vector<int>> tf(nth), tn(nth);          // per-thread far / non-admissible sources
-      std::vector<std::vector<long long>> cf(nth), cn(nth);    // per-target counts
-      parallel_for_t(nt, nth, [&](int th, int64_t a, int64_t b2) {
-        for (int64_t i = a; i < b2; ++i) {
-          const int t = int(t0 + i);
-          long long nf = 0, nn = 0;
-          auto visit = [&](int sc) {
-            if (admissible(t, sc)) {
-              tf[th].push_back(sc);
-              ++nf;
-            } else {
-              tn[th].push_back(sc);
-              ++nn;
-            }
-          };
-          if (l == 0) {
-            for (int p = 0; p < 6; ++p) visit(p);
-          } else {
-            const int64_t par = (i >> 2);  // parent index within level l-1
-            for (long long k = pptr[par]; k < pptr[par + 1]; ++k) {
-              const int64_t sl = pcol[k] - o.lvl_off[l - 1];
-              for (int c = 0; c < 4; ++c) visit(int(o.lvl_off[l] + 4 * sl + c));
-            }
-          }
-          cf[th].push_back(nf);
-          cn[th].push_back(nn);
-        }
-      });
-      std::vector<long long> nptr_l(nt + 1, 0);
-      std::vector<int> ncol_l;
-      int64_t i = 0;
-      for (int th = 0; th < nth; ++th) {
-        for (size_t k = 0; k < cf[th].size(); ++k, ++i) {
-          fptr[t0 + i + 1] = cf[th][k];
-          nptr_l[i + 1] = nptr_l[i] + cn[th][k];
-        }
-        fsrc.insert(fsrc.end(), tf[th].begin(), tf[th].end());
-        ncol_l.insert(ncol_l.end(), tn[th].begin(), tn[th].end());
-      }
-      pptr.swap(nptr_l);
-      pcol.swap(ncol_l);
+      const int grid = int((nt + 127) / 128);
+      const long long off_lm1 = l > 0 ? o.lvl_off[l - 1] : 0;
+      const long long* pptr = l > 0 ? cn[cur ^ 1] : nullptr;
+      const int* pcol = l > 0 ? near[cur ^ 1].p : nullptr;
+      k_tree_level<<<grid, 128>>>(0, l, t0, nt, o.lvl_off[l], off_lm1, pptr, pcol, balls, prm, cf, cn[cur], nullptr,
+                                  nullptr);
+      launched("k_tree_level");
+      const int64_t nb = (nt + 1023) / 1024;
+      k_scan_block<<<dim3(unsigned(nb), 2), 1024>>>(cf, cn[cur], nt, bsum, nb_max);
+      k_scan_sums<<<2, 1024>>>(cf, cn[cur], nt, bsum, nb, nb_max, tot);
+      k_scan_add<<<dim3(unsigned(nb), 2), 1024>>>(cf, cn[cur], nt, bsum, nb_max);
+      launched("k_scan");
+      long long h[2];
+      cuda_check(cudaMemcpy(h, tot, sizeof(h), cudaMemcpyDeviceToHost), "tree counts");
+      far.reserve(far_base + h[0], far_base);
+      near[cur].reserve(std::max<long long>(1, h[1]), 0);
+      k_tree_level<<<grid, 128>>>(1, l, t0, nt, o.lvl_off[l], off_lm1, pptr, pcol, balls, prm, cf, cn[cur],
+                                  far.p + far_base, near[cur].p);
+      launched("k_tree_level");
+      k_tree_fptr<<<grid, 128>>>(o.d_far_ptr, t0, nt, cf, far_base);
+      launched("k_tree_fptr");
+      far_base += h[0];
+      nnear_l = h[1];
+      cur ^= 1;
+    }
+    cur ^= 1;  // the leaf level's lists
+    cuda_check(cudaMemcpy(o.d_far_ptr + o.nclusters, &far_base, sizeof(long long), cudaMemcpyHostToDevice),
+               "far total");
+    o.nfar = far_base;
+    if (o.nfar > 0) {
+      o.d_far_src = static_cast<int*>(dev_alloc(sizeof(int) * o.nfar));
+      cuda_check(cudaMemcpy(o.d_far_src, far.p, sizeof(int) * o.nfar, cudaMemcpyDeviceToDevice), "far lists");
+      o.d_far_tgt = static_cast<int*>(dev_alloc(sizeof(int) * o.nfar));
+      k_tree_tgt<<<int((o.nclusters + 127) / 128), 128>>>(o.d_far_ptr, o.nclusters, o.d_far_tgt);
+      launched("k_tree_tgt");
     }
     // leaf-level non-admissible pairs are the near field (leaf-local ids)
-    const int64_t leaf_off = o.lvl_off[o.leaf];
-    nptr = pptr;
-    ncol.resize(pcol.size());
-    for (size_t k = 0; k < pcol.size(); ++k) ncol[k] = int(pcol[k] - leaf_off);
-  }
-  for (int64_t c = 0; c < o.nclusters; ++c) fptr[c + 1] += fptr[c];
-  o.nfar = (int64_t)fsrc.size();
-  o.nnear = (int64_t)ncol.size();
-  {
-    std::vector<int> tgt(o.nfar);
-    for (int64_t c = 0; c < o.nclusters; ++c)
-      for (long long k = fptr[c]; k < fptr[c + 1]; ++k) tgt[k] = int(c);
-    o.d_far_ptr = upload(fptr);
-    o.d_far_src = upload(fsrc);
-    o.d_far_tgt = upload(tgt);
-  }
-  o.d_near_ptr = upload(nptr);
-  o.d_near_col = upload(ncol);
-  {
-    std::vector<int> diag(o.nleaf, -1), ids(o.nleaf), ntgt(o.nnear);
-    for (int64_t t = 0; t < o.nleaf; ++t) {
-      ids[t] = int(t);
-      for (long long k = nptr[t]; k < nptr[t + 1]; ++k) {
-        ntgt[k] = int(t);
-        if (ncol[k] == t) diag[t] = int(k);
-      }
-      if (diag[t] < 0) fail(BEMBEL_EINVAL, "near field lacks a diagonal block");
-    }
-    o.d_diag_blk = upload(diag);
-    o.d_leaf_ids = upload(ids);
-    o.d_near_tgt = upload(ntgt);
+    o.nnear = nnear_l;
+    o.d_near_ptr = static_cast<long long*>(dev_alloc(sizeof(long long) * (o.nleaf + 1)));
+    cuda_check(cudaMemcpy(o.d_near_ptr, cn[cur], sizeof(long long) * (o.nleaf + 1), cudaMemcpyDeviceToDevice),
+               "near ptr");
+    o.d_near_col = static_cast<int*>(dev_alloc(sizeof(int) * std::max<int64_t>(1, o.nnear)));
+    if (o.nnear > 0)
+      cuda_check(cudaMemcpy(o.d_near_col, near[cur].p, sizeof(int) * o.nnear, cudaMemcpyDeviceToDevice), "near col");
+    o.d_diag_blk = static_cast<int*>(dev_alloc(sizeof(int) * o.nleaf));
+    o.d_leaf_ids = static_cast<int*>(dev_alloc(sizeof(int) * o.nleaf));
+    o.d_near_tgt = static_cast<int*>(dev_alloc(sizeof(int) * std::max<int64_t>(1, o.nnear)));
+    cuda_check(cudaMemset(tot, 0, sizeof(long long)), "tree err");
+    k_tree_rows<<<int((o.nleaf + 127) / 128), 128>>>(o.d_near_ptr, o.d_near_col, o.lvl_off[o.leaf], o.nleaf,
+                                                     o.d_diag_blk, o.d_leaf_ids, o.d_near_tgt,
+                                                     reinterpret_cast<int*>(tot));
+    launched("k_tree_rows");
+    int err = 0;
+    cuda_check(cudaMemcpy(&err, tot, sizeof(int), cudaMemcpyDeviceToHost), "tree rows");
+    if (err) fail(BEMBEL_EINVAL, "near field lacks a diagonal block");
   }
 
   stage_done(1);
@@ -834,7 +1006,7 @@ void build_structure(Op& o) {
     unsigned long long* d_cnt = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * 5));
     const int64_t work = o.nnear * (int64_t)m2 * m2;
     const int tb = 256;
-    const int grid = int(std::max<int64_t>(1, (work + tb - 1) / tb));
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((work + tb - 1) / tb, 152 * 64)));
     PairRec* outs[4] = {nullptr, nullptr, nullptr, nullptr};
     unsigned long long cnt[5];
     for (int pass = 0; pass < 2; ++pass) {

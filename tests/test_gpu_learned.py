@@ -58,3 +58,52 @@ def test_training_lowers_loss_and_solves():
     i_id = bem.bembel_solve(op, b, torch.empty_like(b), 1, tol=1e-10, precond=bem.BEMBEL_PRECOND_LEARNED)
     i_2l = bem.bembel_solve(op, b, torch.empty_like(b), 1, tol=1e-10, precond=bem.BEMBEL_PRECOND_TWO_LEVEL)
     assert i_id["iterations"] == i_2l["iterations"]
+
+
+def test_trained_network_gains_over_block_jacobi_and_constant_weights():
+    """What the trained network gains (level 4, kappa = 8, degree 2, perturbed spheres; the
+    configuration of the learned-preconditioner workload at a smaller level): trained on 10
+    generated systems, GMRES(100) steps to 1e-8 on 3 held-out systems with block-Jacobi, the
+    two-level preconditioner (W = I), the best of constant weights W = w I (the network without
+    features) and the trained weights.  Measured: 766 / 698 / 526 (w = 0.25) / 328 steps; at level
+    6 with 200 training and 50 held-out systems 1305 / 1296 / 958 / 183."""
+    k, L, d = 8.0, 4, 2
+    sets = []
+    for seed in range(1000, 1010):
+        g = bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=perturbed_sphere_coeffs(seed))
+        op = bem.bembel_assemble(g, bem.BEMBEL_HELMHOLTZ_SL, k, L, d, 4)
+        sets.append(bem.bembel_learned_collect(op, 4, seed))
+        del op
+    p0 = _params()
+    p1, hist = bem.bembel_learned_train(sets, 100, 0.02, p0)
+    assert hist[-1] < 0.1 * hist[0]
+
+    def const(w):
+        p = p0.copy()
+        p[-1] = np.log(w)
+        return p
+
+    steps = {"bj": [], "two": [], "const": [], "learned": []}
+    for seed in range(2000, 2003):
+        g = bem.bembel_geom_create(bem.BEMBEL_GEOM_PERTURBED_SPHERE, coeffs=perturbed_sphere_coeffs(seed))
+        op = bem.bembel_assemble(g, bem.BEMBEL_HELMHOLTZ_SL, k, L, d, 4, precision=bem.BEMBEL_PREC_MIXED)
+        n = bem.bembel_ndofs(op)
+        b = torch.empty(n, dtype=torch.complex128, device="cuda")
+        bem.bembel_rhs(op, bem.BEMBEL_RHS_PLANE_WAVE, [[0.0, 0.0, 1.0]], b)
+        x = torch.empty_like(b)
+
+        def run(kind, prm=None):
+            if prm is not None:
+                bem.bembel_learned_attach(op, prm)
+            inf = bem.bembel_solve(op, b, x, 1, tol=1e-8, restart=100, max_iter=4000, precond=kind)
+            assert inf["converged"], inf
+            return inf["iterations"]
+
+        steps["bj"].append(run(bem.BEMBEL_PRECOND_BLOCK_JACOBI))
+        steps["two"].append(run(bem.BEMBEL_PRECOND_TWO_LEVEL))
+        steps["const"].append(min(run(bem.BEMBEL_PRECOND_LEARNED, const(w)) for w in (0.25, 0.5)))
+        steps["learned"].append(run(bem.BEMBEL_PRECOND_LEARNED, p1))
+    m = {key: float(np.mean(v)) for key, v in steps.items()}
+    print("mean GMRES steps:", m)
+    assert m["learned"] < 0.6 * m["bj"]
+    assert m["learned"] < 0.85 * m["const"] and m["learned"] < m["two"]
