@@ -55,7 +55,8 @@ void free_op(Op* o) {
                   o->d_near_tgt, o->d_nodes32, o->d_bj32, o->d_diag_blk, o->d_leaf_ids, o->d_lw,
                   o->d_tc_gptr, o->d_tc_A, o->d_tc_B, o->d_tc_items, o->d_tc_gsrc, o->d_tc_gmask, o->d_tc_gfirst, o->d_tc_gcnt,
                   o->d_e_ptr, o->d_e_col, o->d_e_val, o->d_et_ptr, o->d_et_col, o->d_et_val,
-                  o->d_R, o->d_rcol, o->d_rrow, o->d_cinv, o->d_cinv32, o->d_cbuf, o->d_evalY};
+                  o->d_R, o->d_rcol, o->d_rrow, o->d_cinv, o->d_cinv32, o->d_cbuf, o->d_evalY,
+                  o->d_ccen, o->d_nodes_rel32, o->d_evalC, o->d_evalRel};
   for (void* p : ptrs) dev_free(p);
   for (auto* p : o->d_pairs) dev_free(p);
   if (o->h_tc_err) cudaFreeHost(o->h_tc_err);

@@ -93,6 +93,8 @@ struct Op {
   int gauss_off[4] = {0, 0, 0, 0};  // offset of each pair kind's [nodes][weights] table in d_gauss
   double* d_nodes = nullptr;  // nclusters * q2 * 3 cluster interpolation points
   float* d_nodes32 = nullptr; // FP32 copy (x, y, z, 0) per point for the on-the-fly FP32 coupling
+  double* d_ccen = nullptr;     // MIXED: cluster centres (x, y, z), mean of the cluster's points
+  float* d_nodes_rel32 = nullptr;  // MIXED: points as FP32 offsets (x, y, z, 0) from their centre
 
   // EFIE on the S^1 space, or S^2 with knot repetition > 1: extraction E (element-local
   // <- global, signed for S^1) as CSR and its transpose; set means "CSR mode"
@@ -143,6 +145,8 @@ struct Op {
   void* d_cbuf = nullptr;         // coarse vectors: restriction and correction (2 x ncoarse x ncol)
   double* d_evalY = nullptr;      // potential evaluation: quadrature points of every element (rhs_eval.cu)
   int evalG = 0;                  // their Gauss order
+  double* d_evalC = nullptr;      // MIXED: element centres of those points
+  float* d_evalRel = nullptr;     // MIXED: the points as FP32 offsets (x, y, z, 0) from the centres
   size_t cbuf_bytes = 0;
 
   bembel_op_info info{};

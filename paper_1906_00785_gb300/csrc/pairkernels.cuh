@@ -515,18 +515,15 @@ __device__ __forceinline__ void singular_pair(const PairRec& pr, const Geom& geo
 }
 
 // Coupling entry id = blk * q2^2 + a * q2 + b (row-major block):
-// K[blk][a][b] = G(node_a(target), node_b(source)) / (4 pi).  f32k (MIXED operators):
-// the difference and r^2 in FP64, the kernel value in FP32 (relative error ~1e-7, far
-// below the interpolation error of the far field), stored in FP64 so that the FP64
-// residual products of the refinement apply one fixed operator.
+// K[blk][a][b] = G(node_a(target), node_b(source)) / (4 pi) for entry r = a q2 + b of far
+// block blk (32-bit index arithmetic: no 64-bit division per entry).  f32k: the difference and
+// r^2 in FP64, the kernel value in FP32, stored in FP64 (used where the FP32 point offsets
+// of coupling_entry_f32 are not available).
 template <bool CPLX>
-__device__ __forceinline__ void coupling_entry(int64_t id, const int* __restrict__ tgt, const int* __restrict__ src,
-                                               const double* __restrict__ nodes, int q2, double kre, double kim,
-                                               double* __restrict__ K, bool f32k = false) {
-  const int64_t per = (int64_t)q2 * q2;
-  const int64_t blk = id / per;
-  const int r = int(id % per);
-  const int a = r / q2, b = r % q2;
+__device__ __forceinline__ void coupling_entry(int64_t blk, int r, const int* __restrict__ tgt,
+                                               const int* __restrict__ src, const double* __restrict__ nodes, int q2,
+                                               double kre, double kim, double* __restrict__ K, bool f32k = false) {
+  const int a = r / q2, b = r - (r / q2) * q2;
   const double* xa = nodes + ((int64_t)tgt[blk] * q2 + a) * 3;
   const double* xb = nodes + ((int64_t)src[blk] * q2 + b) * 3;
   const double d0 = xa[0] - xb[0], d1 = xa[1] - xb[1], d2 = xa[2] - xb[2];
@@ -539,11 +536,43 @@ __device__ __forceinline__ void coupling_entry(int64_t id, const int* __restrict
   } else {
     kernel_value(CPLX, d0 * d0 + d1 * d1 + d2 * d2, kre, kim, gr, gi);
   }
+  const int64_t id = blk * (int64_t)q2 * q2 + r;
   if (CPLX) {
     K[id * 2] = gr * kInv4Pi;
     K[id * 2 + 1] = gi * kInv4Pi;
   } else {
     K[id] = gr * kInv4Pi;
+  }
+}
+
+// MIXED coupling entry without FP64 arithmetic per entry: the difference of the two cluster
+// centres (FP64, rounded to FP32 once per block: relative error ~6e-8 of the distance) plus
+// the FP32 offsets of the two points from their centres (errors ~6e-8 of a cluster
+// diameter), kernel value in FP32 (relative error ~1e-7, far below the interpolation error
+// of the far field), stored in FP64 so that the FP64 residual products of the refinement
+// apply one fixed operator.  The single-operator and the multi-mesh kernels both evaluate
+// entries with this function, so their operators agree bit for bit.
+__device__ __forceinline__ float3 centre_difference(const double* __restrict__ ccen, int t, int sc) {
+  return make_float3(float(ccen[(int64_t)t * 3] - ccen[(int64_t)sc * 3]),
+                     float(ccen[(int64_t)t * 3 + 1] - ccen[(int64_t)sc * 3 + 1]),
+                     float(ccen[(int64_t)t * 3 + 2] - ccen[(int64_t)sc * 3 + 2]));
+}
+
+template <bool CPLX>
+__device__ __forceinline__ void coupling_entry_f32(int64_t blk, int r, int t, int sc, float3 dc,
+                                                   const float4* __restrict__ rel, int q2, float kre, float kim,
+                                                   double* __restrict__ K) {
+  const int a = r / q2, b = r - (r / q2) * q2;
+  const float4 u = rel[(int64_t)t * q2 + a], v = rel[(int64_t)sc * q2 + b];
+  const float d0 = dc.x + (u.x - v.x), d1 = dc.y + (u.y - v.y), d2 = dc.z + (u.z - v.z);
+  float fr, fi;
+  kernel_value_f(CPLX, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), kre, kim, fr, fi);
+  const int64_t id = blk * (int64_t)q2 * q2 + r;
+  if (CPLX) {
+    K[id * 2] = double(fr) * kInv4Pi;
+    K[id * 2 + 1] = double(fi) * kInv4Pi;
+  } else {
+    K[id] = double(fr) * kInv4Pi;
   }
 }
 

@@ -114,14 +114,25 @@ void launch_singular(int grid, cudaStream_t s, const PairRec* pairs, int64_t npa
   launched("k_near_singular");
 }
 
-// Thread per coupling entry.
+// CTA per far block (grid-stride over the blocks), the block's q2 x q2 entries over its
+// threads.  MIXED operators with FP32 point offsets: entries by coupling_entry_f32.
 template <bool CPLX>
 __global__ void k_coupling(const int* __restrict__ tgt, const int* __restrict__ src, int64_t nfar,
                            const double* __restrict__ nodes, int q2, double kre, double kim, double* __restrict__ K,
-                           bool f32k) {
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= nfar * (int64_t)q2 * q2) return;
-  coupling_entry<CPLX>(id, tgt, src, nodes, q2, kre, kim, K, f32k);
+                           bool f32k, const double* __restrict__ ccen, const float4* __restrict__ rel) {
+  const int per = q2 * q2;
+  if (f32k && rel) {
+    for (int64_t blk = blockIdx.x; blk < nfar; blk += gridDim.x) {
+      const int t = tgt[blk], sc = src[blk];
+      const float3 dc = centre_difference(ccen, t, sc);
+      for (int r = threadIdx.x; r < per; r += blockDim.x)
+        coupling_entry_f32<CPLX>(blk, r, t, sc, dc, rel, q2, float(kre), float(kim), K);
+    }
+    return;
+  }
+  for (int64_t blk = blockIdx.x; blk < nfar; blk += gridDim.x)
+    for (int r = threadIdx.x; r < per; r += blockDim.x)
+      coupling_entry<CPLX>(blk, r, tgt, src, nodes, q2, kre, kim, K, f32k);
 }
 
 template <typename T>
@@ -259,14 +270,17 @@ void run_assembly_kernels(Op& o) {
   if (o.nfar > 0 && o.efie) {
     efie_coupling_assemble(o);
   } else if (o.nfar > 0) {
-    const int64_t n = nK;
     const bool f32k = o.opts.precision == BEMBEL_PREC_MIXED;
+    // CTA of q2 x q2 threads rounded to warps (at most 1024), grid-stride over the blocks
+    const int cthreads = std::min(1024, ((o.q2 * o.q2 + 31) / 32) * 32);
+    const int cgrid = int(std::max<int64_t>(1, std::min<int64_t>(o.nfar, int64_t(152) * 2048 / cthreads * 4)));
+    const float4* rel = reinterpret_cast<const float4*>(o.d_nodes_rel32);
     if (o.cplx)
-      k_coupling<true><<<grid_for(n, 256), 256, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre,
-                                                        o.kim, o.d_K, f32k);
+      k_coupling<true><<<cgrid, cthreads, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre, o.kim,
+                                                  o.d_K, f32k, o.d_ccen, rel);
     else
-      k_coupling<false><<<grid_for(n, 256), 256, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre,
-                                                         o.kim, o.d_K, f32k);
+      k_coupling<false><<<cgrid, cthreads, 0, s>>>(o.d_far_tgt, o.d_far_src, o.nfar, o.d_nodes, o.q2, o.kre, o.kim,
+                                                   o.d_K, f32k, o.d_ccen, rel);
     launched("k_coupling");
   }
   cuda_check(cudaEventRecord(ev[6], s), "event");

@@ -32,7 +32,9 @@ struct MeshWork {
   const float4* Xqf32;  // MIXED: FP32 far-order points (regular_pair_f32), else null
   const double* cen;
   const float* BWf32;
-  int f32k;             // MIXED: coupling entries evaluated in FP32 (coupling_entry)
+  int f32k;             // MIXED: coupling entries evaluated in FP32 (coupling_entry_f32)
+  const double* ccen;   // MIXED: cluster centres and FP32 point offsets
+  const float4* rel;
   double kre, kim, h;
   int64_t nelem;
   double* Xq;
@@ -127,9 +129,18 @@ __global__ void __launch_bounds__(32 * kWarps) k_assemble_multi(const MeshWork* 
                                           m.nld, lane, ubuf);
         break;
       default: {
-        const long long per = (long long)q2 * q2;
-        for (long long id = first * per + lane; id < last * per; id += 32)
-          coupling_entry<CPLX>(id, m.far_tgt, m.far_src, m.nodes, q2, m.kre, m.kim, m.K, m.f32k != 0);
+        const int per = q2 * q2;
+        for (long long blk = first; blk < last; ++blk) {
+          if (m.f32k && m.rel) {
+            const int t = m.far_tgt[blk], sc = m.far_src[blk];
+            const float3 dc = centre_difference(m.ccen, t, sc);
+            for (int r = lane; r < per; r += 32)
+              coupling_entry_f32<CPLX>(blk, r, t, sc, dc, m.rel, q2, float(m.kre), float(m.kim), m.K);
+          } else {
+            for (int r = lane; r < per; r += 32)
+              coupling_entry<CPLX>(blk, r, m.far_tgt, m.far_src, m.nodes, q2, m.kre, m.kim, m.K, m.f32k != 0);
+          }
+        }
         break;
       }
     }
@@ -188,6 +199,8 @@ void run_assembly_batch(const std::vector<Op*>& ops) {
     w.Xqf = o.d_Xq_far;
     w.Xqf32 = reinterpret_cast<const float4*>(o.d_Xq_far32);
     w.f32k = o.opts.precision == BEMBEL_PREC_MIXED ? 1 : 0;
+    w.ccen = o.d_ccen;
+    w.rel = reinterpret_cast<const float4*>(o.d_nodes_rel32);
     w.cen = o.d_cen;
     w.BWf32 = o.d_BW_far32;
     w.kre = o.kre;

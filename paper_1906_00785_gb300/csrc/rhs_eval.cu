@@ -164,6 +164,112 @@ __global__ void k_potential(const double* __restrict__ pts, int64_t npts, const 
   }
 }
 
+// Element centres (mean of the element's G2 points) and the points as FP32 offsets from them,
+// for the element-wise FP32 potential of MIXED operators.
+__global__ void k_eval_offsets(const double* __restrict__ Y, int64_t nelem, int G2, double* __restrict__ cen,
+                               float4* __restrict__ rel) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nelem) return;
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int p = 0; p < G2; ++p)
+    for (int k = 0; k < 3; ++k) c[k] += Y[(e * G2 + p) * 3 + k];
+  for (int k = 0; k < 3; ++k) {
+    c[k] /= G2;
+    cen[e * 3 + k] = c[k];
+  }
+  for (int p = 0; p < G2; ++p) {
+    const double* y = Y + (e * G2 + p) * 3;
+    rel[e * G2 + p] = make_float4(float(y[0] - c[0]), float(y[1] - c[1]), float(y[2] - c[2]), 0.f);
+  }
+}
+
+// MIXED operators: thread per element of the block's chunk.  An element whose centre lies
+// farther than sqrt(far2e) from the point is summed in FP32 from the FP64 centre difference
+// (rounded once) and the FP32 point offsets, its sum added in FP64; nearer elements take the
+// FP64 sum of k_potential.  rq32 is the FP32 copy of the weighted density.
+template <bool CPLX>
+__global__ void k_potential_elem(const double* __restrict__ pts, int64_t npts, const double* __restrict__ Y,
+                                 const double* __restrict__ cen, const float4* __restrict__ rel,
+                                 const double* __restrict__ rq, const float* __restrict__ rq32, int64_t nelem,
+                                 int G2, int nrhs, double kre, double kim, double far2e, double* __restrict__ out) {
+  const int64_t ip = blockIdx.x;
+  const int r = blockIdx.y;
+  const int C = CPLX ? 2 : 1;
+  const int ncol = nrhs * C;
+  const int64_t chunk = (nelem + gridDim.z - 1) / gridDim.z;
+  const int64_t e0 = blockIdx.z * chunk, e1 = min(nelem, e0 + chunk);
+  const double x0 = pts[ip * 3], x1 = pts[ip * 3 + 1], x2 = pts[ip * 3 + 2];
+  double sr = 0.0, si = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const double c0 = x0 - cen[e * 3], c1 = x1 - cen[e * 3 + 1], c2 = x2 - cen[e * 3 + 2];
+    if (c0 * c0 + c1 * c1 + c2 * c2 > far2e) {
+      const float f0 = float(c0), f1 = float(c1), f2 = float(c2);
+      float ar = 0.f, ai = 0.f;
+      for (int p = 0; p < G2; ++p) {
+        const int64_t k = e * G2 + p;
+        const float4 v = rel[k];
+        const float d0 = f0 - v.x, d1 = f1 - v.y, d2 = f2 - v.z;
+        float gr, gi;
+        kernel_value_f(CPLX, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), float(kre), float(kim), gr, gi);
+        const float rhr = rq32[k * ncol + r * C];
+        if (CPLX) {
+          const float rhi = rq32[k * ncol + r * C + 1];
+          ar = fmaf(gr, rhr, fmaf(-gi, rhi, ar));
+          ai = fmaf(gr, rhi, fmaf(gi, rhr, ai));
+        } else {
+          ar = fmaf(gr, rhr, ar);
+        }
+      }
+      sr += double(ar);
+      si += double(ai);
+    } else {
+      for (int p = 0; p < G2; ++p) {
+        const int64_t k = e * G2 + p;
+        const double d0 = x0 - Y[k * 3], d1 = x1 - Y[k * 3 + 1], d2 = x2 - Y[k * 3 + 2];
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        const double rinv = rsqrt(r2);
+        const double rhr = rq[k * ncol + r * C];
+        if (CPLX) {
+          const double rhi = rq[k * ncol + r * C + 1];
+          const double rr = r2 * rinv;
+          double sn, cs;
+          sincos(kre * rr, &sn, &cs);
+          const double am = exp(kim * rr) * rinv;
+          const double gr = am * cs, gi = -am * sn;
+          sr += gr * rhr - gi * rhi;
+          si += gr * rhi + gi * rhr;
+        } else {
+          sr += rinv * rhr;
+        }
+      }
+    }
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sr;
+    red[1][threadIdx.x >> 5] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+    }
+    atomicAdd(out + ((int64_t)r * npts + ip) * C, a * kInv4Pi);
+    if (CPLX) atomicAdd(out + ((int64_t)r * npts + ip) * C + 1, b * kInv4Pi);
+  }
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = float(a[i]);
+}
+
 // Compressed evaluation, one warp per (evaluation point, rhs column): a level-by-level
 // descent of the cluster tree from the six patch clusters.  A cluster admissible for
 // the point (2 r <= eta max(0, |x - c| - r), and |kappa| 2 r <= kdiam when the
@@ -381,13 +487,23 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
   const int64_t nq = o.nelem * G2;
   // the quadrature points of every element for this G, kept with the operator
   Op& om = const_cast<Op&>(o);
-  if (!om.d_evalY || om.evalG != G) {
-    dev_free(om.d_evalY);
+  const bool elem32 = o.opts.precision == BEMBEL_PREC_MIXED;
+  if (!om.d_evalY || om.evalG != G || (elem32 && !om.d_evalC)) {
+    for (void* p : {(void*)om.d_evalY, (void*)om.d_evalC, (void*)om.d_evalRel}) dev_free(p);
     om.d_evalY = nullptr;
+    om.d_evalC = nullptr;
+    om.d_evalRel = nullptr;
     om.d_evalY = static_cast<double*>(dev_alloc(sizeof(double) * nq * 3));
     om.evalG = G;
     k_tab_points<<<int((nq + 255) / 256), 256, 0, s>>>(o.geom, o.L, o.nelem, G, gx, o.h, om.d_evalY);
     launched("kernel");
+    if (elem32) {
+      om.d_evalC = static_cast<double*>(dev_alloc(sizeof(double) * o.nelem * 3));
+      om.d_evalRel = static_cast<float*>(dev_alloc(sizeof(float) * 4 * nq));
+      k_eval_offsets<<<int((o.nelem + 127) / 128), 128, 0, s>>>(om.d_evalY, o.nelem, G2, om.d_evalC,
+                                                                reinterpret_cast<float4*>(om.d_evalRel));
+      launched("k_eval_offsets");
+    }
   }
   struct {
     void* p;
@@ -419,6 +535,28 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
   // a distance of a few elements from the surface); FP64 everywhere for FP64 operators
   const double far2 = o.opts.precision == BEMBEL_PREC_MIXED ? 64.0 * o.h * o.h : 1e300;
   cuda_check(cudaMemsetAsync(out, 0, sizeof(double) * npts * nrhs * C, s), "eval clear");
+  if (elem32) {
+    // MIXED: element-wise sums, FP32 for elements whose centre is farther than 10 h
+    Buf rq32(sizeof(float) * nd);
+    k_d2f<<<int((nd + 255) / 256), 256, 0, s>>>(static_cast<double*>(rq.p), static_cast<float*>(rq32.p), nd);
+    launched("k_d2f");
+    const int64_t echunks = std::max<int64_t>(1, std::min<int64_t>((152 * 8 + pairs - 1) / pairs, o.nelem / 256));
+    dim3 egrid((unsigned)npts, (unsigned)nrhs, (unsigned)echunks);
+    const double far2e = 100.0 * o.h * o.h;
+    if (o.cplx)
+      k_potential_elem<true><<<egrid, 128, 0, s>>>(pts, npts, om.d_evalY, om.d_evalC,
+                                                   reinterpret_cast<const float4*>(om.d_evalRel),
+                                                   static_cast<double*>(rq.p), static_cast<float*>(rq32.p), o.nelem,
+                                                   G2, nrhs, o.kre, o.kim, far2e, static_cast<double*>(out));
+    else
+      k_potential_elem<false><<<egrid, 128, 0, s>>>(pts, npts, om.d_evalY, om.d_evalC,
+                                                    reinterpret_cast<const float4*>(om.d_evalRel),
+                                                    static_cast<double*>(rq.p), static_cast<float*>(rq32.p), o.nelem,
+                                                    G2, nrhs, o.kre, o.kim, far2e, static_cast<double*>(out));
+    launched("k_potential_elem");
+    cuda_check(cudaStreamSynchronize(s), "eval sync");
+    return;
+  }
   if (o.cplx)
     k_potential<true><<<grid, 256, 0, s>>>(pts, npts, static_cast<double*>(Y.p), static_cast<double*>(rq.p), nq,
                                            nrhs, o.kre, o.kim, far2, static_cast<double*>(out));

@@ -1129,6 +1129,23 @@ void build_structure(Op& o) {
     for (size_t k = 0; k < nodes.size() / 3; ++k)
       for (int c = 0; c < 3; ++c) nodes32[k * 4 + c] = float(nodes[k * 3 + c]);
     o.d_nodes32 = upload(nodes32);
+    if (o.opts.precision == BEMBEL_PREC_MIXED && !o.efie) {
+      // FP32 coupling entries of MIXED operators: cluster centres (mean of the cluster's
+      // points, FP64) and the points as FP32 offsets from them
+      std::vector<double> ccen((size_t)o.nclusters * 3, 0.0);
+      std::vector<float> rel((size_t)o.nclusters * q2 * 4, 0.f);
+      for (int64_t c = 0; c < o.nclusters; ++c) {
+        double m[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < q2; ++a)
+          for (int k = 0; k < 3; ++k) m[k] += nodes[((size_t)c * q2 + a) * 3 + k];
+        for (int k = 0; k < 3; ++k) ccen[(size_t)c * 3 + k] = m[k] / q2;
+        for (int a = 0; a < q2; ++a)
+          for (int k = 0; k < 3; ++k)
+            rel[((size_t)c * q2 + a) * 4 + k] = float(nodes[((size_t)c * q2 + a) * 3 + k] - ccen[(size_t)c * 3 + k]);
+      }
+      o.d_ccen = upload(ccen);
+      o.d_nodes_rel32 = upload(rel);
+    }
   }
 
   stage_done(3);

@@ -3,7 +3,7 @@ FP32 far-field coupling evaluated on the fly or streamed from a stored FP32 copy
 
 * The report's scores are positive for the levels tried and the chosen leaf level is the
   cheapest one; the chosen storage is the faster of the two timed products.
-* Both storages give the same FP32 product up to FP32 rounding of the kernel values, and
+* Both storages give the same FP32 product up to FP32 rounding of the kernel values (5e-6), and
   both stay within FP32 accuracy of the FP64 product."""
 import numpy as np
 import pytest
@@ -43,7 +43,9 @@ def test_layout_choice(kind, k):
     bem.bembel_matvec(ops[0], x, y64, 1)
     torch.cuda.synchronize()
     nrm = torch.linalg.norm(y64).item()
-    assert torch.linalg.norm(y[0] - y[1]).item() / nrm < 1e-6
+    # on the fly: kernel values from absolute FP32 points (distance error up to ~6e-8 |x| / r,
+    # about 1e-6 for the closest far blocks); stored: from FP32 offsets to the cluster centres
+    assert torch.linalg.norm(y[0] - y[1]).item() / nrm < 5e-6
     for yy in y:
         assert torch.linalg.norm(yy.to(y64.dtype) - y64).item() / nrm < 1e-5
 
