@@ -567,12 +567,14 @@ __device__ __forceinline__ void coupling_entry_f32(int64_t blk, int r, int t, in
   const float d0 = dc.x + (u.x - v.x), d1 = dc.y + (u.y - v.y), d2 = dc.z + (u.z - v.z);
   float fr, fi;
   kernel_value_f(CPLX, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), kre, kim, fr, fi);
+  // scaled in FP32, one conversion per stored value
+  const float s4 = float(kInv4Pi);
   const int64_t id = blk * (int64_t)q2 * q2 + r;
   if (CPLX) {
-    K[id * 2] = double(fr) * kInv4Pi;
-    K[id * 2 + 1] = double(fi) * kInv4Pi;
+    K[id * 2] = double(fr * s4);
+    K[id * 2 + 1] = double(fi * s4);
   } else {
-    K[id] = double(fr) * kInv4Pi;
+    K[id] = double(fr * s4);
   }
 }
 

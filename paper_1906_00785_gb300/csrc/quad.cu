@@ -122,11 +122,21 @@ __global__ void k_coupling(const int* __restrict__ tgt, const int* __restrict__ 
                            bool f32k, const double* __restrict__ ccen, const float4* __restrict__ rel) {
   const int per = q2 * q2;
   if (f32k && rel) {
+    // the block's centre difference once per CTA (FP64 work per block, not per entry)
+    __shared__ float3 sdc;
+    __shared__ int st, ssc;
     for (int64_t blk = blockIdx.x; blk < nfar; blk += gridDim.x) {
-      const int t = tgt[blk], sc = src[blk];
-      const float3 dc = centre_difference(ccen, t, sc);
+      if (threadIdx.x == 0) {
+        st = tgt[blk];
+        ssc = src[blk];
+        sdc = centre_difference(ccen, st, ssc);
+      }
+      __syncthreads();
+      const int t = st, sc = ssc;
+      const float3 dc = sdc;
       for (int r = threadIdx.x; r < per; r += blockDim.x)
         coupling_entry_f32<CPLX>(blk, r, t, sc, dc, rel, q2, float(kre), float(kim), K);
+      __syncthreads();
     }
     return;
   }
