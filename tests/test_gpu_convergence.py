@@ -7,7 +7,7 @@ available): plane wave along +z polarised in x, kappa = 3, scattered field at th
 points of the sphere grid of radius 6 (Sec. 5, Util::makeSphereGrid(6, 10)) against the
 Mie series, dense operators (q = 0) at high quadrature orders so that quadrature stays
 below the discretisation error.  The S^2 analogue is the Laplace point-charge problem of
-the interior ball (config 1): potential at 100 points in the ball of radius 0.5 against
+the interior ball (point charge at (0, 0, 2)): potential at 100 points in the ball of radius 0.5 against
 1/|x - x0|, expected order 2d + 3 for ansatz degree d.
 
 Fitted orders come from the last two levels and must reach the expected order minus 0.8
