@@ -470,7 +470,9 @@ int bembel_rhs(const bembel_op* op, int kind, const double* params, int nrhs, in
  * b_dev, x_dev: device FP64 (complex for Helmholtz), column-major.  MIXED
  * operators with refine = 1 run FP32 inner GMRES inside FP64 iterative
  * refinement (residual r = b - A x in FP64 each outer step).  info may be NULL.
- * Errors: EINVAL, ENOMEM, ECUDA, ENOTCONV (x holds the last iterate). */
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOTCONV (x holds the last iterate), EUNSUPPORTED
+ * (a preconditioner the operator cannot take: block-Jacobi leaves whose [D | I] exceeds
+ * 227 KiB, a coarse space with knot_repetition > 1). */
 int bembel_solve(const bembel_op* op, const void* b_dev, void* x_dev, int nrhs, const bembel_solve_opts* so,
                  bembel_solve_info* info);
 

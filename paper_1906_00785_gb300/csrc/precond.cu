@@ -8,6 +8,7 @@
 // injective, so for the SPD Laplace blocks M^-1 is SPD.  Not part of the paper
 // (which solves without a preconditioner); it is the fallback preconditioner
 // of the solver.
+#include <string>
 #include <vector>
 
 #include "op.h"
@@ -114,11 +115,15 @@ __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b
 void precond_setup(Op& o) {
   if (o.d_bj) return;
   const int C = o.cplx ? 2 : 1;
+  const size_t shm = sizeof(double) * o.nld * 2 * o.nld * C;
+  // one CTA holds [D | I] of a leaf in shared memory (at most 227 KiB)
+  if (shm > 227 * 1024)
+    fail(BEMBEL_EUNSUPPORTED, "block-Jacobi: leaf blocks of " + std::to_string(o.nld) +
+                                  " local dofs exceed one CTA's shared memory (use a finer leaf level)");
   const int64_t n = o.nleaf * (int64_t)o.nld * o.nld * C;
   o.d_bj = static_cast<double*>(dev_alloc(sizeof(double) * n));
   int* info = static_cast<int*>(dev_alloc(sizeof(int) * o.nleaf));
   cuda_check(cudaMemsetAsync(info, 0, sizeof(int) * o.nleaf, o.stream), "bj info");
-  const size_t shm = sizeof(double) * o.nld * 2 * o.nld * C;
   const int threads = std::max(32, ((o.nld + 31) / 32) * 32);
   if (o.cplx) {
     if (shm > 48 * 1024)
