@@ -118,3 +118,18 @@ def test_invalid_uses(geom):
     with pytest.raises(bem.BembelError) as ei:
         bem.bembel_precond_apply(efie, BJ, xe, torch.empty_like(xe), 1)
     assert ei.value.code == bem.BEMBEL_EUNSUPPORTED
+
+
+def test_block_jacobi_leaf_too_large(geom):
+    """Leaves of 576 local dofs (level 4, degree 2, leaf level 1): [D | I] of one leaf does not
+    fit one CTA's shared memory, and the set-up says so before any device work."""
+    gop = bem.bembel_assemble(geom, LAP, 0.0, 4, 2, 4, leaf_level=1)
+    n = bem.bembel_ndofs(gop)
+    x = torch.from_numpy(random_vector(n, 4)).cuda()
+    with pytest.raises(bem.BembelError) as ei:
+        bem.bembel_precond_apply(gop, BJ, x, torch.empty_like(x), 1)
+    assert ei.value.code == bem.BEMBEL_EUNSUPPORTED
+    # the operator stays usable: its product runs
+    y = torch.empty_like(x)
+    bem.bembel_matvec(gop, x, y, 1)
+    assert torch.isfinite(y).all().item()
