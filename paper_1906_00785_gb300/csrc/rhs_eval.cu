@@ -97,11 +97,12 @@ __global__ void k_density_points(const double* __restrict__ rl, int64_t nelem, i
   rq[id] = acc * gw[p % G] * gw[p / G] * h * h;
 }
 
-// Block per (evaluation point, rhs): u = sum over element points G(x, y) rq / (4 pi).
+// Block per (evaluation point, rhs, source chunk): u = sum over element points G(x, y) rq /
+// (4 pi), in FP64 (FP64 operators; MIXED operators use k_potential_elem).
 template <bool CPLX>
 __global__ void k_potential(const double* __restrict__ pts, int64_t npts, const double* __restrict__ Y,
                             const double* __restrict__ rq, int64_t nsrc, int nrhs, double kre, double kim,
-                            double far2, double* __restrict__ out) {
+                            double* __restrict__ out) {
   // block (point, column, source chunk): the chunk's partial sum is added to out
   const int64_t ip = blockIdx.x;
   const int r = blockIdx.y;
@@ -116,24 +117,16 @@ __global__ void k_potential(const double* __restrict__ pts, int64_t npts, const 
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
     const double rhr = rq[k * ncol + r * C];
     double gr, gi = 0.0;
-    if (r2 > far2) {
-      // separated point (MIXED operators): the kernel value in FP32 from the FP64 distance
-      float fr, fi;
-      kernel_value_f(CPLX, float(r2), float(kre), float(kim), fr, fi);
-      gr = fr;
-      gi = fi;
+    const double rinv = rsqrt(r2);
+    if (CPLX) {
+      const double rr = r2 * rinv;
+      double sn, cs;
+      sincos(kre * rr, &sn, &cs);
+      const double am = exp(kim * rr) * rinv;
+      gr = am * cs;
+      gi = -am * sn;
     } else {
-      const double rinv = rsqrt(r2);
-      if (CPLX) {
-        const double rr = r2 * rinv;
-        double sn, cs;
-        sincos(kre * rr, &sn, &cs);
-        const double am = exp(kim * rr) * rinv;
-        gr = am * cs;
-        gi = -am * sn;
-      } else {
-        gr = rinv;
-      }
+      gr = rinv;
     }
     if (CPLX) {
       const double rhi = rq[k * ncol + r * C + 1];
@@ -531,9 +524,6 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
   const int64_t pairs = npts * nrhs;
   const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((152 * 8 + pairs - 1) / pairs, nq / 4096));
   dim3 grid((unsigned)npts, (unsigned)nrhs, (unsigned)chunks);
-  // MIXED operators: FP32 kernel values beyond 8 parameter-element sizes (points that keep
-  // a distance of a few elements from the surface); FP64 everywhere for FP64 operators
-  const double far2 = o.opts.precision == BEMBEL_PREC_MIXED ? 64.0 * o.h * o.h : 1e300;
   cuda_check(cudaMemsetAsync(out, 0, sizeof(double) * npts * nrhs * C, s), "eval clear");
   if (elem32) {
     // MIXED: element-wise sums, FP32 for elements whose centre is farther than 10 h
@@ -559,10 +549,10 @@ void eval_device(const Op& o, const double* pts, int64_t npts, const void* rho, 
   }
   if (o.cplx)
     k_potential<true><<<grid, 256, 0, s>>>(pts, npts, static_cast<double*>(Y.p), static_cast<double*>(rq.p), nq,
-                                           nrhs, o.kre, o.kim, far2, static_cast<double*>(out));
+                                           nrhs, o.kre, o.kim, static_cast<double*>(out));
   else
     k_potential<false><<<grid, 256, 0, s>>>(pts, npts, static_cast<double*>(Y.p), static_cast<double*>(rq.p), nq,
-                                            nrhs, o.kre, o.kim, far2, static_cast<double*>(out));
+                                            nrhs, o.kre, o.kim, static_cast<double*>(out));
   launched("eval kernels");
   cuda_check(cudaStreamSynchronize(s), "eval sync");
 }
