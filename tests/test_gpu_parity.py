@@ -101,7 +101,7 @@ def test_multi_rhs_equals_columns(geom):
         assert torch.max(torch.abs(y1 - Y[r])) <= 1e-13 * torch.max(torch.abs(Y[r]))
 
 
-def test_config1_dense_laplace_end_to_end(geom):
+def test_dense_laplace_point_charge_end_to_end(geom):
     """Dense Laplace, level 3, degree 0: load vector, GMRES, potential."""
     x0 = np.array([0.0, 0.0, 2.0])
     sp = S2Space(Sphere6(), 3, 0)

@@ -75,7 +75,7 @@ def test_laplace_spd_and_pair_symmetry():
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * np.abs(a).max())
 
 
-def test_point_charge_interior_config1():
+def test_point_charge_interior_ball():
     """Interior Dirichlet problem of the dense Laplace workload (level 3, degree 0)."""
     x0 = np.array([0.0, 0.0, 2.0])
     pts = ball_points(100, 0.5, 1)
